@@ -1,0 +1,183 @@
+/*
+ * spgemm.h -- C ABI of the GB300 (sm_103a) semiring SpGEMM library.
+ *
+ * The library computes C = A (x).(+) B for sparse matrices in CSR form over a
+ * semiring chosen by id: the local multiplication at the core of distributed
+ * Sparse SUMMA (McFarland, Bellavita, Guidi, "Parallel GPU-Enabled
+ * Algorithms for SpGEMM on Arbitrary Semirings with Hybrid Communication",
+ * ICPE'25; SpGEMM and Sparse SUMMA: Section 2.1; semirings: Section 2.2;
+ * CSR: Section 2.4; merge of per-stage products: Section 3.4).
+ *
+ * Definition computed (every entry point that multiplies):
+ *     C[i,j] = (+)_{k in cols(A_i), j in cols(B_k)}  A[i,k] (x) B[k,j]
+ * and (i,j) is stored iff at least one product exists (structural pattern;
+ * no entry is dropped because of its value).
+ *
+ * Conventions shared by all entry points
+ * --------------------------------------
+ * - Matrices are CSR: row_ptr is int64 [nrows+1] with row_ptr[0] == 0 and
+ *   non-decreasing; col is int32 [nnz] with column ids in [0, ncols) strictly
+ *   ascending inside each row; val is [nnz] values of the semiring's input type
+ *   (NULL for SPG_SR_BOOL_OR_AND).  Outputs follow the same rules.
+ * - Unless an entry point says "host", every pointer is a DEVICE pointer owned
+ *   by the caller.  The library never frees caller memory and never keeps a
+ *   pointer past the call.  Scratch memory comes from the caller's workspace.
+ * - Work is queued on the caller's CUDA stream (`stream`, a cudaStream_t; NULL
+ *   is the legacy default stream) and runs asynchronously, except where a
+ *   call returns a host count (it then synchronises that stream).
+ * - Argument errors are returned synchronously.  Errors found by kernels
+ *   (hash-table overflow, timeouts) are recorded in the workspace and
+ *   reported by the next call that synchronises, or by spgemm_check().
+ * - B.nrows must equal A.ncols.  Empty matrices and empty rows are valid and
+ *   give empty output rows.
+ */
+#ifndef SPGEMM_H
+#define SPGEMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPG_OK = 0,
+    SPG_ERR_INVALID_ARG = 1,   /* a NULL pointer, a bad id or mismatched shapes      */
+    SPG_ERR_INVALID_CSR = 2,   /* spgemm_validate_csr found a malformed matrix       */
+    SPG_ERR_OOM = 3,           /* a host-side allocation of the host API failed      */
+    SPG_ERR_CUDA = 4,          /* a CUDA runtime call failed (see spgemm_last_error) */
+    SPG_ERR_UNSUPPORTED = 5,   /* shape beyond the library's index range             */
+    SPG_ERR_OVERFLOW = 6,      /* a hash table ran out of slots (capacity too small) */
+    SPG_ERR_TIMEOUT = 7,       /* a bounded device wait gave up                      */
+    SPG_ERR_WORKSPACE = 8      /* workspace NULL or smaller than required            */
+} spg_status;
+
+/* Semirings (Section 2.2): (+) must be commutative and associative, (x) associative. */
+typedef enum {
+    SPG_SR_PLUS_TIMES_F64 = 0, /* (+)=+, (x)=*, double in and out                           */
+    SPG_SR_BOOL_OR_AND = 1,    /* pattern only: val pointers are ignored (pass NULL)         */
+    SPG_SR_MIN_PLUS_F32 = 2,   /* (+)=min, (x)=+, float; min orders -0 below +0; no NaN     */
+    SPG_SR_OVERLAP_I32 = 3,    /* in: int32 position of a k-mer in its read; out: spg_overlap */
+    SPG_SR_PLUS_TIMES_I64 = 4, /* int64, wrap-around modulo 2^64                             */
+    SPG_SR_PLUS_TIMES_F32 = 5  /* float: the "float" semiring of the paper's experiments    */
+} spg_semiring;
+
+/* One CSR matrix (see conventions above). */
+typedef struct {
+    int64_t nrows, ncols, nnz;
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const void* val;
+} spg_csr;
+
+/*
+ * Output record of SPG_SR_OVERLAP_I32 (20 bytes, no padding).  For reads i, j
+ * sharing k-mers: count = number of shared k-mers; (a0,b0) and (a1,b1) are the
+ * two lexicographically smallest (position in read i, position in read j)
+ * pairs, a0 <= a1.  A missing second pair is (INT32_MAX, INT32_MAX).
+ * (x) makes {1, (a,b), none}; (+) adds counts and keeps the two smallest pairs.
+ */
+typedef struct {
+    int32_t count, a0, b0, a1, b1;
+} spg_overlap;
+
+/* Kernel tier limits; 0 in any field keeps the library default. */
+typedef struct {
+    int64_t sym_warp_max_ub;    /* symbolic: ub_i <= this -> one warp per row, hash     */
+    int64_t sym_block_max_ub;   /* symbolic: ub_i <= this -> one CTA per row, hash      */
+    int64_t num_warp_max_nnz;   /* numeric: nnz(C_i) <= this -> warp hash + warp sort  */
+    int64_t num_block_max_nnz;  /* numeric: nnz(C_i) <= this -> CTA hash + CTA sort   */
+    int64_t dense_slab_cols;    /* numeric dense tier: columns per shared-memory slab   */
+    int64_t sym_slab_cols;      /* symbolic dense tier: columns per bitmap slab         */
+    int64_t reserved[4];
+} spg_tuning;
+
+/* Counters of the last analysis on a handle (host copy, filled by spgemm_symbolic). */
+typedef struct {
+    int64_t products;           /* P = sum_i sum_{k in A_i} nnz(B_k)                      */
+    int64_t nnz_c;              /* nnz(C)                                                */
+    int64_t rows_per_tier[4];   /* symbolic rows: dense, block, warp, empty              */
+    int64_t reserved[6];
+} spg_stats;
+
+typedef struct spg_handle spg_handle;
+
+/* Create / destroy a handle (holds tuning, the current device's properties and
+ * the last error text).  A handle is used by one host thread at a time. */
+spg_status spgemm_create(spg_handle** handle);
+spg_status spgemm_destroy(spg_handle* handle);
+
+/* Text of the last error on this handle ("" if none).  Owned by the handle. */
+const char* spgemm_last_error(const spg_handle* handle);
+
+/* Tier limits (see spg_tuning).  They change speed only, never C. */
+spg_status spgemm_set_tuning(spg_handle* handle, const spg_tuning* tuning);
+spg_status spgemm_get_tuning(const spg_handle* handle, spg_tuning* tuning);
+spg_status spgemm_get_stats(const spg_handle* handle, spg_stats* stats);
+
+/*
+ * Bytes of device workspace needed by spgemm_symbolic + spgemm_numeric for
+ * these shapes (only nrows, ncols and nnz of A and B are read).  The same
+ * workspace must be passed to both calls, unchanged in between.
+ */
+spg_status spgemm_workspace_size(spg_handle* handle, spg_semiring sr, const spg_csr* A,
+                                 const spg_csr* B, size_t* bytes);
+
+/*
+ * Symbolic phase (Gustavson, Section 2.1 definition): row analysis and
+ * binning, exact nnz(C_i) per row, and the exclusive scan into C's row_ptr.
+ *   c_row_ptr : device int64 [A.nrows + 1], written.
+ *   c_nnz     : HOST int64, written; the call synchronises `stream` for it.
+ * Errors: SPG_ERR_INVALID_ARG, SPG_ERR_WORKSPACE, SPG_ERR_CUDA, SPG_ERR_OVERFLOW.
+ */
+spg_status spgemm_symbolic(spg_handle* handle, spg_semiring sr, const spg_csr* A,
+                           const spg_csr* B, int64_t* c_row_ptr, int64_t* c_nnz,
+                           void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Numeric phase: accumulates every product with the semiring and writes each
+ * row sorted by column.  Requires the c_row_ptr and workspace of the
+ * spgemm_symbolic call for the same A and B (values of A and B may differ
+ * from that call; patterns may not).
+ *   c_col : device int32 [nnz(C)], written.
+ *   c_val : device [nnz(C)] of the output type (double, float, int64 or
+ *           spg_overlap), written; ignored for SPG_SR_BOOL_OR_AND.
+ * Asynchronous.  Errors found by the kernels surface in spgemm_check().
+ */
+spg_status spgemm_numeric(spg_handle* handle, spg_semiring sr, const spg_csr* A,
+                          const spg_csr* B, const int64_t* c_row_ptr, int32_t* c_col,
+                          void* c_val, void* workspace, size_t workspace_bytes,
+                          void* stream);
+
+/* Synchronises `stream` and returns the first kernel-detected error recorded
+ * in `workspace` since the last spgemm_symbolic (SPG_OK if none). */
+spg_status spgemm_check(spg_handle* handle, void* workspace, void* stream);
+
+/*
+ * CSR validity check (row_ptr monotone from 0 to nnz, columns in range and
+ * strictly ascending per row).  Synchronises `stream`.  Needs 64 bytes of
+ * workspace.  Returns SPG_OK or SPG_ERR_INVALID_CSR.
+ */
+spg_status spgemm_validate_csr(spg_handle* handle, const spg_csr* M, void* workspace,
+                               size_t workspace_bytes, void* stream);
+
+/*
+ * CSR transpose T = A^T with values carried (Section 3.1: the identity
+ * AB = (B^T A^T)^T; also forms A^T for C = A A^T).  Output rows are sorted.
+ *   value_bytes : bytes per value to carry (0 = pattern only; 4, 8, 20, ... <= 64)
+ *   t_row_ptr   : device int64 [A.ncols + 1], written
+ *   t_col       : device int32 [A.nnz], written (row ids of A)
+ *   t_val       : device [A.nnz * value_bytes], written (NULL if value_bytes == 0)
+ * Requires A.nnz < 2^31 - 1.  Asynchronous.
+ */
+spg_status spgemm_transpose_workspace_size(spg_handle* handle, const spg_csr* A, size_t* bytes);
+spg_status spgemm_transpose(spg_handle* handle, const spg_csr* A, int value_bytes,
+                            int64_t* t_row_ptr, int32_t* t_col, void* t_val, void* workspace,
+                            size_t workspace_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPGEMM_H */

@@ -1,0 +1,373 @@
+// C ABI of the SpGEMM library: argument checks, workspace layout, the order
+// of the phases, and the host side of errors.  Every arithmetic step runs in
+// the kernels of symbolic.cu / numeric.cu.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/spgemm.h"
+#include "plan.h"
+#include "semiring.cuh"
+
+using namespace spg;
+
+static constexpr size_t kPinnedBytes = 16384;
+
+struct spg_handle {
+    spg_tuning user;               // user overrides (0 = default)
+    DevInfo dev;
+    int device;
+    std::string err;
+    spg_stats stats;
+    void* pinned;                  // small pinned staging buffer for device counters
+};
+
+namespace spg {
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+WsLayout ws_layout(int64_t R, int64_t E) {
+    WsLayout L{};
+    L.R = R;
+    L.E = E;
+    size_t o = 0;
+    L.status = o;    o = align256(o + sizeof(DevStatus));
+    L.counters = o;  o = align256(o + sizeof(Counters));
+    L.probs = o;     o = align256(o + sizeof(Prob) * kMaxProb);
+    L.ub = o;        o = align256(o + sizeof(int64_t) * (size_t)R);
+    L.cnt = o;       o = align256(o + sizeof(int64_t) * (size_t)(R + 1));
+    L.rows_sym = o;  o = align256(o + sizeof(int32_t) * (size_t)R);
+    L.rows_num = o;  o = align256(o + sizeof(int32_t) * (size_t)R);
+    const int64_t nparts = (R + 2047) / 2048;
+    L.scan_part = o; o = align256(o + sizeof(int64_t) * (size_t)(nparts + 1));
+    L.cursor = o;    o = align256(o + sizeof(int32_t) * (size_t)E);
+    L.total = o;
+    return L;
+}
+
+WsPtrs ws_ptrs(void* ws, const WsLayout& L) {
+    char* b = (char*)ws;
+    WsPtrs w;
+    w.status = (DevStatus*)(b + L.status);
+    w.ctr = (Counters*)(b + L.counters);
+    w.probs = (Prob*)(b + L.probs);
+    w.ub = (int64_t*)(b + L.ub);
+    w.cnt = (int64_t*)(b + L.cnt);
+    w.rows_sym = (int32_t*)(b + L.rows_sym);
+    w.rows_num = (int32_t*)(b + L.rows_num);
+    w.scan_part = (int64_t*)(b + L.scan_part);
+    w.cursor = (int32_t*)(b + L.cursor);
+    return w;
+}
+
+// Shared-memory budget for one CTA's dynamic allocation (leaves room for the
+// kernels' static shared variables).
+constexpr size_t kSmemBudget = 200 * 1024;
+
+Tuning default_tuning(int sr) {
+    Tuning t;
+    t.sym_warp_max_ub = 512;
+    t.sym_block_max_ub = 8192;
+    t.sym_slab_cols = 1 << 20;
+    t.num_warp_max_nnz = 128;
+    t.num_block_max_nnz = 2048;
+    switch (sr) {
+        case SR_BOOL: t.dense_slab_cols = 1 << 18; break;
+        case SR_MP_F32: case SR_PT_F32: t.dense_slab_cols = 16384; break;
+        case SR_OVERLAP: t.dense_slab_cols = 4096; break;
+        default: t.dense_slab_cols = 8192; break;
+    }
+    return t;
+}
+
+static int64_t round_down_pow2(int64_t x) {
+    int64_t p = 1;
+    while (p * 2 <= x) p *= 2;
+    return p;
+}
+
+Tuning clamp_tuning(Tuning t, int sr) {
+    if (t.sym_warp_max_ub < 1) t.sym_warp_max_ub = 1;
+    if (t.sym_block_max_ub < t.sym_warp_max_ub) t.sym_block_max_ub = t.sym_warp_max_ub;
+    while (sym_warp_smem_per_warp(t) * kWarpTierWarps > kSmemBudget)
+        t.sym_warp_max_ub = round_down_pow2(t.sym_warp_max_ub) / 2;
+    while ((size_t)next_pow2(2 * t.sym_block_max_ub) * 4 > kSmemBudget)
+        t.sym_block_max_ub = round_down_pow2(t.sym_block_max_ub) / 2;
+    if (t.sym_block_max_ub < t.sym_warp_max_ub) t.sym_warp_max_ub = t.sym_block_max_ub;
+    t.sym_slab_cols = (t.sym_slab_cols + 1023) / 1024 * 1024;
+    if (t.sym_slab_cols < 1024) t.sym_slab_cols = 1024;
+    while ((size_t)t.sym_slab_cols / 8 > kSmemBudget) t.sym_slab_cols -= 1024;
+    if (t.num_warp_max_nnz < 1) t.num_warp_max_nnz = 1;
+    if (t.num_block_max_nnz < t.num_warp_max_nnz) t.num_block_max_nnz = t.num_warp_max_nnz;
+    while (num_warp_smem_per_warp(sr, t) * kWarpTierWarps > kSmemBudget)
+        t.num_warp_max_nnz = round_down_pow2(t.num_warp_max_nnz) / 2;
+    while (num_block_smem(sr, t) > kSmemBudget)
+        t.num_block_max_nnz = round_down_pow2(t.num_block_max_nnz) / 2;
+    if (t.num_block_max_nnz < t.num_warp_max_nnz) t.num_warp_max_nnz = t.num_block_max_nnz;
+    t.dense_slab_cols = (t.dense_slab_cols + 1023) / 1024 * 1024;
+    if (t.dense_slab_cols < 1024) t.dense_slab_cols = 1024;
+    if (t.dense_slab_cols > 65536 * 16) t.dense_slab_cols = 65536 * 16;
+    while (num_dense_smem(sr, t.dense_slab_cols) > kSmemBudget && t.dense_slab_cols > 1024)
+        t.dense_slab_cols -= 1024;
+    // the dense epilogue scans at most 64 chunks of 1024 columns
+    if (t.dense_slab_cols > 65536) t.dense_slab_cols = 65536;
+    return t;
+}
+
+}  // namespace spg
+
+// ---------------------------------------------------------------------------------
+
+static spg_status fail(spg_handle* h, spg_status s, const char* fmt, ...) {
+    if (h) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        h->err = buf;
+    }
+    return s;
+}
+
+static spg_status cuda_fail(spg_handle* h, cudaError_t e, const char* where) {
+    return fail(h, SPG_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+static bool sr_valid(int sr) { return sr >= 0 && sr <= 5; }
+
+static Tuning effective_tuning(const spg_handle* h, int sr) {
+    Tuning t = default_tuning(sr);
+    const spg_tuning& u = h->user;
+    if (u.sym_warp_max_ub > 0) t.sym_warp_max_ub = u.sym_warp_max_ub;
+    if (u.sym_block_max_ub > 0) t.sym_block_max_ub = u.sym_block_max_ub;
+    if (u.num_warp_max_nnz > 0) t.num_warp_max_nnz = u.num_warp_max_nnz;
+    if (u.num_block_max_nnz > 0) t.num_block_max_nnz = u.num_block_max_nnz;
+    if (u.dense_slab_cols > 0) t.dense_slab_cols = u.dense_slab_cols;
+    if (u.sym_slab_cols > 0) t.sym_slab_cols = u.sym_slab_cols;
+    return clamp_tuning(t, sr);
+}
+
+static DCsr to_dcsr(const spg_csr* M) {
+    return DCsr{M->nrows, M->ncols, M->row_ptr, M->col, M->val};
+}
+
+static spg_status check_csr_arg(spg_handle* h, const spg_csr* M, const char* name, int sr,
+                                bool need_val) {
+    if (!M) return fail(h, SPG_ERR_INVALID_ARG, "%s is NULL", name);
+    if (M->nrows < 0 || M->ncols < 0 || M->nnz < 0)
+        return fail(h, SPG_ERR_INVALID_ARG, "%s has a negative size", name);
+    if (M->nrows >= INT32_MAX || M->ncols >= INT32_MAX)
+        return fail(h, SPG_ERR_UNSUPPORTED, "%s: rows and columns must be < 2^31 - 1", name);
+    if (!M->row_ptr) return fail(h, SPG_ERR_INVALID_ARG, "%s.row_ptr is NULL", name);
+    if (M->nnz > 0 && !M->col) return fail(h, SPG_ERR_INVALID_ARG, "%s.col is NULL", name);
+    if (need_val && sr != SR_BOOL && M->nnz > 0 && !M->val)
+        return fail(h, SPG_ERR_INVALID_ARG, "%s.val is NULL", name);
+    return SPG_OK;
+}
+
+static spg_status check_pair(spg_handle* h, int sr, const spg_csr* A, const spg_csr* B,
+                             bool need_val) {
+    if (!h) return SPG_ERR_INVALID_ARG;
+    if (!sr_valid(sr)) return fail(h, SPG_ERR_INVALID_ARG, "unknown semiring id %d", sr);
+    spg_status s = check_csr_arg(h, A, "A", sr, need_val);
+    if (s != SPG_OK) return s;
+    s = check_csr_arg(h, B, "B", sr, need_val);
+    if (s != SPG_OK) return s;
+    if (A->ncols != B->nrows)
+        return fail(h, SPG_ERR_INVALID_ARG, "A.ncols (%lld) != B.nrows (%lld)",
+                    (long long)A->ncols, (long long)B->nrows);
+    return SPG_OK;
+}
+
+extern "C" {
+
+spg_status spgemm_create(spg_handle** handle) {
+    if (!handle) return SPG_ERR_INVALID_ARG;
+    *handle = nullptr;
+    spg_handle* h = new spg_handle();
+    std::memset(&h->user, 0, sizeof h->user);
+    std::memset(&h->stats, 0, sizeof h->stats);
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&h->dev.sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&h->dev.max_smem_optin,
+                                   cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+    if (e == cudaSuccess) e = cudaMallocHost(&h->pinned, kPinnedBytes);
+    if (e != cudaSuccess) {
+        delete h;
+        return SPG_ERR_CUDA;
+    }
+    *handle = h;
+    return SPG_OK;
+}
+
+spg_status spgemm_destroy(spg_handle* h) {
+    if (!h) return SPG_ERR_INVALID_ARG;
+    if (h->pinned) cudaFreeHost(h->pinned);
+    delete h;
+    return SPG_OK;
+}
+
+const char* spgemm_last_error(const spg_handle* h) { return h ? h->err.c_str() : "no handle"; }
+
+spg_status spgemm_set_tuning(spg_handle* h, const spg_tuning* t) {
+    if (!h || !t) return SPG_ERR_INVALID_ARG;
+    h->user = *t;
+    return SPG_OK;
+}
+
+spg_status spgemm_get_tuning(const spg_handle* h, spg_tuning* t) {
+    if (!h || !t) return SPG_ERR_INVALID_ARG;
+    // report the effective values for plus-times FP64 where the user left 0
+    *t = h->user;
+    return SPG_OK;
+}
+
+spg_status spgemm_get_stats(const spg_handle* h, spg_stats* s) {
+    if (!h || !s) return SPG_ERR_INVALID_ARG;
+    *s = h->stats;
+    return SPG_OK;
+}
+
+spg_status spgemm_workspace_size(spg_handle* h, spg_semiring sr, const spg_csr* A,
+                                 const spg_csr* B, size_t* bytes) {
+    spg_status s = check_pair(h, sr, A, B, false);
+    if (s != SPG_OK) return s;
+    if (!bytes) return fail(h, SPG_ERR_INVALID_ARG, "bytes is NULL");
+    *bytes = ws_layout(A->nrows, A->nnz).total;
+    return SPG_OK;
+}
+
+static spg_status read_status(spg_handle* h, const WsPtrs& w, cudaStream_t st) {
+    DevStatus* hs = (DevStatus*)h->pinned;
+    cudaError_t e = cudaMemcpyAsync(hs, w.status, sizeof(DevStatus), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "status read");
+    if (hs->overflow)
+        return fail(h, SPG_ERR_OVERFLOW, "hash table overflow or inconsistent counts (flat row %lld)",
+                    (long long)hs->info[0]);
+    if (hs->timeout) return fail(h, SPG_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (hs->invalid)
+        return fail(h, SPG_ERR_INVALID_CSR, "invalid CSR (row %lld)", (long long)hs->info[1]);
+    return SPG_OK;
+}
+
+spg_status spgemm_symbolic(spg_handle* h, spg_semiring sr, const spg_csr* A, const spg_csr* B,
+                           int64_t* c_row_ptr, int64_t* c_nnz, void* workspace,
+                           size_t workspace_bytes, void* stream) {
+    spg_status s = check_pair(h, sr, A, B, false);
+    if (s != SPG_OK) return s;
+    if (!c_row_ptr || !c_nnz) return fail(h, SPG_ERR_INVALID_ARG, "c_row_ptr / c_nnz is NULL");
+    const WsLayout L = ws_layout(A->nrows, A->nnz);
+    if (!workspace || workspace_bytes < L.total)
+        return fail(h, SPG_ERR_WORKSPACE, "workspace needs %zu bytes", L.total);
+    cudaStream_t st = (cudaStream_t)stream;
+    const WsPtrs w = ws_ptrs(workspace, L);
+    const Tuning t = effective_tuning(h, sr);
+    cudaError_t e = cudaMemsetAsync(workspace, 0, L.probs, st);   // status + counters
+    if (e != cudaSuccess) return cuda_fail(h, e, "memset");
+    ProbTable* tab = new ProbTable;
+    std::memset(tab, 0, sizeof *tab);
+    tab->p[0] = Prob{to_dcsr(A), to_dcsr(B), c_row_ptr, nullptr, nullptr, 0, 0};
+    e = launch_write_probs(*tab, 1, w, st);
+    delete tab;
+    if (e == cudaSuccess) e = launch_analyze(w, 1, A->nrows, t, st);
+    if (e == cudaSuccess) e = launch_symbolic(w, 1, A->nrows, t, B->ncols, h->dev, st);
+    if (e == cudaSuccess) e = launch_scan_rowptr(w, 1, A->nrows, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "symbolic launch");
+    // bring back nnz, products, bin counts and the status in one copy
+    Counters* hc = (Counters*)((char*)h->pinned);
+    static_assert(sizeof(Counters) <= kPinnedBytes, "staging buffer too small");
+    e = cudaMemcpyAsync(hc, w.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "symbolic");
+    *c_nnz = hc->nnz[0];
+    h->stats.products = (int64_t)hc->products;
+    h->stats.nnz_c = hc->nnz[0];
+    for (int tier = 0; tier < kTiers; ++tier) {
+        int64_t n = 0;
+        for (int b = 0; b < kSubBins; ++b) n += hc->sym_bin_count[tier * kSubBins + b];
+        h->stats.rows_per_tier[tier] = n;
+    }
+    return read_status(h, w, st);
+}
+
+spg_status spgemm_numeric(spg_handle* h, spg_semiring sr, const spg_csr* A, const spg_csr* B,
+                          const int64_t* c_row_ptr, int32_t* c_col, void* c_val,
+                          void* workspace, size_t workspace_bytes, void* stream) {
+    spg_status s = check_pair(h, sr, A, B, true);
+    if (s != SPG_OK) return s;
+    if (!c_row_ptr) return fail(h, SPG_ERR_INVALID_ARG, "c_row_ptr is NULL");
+    const WsLayout L = ws_layout(A->nrows, A->nnz);
+    if (!workspace || workspace_bytes < L.total)
+        return fail(h, SPG_ERR_WORKSPACE, "workspace needs %zu bytes", L.total);
+    cudaStream_t st = (cudaStream_t)stream;
+    const WsPtrs w = ws_ptrs(workspace, L);
+    const Tuning t = effective_tuning(h, sr);
+    ProbTable* tab = new ProbTable;
+    std::memset(tab, 0, sizeof *tab);
+    tab->p[0] = Prob{to_dcsr(A), to_dcsr(B), const_cast<int64_t*>(c_row_ptr), c_col, c_val, 0, 0};
+    cudaError_t e = launch_write_probs(*tab, 1, w, st);
+    delete tab;
+    if (e == cudaSuccess) e = launch_numeric(sr, w, 1, A->nrows, t, B->ncols, h->dev, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "numeric launch");
+    return SPG_OK;
+}
+
+spg_status spgemm_check(spg_handle* h, void* workspace, void* stream) {
+    if (!h || !workspace) return SPG_ERR_INVALID_ARG;
+    const WsLayout L = ws_layout(0, 0);
+    return read_status(h, ws_ptrs(workspace, L), (cudaStream_t)stream);
+}
+
+spg_status spgemm_transpose_workspace_size(spg_handle* h, const spg_csr* A, size_t* bytes) {
+    if (!h) return SPG_ERR_INVALID_ARG;
+    spg_status s = check_csr_arg(h, A, "A", SR_BOOL, false);
+    if (s != SPG_OK) return s;
+    if (!bytes) return fail(h, SPG_ERR_INVALID_ARG, "bytes is NULL");
+    *bytes = transpose_ws_bytes(A->ncols, A->nnz);
+    return SPG_OK;
+}
+
+spg_status spgemm_transpose(spg_handle* h, const spg_csr* A, int value_bytes,
+                            int64_t* t_row_ptr, int32_t* t_col, void* t_val, void* workspace,
+                            size_t workspace_bytes, void* stream) {
+    if (!h) return SPG_ERR_INVALID_ARG;
+    spg_status s = check_csr_arg(h, A, "A", SR_BOOL, false);
+    if (s != SPG_OK) return s;
+    if (A->nnz >= INT32_MAX) return fail(h, SPG_ERR_UNSUPPORTED, "transpose needs nnz < 2^31 - 1");
+    if (value_bytes < 0 || value_bytes > 64)
+        return fail(h, SPG_ERR_INVALID_ARG, "value_bytes must be in [0, 64]");
+    if (value_bytes > 0 && A->nnz > 0 && (!A->val || !t_val))
+        return fail(h, SPG_ERR_INVALID_ARG, "values requested but A.val or t_val is NULL");
+    if (!t_row_ptr || (A->nnz > 0 && !t_col))
+        return fail(h, SPG_ERR_INVALID_ARG, "t_row_ptr / t_col is NULL");
+    const size_t need = transpose_ws_bytes(A->ncols, A->nnz);
+    if (!workspace || workspace_bytes < need)
+        return fail(h, SPG_ERR_WORKSPACE, "workspace needs %zu bytes", need);
+    cudaError_t e = launch_transpose(to_dcsr(A), A->nnz, value_bytes, t_row_ptr, t_col, t_val,
+                                     workspace, h->dev, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "transpose");
+    return SPG_OK;
+}
+
+spg_status spgemm_validate_csr(spg_handle* h, const spg_csr* M, void* workspace,
+                               size_t workspace_bytes, void* stream) {
+    if (!h) return SPG_ERR_INVALID_ARG;
+    spg_status s = check_csr_arg(h, M, "M", SR_BOOL, false);
+    if (s != SPG_OK) return s;
+    if (!workspace || workspace_bytes < 64) return fail(h, SPG_ERR_WORKSPACE, "needs 64 bytes");
+    cudaStream_t st = (cudaStream_t)stream;
+    DevStatus* ds = (DevStatus*)workspace;
+    cudaError_t e = cudaMemsetAsync(ds, 0, sizeof(DevStatus), st);
+    if (e == cudaSuccess) e = launch_validate(to_dcsr(M), M->nnz, ds, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "validate");
+    WsPtrs w{};
+    w.status = ds;
+    return read_status(h, w, st);
+}
+
+}  // extern "C"

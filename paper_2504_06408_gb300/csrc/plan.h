@@ -1,0 +1,104 @@
+// Host-side plan of one SpGEMM call: tuning, workspace layout, kernel
+// launchers.  Shared by the kernel translation units and the C ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace spg {
+
+constexpr int kMaxProb = 128;    // products in one batched call
+constexpr int kTiers = 4;        // 0 dense, 1 block, 2 warp, 3 empty
+constexpr int kSubBins = 40;     // per tier: by floor(log2(work)), heaviest first
+constexpr int kNumBins = kTiers * kSubBins;
+constexpr int kTierDense = 0, kTierBlock = 1, kTierWarp = 2, kTierEmpty = 3;
+
+struct Tuning {
+    int64_t sym_warp_max_ub;
+    int64_t sym_block_max_ub;
+    int64_t num_warp_max_nnz;
+    int64_t num_block_max_nnz;
+    int64_t dense_slab_cols;
+    int64_t sym_slab_cols;
+};
+
+// Per-semiring defaults chosen so that every tier's shared memory fits.
+Tuning default_tuning(int sr);
+// Clamp user values into what the kernels can hold for this semiring.
+Tuning clamp_tuning(Tuning t, int sr);
+
+struct ProbTable {
+    Prob p[kMaxProb];
+};
+
+// Work counters and bin tables at the head of the workspace.
+struct Counters {
+    int32_t sym_bin_count[kNumBins];
+    int32_t sym_bin_off[kNumBins + 1];
+    int32_t sym_bin_cursor[kNumBins];
+    int32_t num_bin_count[kNumBins];
+    int32_t num_bin_off[kNumBins + 1];
+    int32_t num_bin_cursor[kNumBins];
+    int32_t claim[16];                  // per-kernel dynamic row counters
+    unsigned long long products;        // sum of ub over all rows
+    int64_t nnz[kMaxProb];              // per-product nnz(C)
+};
+
+struct WsLayout {
+    size_t status, counters, probs, ub, cnt, rows_sym, rows_num, scan_part, cursor, total;
+    int64_t R;          // flat rows
+    int64_t E;          // flat entries of A (cursor array length)
+};
+
+WsLayout ws_layout(int64_t R, int64_t E);
+
+struct WsPtrs {
+    DevStatus* status;
+    Counters* ctr;
+    Prob* probs;
+    int64_t* ub;
+    int64_t* cnt;
+    int32_t* rows_sym;
+    int32_t* rows_num;
+    int64_t* scan_part;
+    int32_t* cursor;
+};
+WsPtrs ws_ptrs(void* ws, const WsLayout& L);
+
+struct DevInfo {
+    int sms;
+    int max_smem_optin;
+};
+
+// ---- launchers (asynchronous on `st`; return the launch error) ----
+cudaError_t launch_write_probs(const ProbTable& tab, int nprob, const WsPtrs& w, cudaStream_t st);
+cudaError_t launch_analyze(const WsPtrs& w, int nprob, int64_t R, const Tuning& t,
+                           cudaStream_t st);
+cudaError_t launch_symbolic(const WsPtrs& w, int nprob, int64_t R, const Tuning& t,
+                            int64_t max_ncols, const DevInfo& dev, cudaStream_t st);
+cudaError_t launch_scan_rowptr(const WsPtrs& w, int nprob, int64_t R, cudaStream_t st);
+// in-place exclusive scan of cnt[0, R) (int64), cnt[R] = total; part holds
+// scan_parts_needed(R) int64
+cudaError_t launch_scan_inplace(int64_t* cnt, int64_t R, int64_t* part, cudaStream_t st);
+int64_t scan_parts_needed(int64_t R);
+cudaError_t launch_transpose(const DCsr& A, int64_t nnz, int value_bytes, int64_t* t_rp,
+                             int32_t* t_col, void* t_val, void* ws, const DevInfo& dev,
+                             cudaStream_t st);
+size_t transpose_ws_bytes(int64_t ncols, int64_t nnz);
+cudaError_t launch_numeric(int sr, const WsPtrs& w, int nprob, int64_t R, const Tuning& t,
+                           int64_t max_ncols, const DevInfo& dev, cudaStream_t st);
+cudaError_t launch_validate(const DCsr& M, int64_t nnz, DevStatus* status, cudaStream_t st);
+
+// shared-memory bytes of each tier (for tuning clamps and launches)
+size_t sym_warp_smem_per_warp(const Tuning& t);
+size_t num_warp_smem_per_warp(int sr, const Tuning& t);
+size_t num_block_smem(int sr, const Tuning& t);
+size_t num_dense_smem(int sr, int64_t slab_cols);
+
+constexpr int kWarpTierWarps = 8;     // warps per CTA in the warp tiers
+constexpr int kBlockThreads = 512;    // CTA size of the block and dense tiers
+
+}  // namespace spg

@@ -1,0 +1,495 @@
+// Row analysis and binning, symbolic phase, scan into C's row pointers, and
+// the CSR validity check.
+//
+// Symbolic phase: nnz(C_i) = |union over k in cols(A_i) of cols(B_k)| (the
+// pattern of the Section 2.1 product), computed per row in one of three
+// tiers chosen from ub_i = sum_{k in A_i} nnz(B_k):
+//   warp  : one warp per row, key-only hash table in the warp's shared memory
+//   block : one CTA per row, key-only hash table in the CTA's shared memory
+//   dense : one CTA per row, a bitmap over a slab of columns in shared
+//           memory, slab after slab; nnz = popcount.
+#include "plan.h"
+#include "rowwork.cuh"
+
+namespace spg {
+
+SPG_DEV int sym_tier(int64_t ub, const Tuning& t) {
+    if (ub == 0) return kTierEmpty;
+    if (ub <= t.sym_warp_max_ub) return kTierWarp;
+    if (ub <= t.sym_block_max_ub) return kTierBlock;
+    return kTierDense;
+}
+
+// tier-major key; inside a tier rows with more work come first
+SPG_DEV int bin_key(int tier, int64_t work) {
+    int lg = work > 0 ? 63 - __clzll(work) : 0;
+    if (lg > kSubBins - 1) lg = kSubBins - 1;
+    return tier * kSubBins + (kSubBins - 1 - lg);
+}
+
+SPG_DEV int64_t dev_next_pow2(int64_t x) {
+    return x <= 1 ? 1 : (int64_t)1 << (64 - __clzll(x - 1));
+}
+
+__global__ void k_write_probs(ProbTable tab, int nprob, Prob* dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nprob) dst[i] = tab.p[i];
+}
+
+// ub_i, the empty rows' counts, the symbolic bin histogram and P = sum ub.
+__global__ void __launch_bounds__(256) k_analyze(const Prob* __restrict__ probs, int nprob,
+                                                 int64_t R, Tuning t, int64_t* __restrict__ ub,
+                                                 int64_t* __restrict__ cnt, Counters* ctr) {
+    __shared__ int s_hist[kNumBins];
+    for (int b = threadIdx.x; b < kNumBins; b += blockDim.x) s_hist[b] = 0;
+    __syncthreads();
+    const int lane = lane_id();
+    unsigned long long prod = 0;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); g < R; g += nw) {
+        const Prob& P = probs[nprob == 1 ? 0 : find_prob(probs, nprob, g)];
+        const int64_t i = g - P.row_base;
+        const int64_t a0 = ld_i64(P.A.rp + i), a1 = ld_i64(P.A.rp + i + 1);
+        int64_t s = 0;
+        for (int64_t q = a0 + lane; q < a1; q += 32) {
+            const int32_t k = ld_i32(P.A.col + q);
+            s += ld_i64(P.B.rp + k + 1) - ld_i64(P.B.rp + k);
+        }
+        s = warp_sum(s);
+        if (lane == 0) {
+            ub[g] = s;
+            if (s == 0) cnt[g] = 0;
+            atomicAdd(&s_hist[bin_key(sym_tier(s, t), s)], 1);
+            prod += (unsigned long long)s;
+        }
+    }
+    if (lane == 0 && prod) atomicAdd(&ctr->products, prod);
+    __syncthreads();
+    for (int b = threadIdx.x; b < kNumBins; b += blockDim.x)
+        if (s_hist[b]) atomicAdd(&ctr->sym_bin_count[b], s_hist[b]);
+}
+
+// exclusive scan of the kNumBins bin counts (tiny: one thread)
+__global__ void k_bin_offsets(const int32_t* count, int32_t* off, int32_t* cursor) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int32_t s = 0;
+        for (int b = 0; b < kNumBins; ++b) {
+            off[b] = s;
+            cursor[b] = s;
+            s += count[b];
+        }
+        off[kNumBins] = s;
+    }
+}
+
+// rows[...] = flat rows ordered by bin key; per-block aggregation of the
+// global cursor atomics.
+template <class KeyFn>
+SPG_DEV void scatter_by_key(int64_t R, int32_t* cursor, int32_t* rows, KeyFn key_of) {
+    __shared__ int s_cnt[kNumBins];
+    __shared__ int s_base[kNumBins];
+    for (int b = threadIdx.x; b < kNumBins; b += blockDim.x) s_cnt[b] = 0;
+    __syncthreads();
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int key = -1, rank = 0;
+    if (g < R) {
+        key = key_of(g);
+        rank = atomicAdd(&s_cnt[key], 1);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < kNumBins; b += blockDim.x)
+        if (s_cnt[b]) s_base[b] = atomicAdd(&cursor[b], s_cnt[b]);
+    __syncthreads();
+    if (g < R) rows[s_base[key] + rank] = (int32_t)g;
+}
+
+__global__ void __launch_bounds__(1024) k_scatter_sym(int64_t R, Tuning t,
+                                                      const int64_t* __restrict__ ub,
+                                                      Counters* ctr, int32_t* rows) {
+    scatter_by_key(R, ctr->sym_bin_cursor, rows, [&](int64_t g) {
+        const int64_t u = ub[g];
+        return bin_key(sym_tier(u, t), u);
+    });
+}
+
+// ---- symbolic tiers ---------------------------------------------------------------
+
+struct KeyInsertOp {
+    int32_t* tab;
+    int shift;
+    uint32_t mask;
+    const int32_t* bcol;
+    DevStatus* st;
+    int64_t g;
+    int mine;
+    SPG_DEV void operator()(int64_t q, char, bool valid) {
+        if (!valid) return;
+        const int r = hash_insert(tab, shift, mask, ld_i32(bcol + q));
+        if (r > 0) ++mine;
+        else if (r < 0) flag_overflow(st, g);
+    }
+};
+
+__global__ void __launch_bounds__(kWarpTierWarps * 32)
+    k_sym_warp(const Prob* __restrict__ probs, int nprob, const int32_t* __restrict__ rows,
+               const Counters* __restrict__ ctr, const int64_t* __restrict__ ub,
+               int64_t* __restrict__ cnt, DevStatus* st, int per_warp_slots) {
+    extern __shared__ int32_t smem_i32[];
+    int32_t* tab = smem_i32 + (size_t)warp_id() * per_warp_slots;
+    const int lane = lane_id();
+    const int beg = ctr->sym_bin_off[kTierWarp * kSubBins];
+    const int end = ctr->sym_bin_off[(kTierWarp + 1) * kSubBins];
+    const int stride = gridDim.x * kWarpTierWarps;
+    const Slab single{0, 0, true, true, true, nullptr};
+    for (int r = beg + blockIdx.x * kWarpTierWarps + warp_id(); r < end; r += stride) {
+        const int64_t g = rows[r];
+        const Prob& P = probs[nprob == 1 ? 0 : find_prob(probs, nprob, g)];
+        const int64_t i = g - P.row_base;
+        const int64_t u = ub[g];
+        const int64_t distinct = u < P.B.ncols ? u : P.B.ncols;
+        int64_t T = dev_next_pow2(2 * distinct);
+        if (T < 32) T = 32;
+        if (T > per_warp_slots) {   // cannot happen with consistent tuning
+            if (lane == 0) flag_overflow(st, g);
+            continue;
+        }
+        for (int s = lane; s < T; s += 32) tab[s] = kEmptyKey;
+        __syncwarp();
+        KeyInsertOp op{tab, 32 - log2_exact(T), (uint32_t)(T - 1), P.B.col, st, g, 0};
+        const int64_t a0 = ld_i64(P.A.rp + i), a1 = ld_i64(P.A.rp + i + 1);
+        for (int64_t p0 = a0; p0 < a1; p0 += 32)
+            chunk_products<char, false>(P.A, P.B, p0, a1, 0, single, op);
+        const int tot = warp_sum(op.mine);
+        if (lane == 0) cnt[g] = tot;
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(kBlockThreads)
+    k_sym_block(const Prob* __restrict__ probs, int nprob, const int32_t* __restrict__ rows,
+                Counters* ctr, const int64_t* __restrict__ ub, int64_t* __restrict__ cnt,
+                DevStatus* st, int table_slots) {
+    extern __shared__ int32_t smem_i32[];
+    int32_t* tab = smem_i32;
+    __shared__ int s_row, s_next, s_cnt;
+    const int lane = lane_id();
+    const int beg = ctr->sym_bin_off[kTierBlock * kSubBins];
+    const int end = ctr->sym_bin_off[(kTierBlock + 1) * kSubBins];
+    const Slab single{0, 0, true, true, true, nullptr};
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_row = beg + atomicAdd(&ctr->claim[0], 1);
+            s_next = 0;
+            s_cnt = 0;
+        }
+        __syncthreads();
+        const int r = s_row;
+        if (r >= end) break;
+        const int64_t g = rows[r];
+        const Prob& P = probs[nprob == 1 ? 0 : find_prob(probs, nprob, g)];
+        const int64_t i = g - P.row_base;
+        const int64_t u = ub[g];
+        const int64_t distinct = u < P.B.ncols ? u : P.B.ncols;
+        int64_t T = dev_next_pow2(2 * distinct);
+        if (T < 32) T = 32;
+        if (T > table_slots) {
+            if (threadIdx.x == 0) flag_overflow(st, g);
+            __syncthreads();
+            continue;
+        }
+        for (int s = threadIdx.x; s < T; s += blockDim.x) tab[s] = kEmptyKey;
+        __syncthreads();
+        KeyInsertOp op{tab, 32 - log2_exact(T), (uint32_t)(T - 1), P.B.col, st, g, 0};
+        const int64_t a0 = ld_i64(P.A.rp + i), a1 = ld_i64(P.A.rp + i + 1);
+        for (;;) {
+            int c = 0;
+            if (lane == 0) c = atomicAdd(&s_next, 1);
+            c = __shfl_sync(kFull, c, 0);
+            const int64_t p0 = a0 + (int64_t)c * 32;
+            if (p0 >= a1) break;
+            chunk_products<char, false>(P.A, P.B, p0, a1, 0, single, op);
+        }
+        const int tot = warp_sum(op.mine);
+        if (lane == 0 && tot) atomicAdd(&s_cnt, tot);
+        __syncthreads();
+        if (threadIdx.x == 0) cnt[g] = s_cnt;
+        __syncthreads();
+    }
+}
+
+struct BitOrOp {
+    uint32_t* bm;
+    int32_t lo;
+    const int32_t* bcol;
+    SPG_DEV void operator()(int64_t q, char, bool valid) {
+        if (!valid) return;
+        const int32_t c = ld_i32(bcol + q) - lo;
+        atomicOr(bm + (c >> 5), 1u << (c & 31));
+    }
+};
+
+__global__ void __launch_bounds__(kBlockThreads)
+    k_sym_dense(const Prob* __restrict__ probs, int nprob, const int32_t* __restrict__ rows,
+                Counters* ctr, int64_t* __restrict__ cnt, int32_t* cursor, int slab_cols) {
+    extern __shared__ uint32_t smem_u32[];
+    uint32_t* bm = smem_u32;
+    __shared__ int s_row, s_next;
+    __shared__ unsigned long long s_tot;
+    const int lane = lane_id();
+    const int beg = ctr->sym_bin_off[kTierDense * kSubBins];
+    const int end = ctr->sym_bin_off[(kTierDense + 1) * kSubBins];
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_row = beg + atomicAdd(&ctr->claim[1], 1);
+            s_tot = 0;
+        }
+        __syncthreads();
+        const int r = s_row;
+        if (r >= end) break;
+        const int64_t g = rows[r];
+        const Prob& P = probs[nprob == 1 ? 0 : find_prob(probs, nprob, g)];
+        const int64_t i = g - P.row_base;
+        const int64_t a0 = ld_i64(P.A.rp + i), a1 = ld_i64(P.A.rp + i + 1);
+        const int64_t ncols = P.B.ncols;
+        const int nslabs = (int)((ncols + slab_cols - 1) / slab_cols);
+        for (int s = 0; s < nslabs; ++s) {
+            const int32_t lo = (int32_t)((int64_t)s * slab_cols);
+            const int64_t hi64 = (int64_t)lo + slab_cols < ncols ? (int64_t)lo + slab_cols : ncols;
+            const int32_t hi = (int32_t)hi64;
+            const int words = (hi - lo + 31) >> 5;
+            for (int w = threadIdx.x; w < words; w += blockDim.x) bm[w] = 0u;
+            if (threadIdx.x == 0) s_next = 0;
+            __syncthreads();
+            const Slab slab{lo, hi, s == 0, s == nslabs - 1, nslabs == 1, cursor};
+            BitOrOp op{bm, lo, P.B.col};
+            for (;;) {
+                int c = 0;
+                if (lane == 0) c = atomicAdd(&s_next, 1);
+                c = __shfl_sync(kFull, c, 0);
+                const int64_t p0 = a0 + (int64_t)c * 32;
+                if (p0 >= a1) break;
+                chunk_products<char, false>(P.A, P.B, p0, a1, P.nnz_base + p0, slab, op);
+            }
+            __syncthreads();
+            int mine = 0;
+            for (int w = threadIdx.x; w < words; w += blockDim.x) mine += __popc(bm[w]);
+            mine = warp_sum(mine);
+            if (lane == 0 && mine) atomicAdd(&s_tot, (unsigned long long)mine);
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) cnt[g] = (int64_t)s_tot;
+        __syncthreads();
+    }
+}
+
+// ---- scan of the flat counts into row pointers ------------------------------------
+
+constexpr int kScanThreads = 256, kScanItems = 8, kScanTile = kScanThreads * kScanItems;
+
+SPG_DEV int64_t block_excl_scan(int64_t v, int64_t* total) {
+    __shared__ int64_t s_w[kScanThreads / 32];
+    const int lane = lane_id(), w = warp_id();
+    int64_t incl = warp_incl_scan(v);
+    if (lane == 31) s_w[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int64_t x = lane < kScanThreads / 32 ? s_w[lane] : 0;
+        int64_t xi = warp_incl_scan(x);
+        if (lane < kScanThreads / 32) s_w[lane] = xi - x;
+        if (lane == kScanThreads / 32 - 1) *total = xi;
+    }
+    __syncthreads();
+    const int64_t r = s_w[w] + incl - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int64_t* cnt, int64_t R,
+                                                              int64_t* part) {
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    int64_t s = 0;
+    for (int t = 0; t < kScanItems; ++t) {
+        const int64_t g = base + (int64_t)t * kScanThreads + threadIdx.x;
+        if (g < R) s += cnt[g];
+    }
+    __shared__ int64_t tot;
+    block_excl_scan(s, &tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_parts(int64_t* part, int64_t nparts) {
+    __shared__ int64_t tot;
+    int64_t carry = 0;
+    for (int64_t base = 0; base < nparts; base += kScanThreads) {
+        const int64_t idx = base + threadIdx.x;
+        const int64_t v = idx < nparts ? part[idx] : 0;
+        const int64_t ex = block_excl_scan(v, &tot);
+        if (idx < nparts) part[idx] = carry + ex;
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[nparts] = carry;
+}
+
+// in-place exclusive scan of cnt[0, R) using per-tile offsets; cnt[R] = total
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(int64_t* cnt, int64_t R,
+                                                             const int64_t* part, int64_t nparts) {
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t v[kScanItems];
+    int64_t s = 0;
+    for (int t = 0; t < kScanItems; ++t) {
+        const int64_t g = base + t;
+        v[t] = g < R ? cnt[g] : 0;
+        s += v[t];
+    }
+    __shared__ int64_t tot;
+    int64_t run = block_excl_scan(s, &tot) + part[blockIdx.x];
+    for (int t = 0; t < kScanItems; ++t) {
+        const int64_t g = base + t;
+        if (g < R) cnt[g] = run;
+        run += v[t];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) cnt[R] = part[nparts];
+}
+
+__global__ void k_write_rowptr(const Prob* __restrict__ probs, const int64_t* __restrict__ cnt,
+                               Counters* ctr) {
+    const Prob& P = probs[blockIdx.y];
+    const int64_t n = P.A.nrows;
+    const int64_t b = cnt[P.row_base];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        P.c_rp[i] = cnt[P.row_base + i] - b;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctr->nnz[blockIdx.y] = cnt[P.row_base + n] - b;
+}
+
+// ---- CSR validity check -----------------------------------------------------------
+
+__global__ void k_validate(DCsr M, int64_t nnz, DevStatus* st) {
+    const int lane = lane_id();
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (M.rp[0] != 0 || M.rp[M.nrows] != nnz) atomicExch(&st->invalid, 1);
+    }
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); i < M.nrows; i += nw) {
+        const int64_t a = M.rp[i], b = M.rp[i + 1];
+        bool bad = b < a;
+        if (!bad) {
+            for (int64_t q = a + lane; q < b; q += 32) {
+                const int32_t c = M.col[q];
+                if (c < 0 || c >= M.ncols) bad = true;
+                if (q > a && M.col[q - 1] >= c) bad = true;
+            }
+        }
+        bad = __any_sync(kFull, bad);
+        if (bad && lane == 0 && atomicExch(&st->invalid, 1) == 0) st->info[1] = i;
+    }
+}
+
+// ---- launchers -------------------------------------------------------------------
+
+cudaError_t launch_write_probs(const ProbTable& tab, int nprob, const WsPtrs& w, cudaStream_t st) {
+    k_write_probs<<<1, kMaxProb, 0, st>>>(tab, nprob, w.probs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_analyze(const WsPtrs& w, int nprob, int64_t R, const Tuning& t,
+                           cudaStream_t st) {
+    if (R > 0) {
+        int64_t blocks = (R + 7) / 8;
+        if (blocks > 152 * 16) blocks = 152 * 16;
+        k_analyze<<<(unsigned)blocks, 256, 0, st>>>(w.probs, nprob, R, t, w.ub, w.cnt, w.ctr);
+    }
+    k_bin_offsets<<<1, 32, 0, st>>>(w.ctr->sym_bin_count, w.ctr->sym_bin_off,
+                                    w.ctr->sym_bin_cursor);
+    if (R > 0)
+        k_scatter_sym<<<(unsigned)((R + 1023) / 1024), 1024, 0, st>>>(R, t, w.ub, w.ctr,
+                                                                       w.rows_sym);
+    return cudaGetLastError();
+}
+
+size_t sym_warp_smem_per_warp(const Tuning& t) {
+    int64_t T = next_pow2(2 * t.sym_warp_max_ub);
+    if (T < 32) T = 32;
+    return (size_t)T * sizeof(int32_t);
+}
+
+static int occupancy(const void* fn, int threads, size_t smem, const DevInfo& dev) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
+    if (per_sm < 1) per_sm = 1;
+    return per_sm * dev.sms;
+}
+
+cudaError_t launch_symbolic(const WsPtrs& w, int nprob, int64_t R, const Tuning& t,
+                            int64_t max_ncols, const DevInfo& dev, cudaStream_t st) {
+    if (R == 0) return cudaSuccess;
+    cudaError_t e;
+    // dense tier first: it holds the heaviest rows
+    {
+        int64_t slab = t.sym_slab_cols;
+        if (slab > max_ncols) slab = (max_ncols + 1023) / 1024 * 1024;
+        if (slab < 1024) slab = 1024;
+        const size_t smem = (size_t)slab / 8;
+        e = cudaFuncSetAttribute(k_sym_dense, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        const int grid = occupancy((const void*)k_sym_dense, kBlockThreads, smem, dev);
+        k_sym_dense<<<grid, kBlockThreads, smem, st>>>(w.probs, nprob, w.rows_sym, w.ctr, w.cnt,
+                                                       w.cursor, (int)slab);
+    }
+    {
+        int64_t T = next_pow2(2 * t.sym_block_max_ub);
+        if (T < 32) T = 32;
+        const size_t smem = (size_t)T * sizeof(int32_t);
+        e = cudaFuncSetAttribute(k_sym_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        const int grid = occupancy((const void*)k_sym_block, kBlockThreads, smem, dev);
+        k_sym_block<<<grid, kBlockThreads, smem, st>>>(w.probs, nprob, w.rows_sym, w.ctr, w.ub,
+                                                       w.cnt, w.status, (int)T);
+    }
+    {
+        const size_t per_warp = sym_warp_smem_per_warp(t);
+        const size_t smem = per_warp * kWarpTierWarps;
+        e = cudaFuncSetAttribute(k_sym_warp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        const int grid = occupancy((const void*)k_sym_warp, kWarpTierWarps * 32, smem, dev);
+        k_sym_warp<<<grid, kWarpTierWarps * 32, smem, st>>>(
+            w.probs, nprob, w.rows_sym, w.ctr, w.ub, w.cnt, w.status,
+            (int)(per_warp / sizeof(int32_t)));
+    }
+    return cudaGetLastError();
+}
+
+int64_t scan_parts_needed(int64_t R) { return (R + kScanTile - 1) / kScanTile + 1; }
+
+cudaError_t launch_scan_inplace(int64_t* cnt, int64_t R, int64_t* part, cudaStream_t st) {
+    const int64_t nparts = (R + kScanTile - 1) / kScanTile;
+    if (R > 0) {
+        k_scan_reduce<<<(unsigned)nparts, kScanThreads, 0, st>>>(cnt, R, part);
+        k_scan_parts<<<1, kScanThreads, 0, st>>>(part, nparts);
+        k_scan_apply<<<(unsigned)nparts, kScanThreads, 0, st>>>(cnt, R, part, nparts);
+    } else {
+        cudaMemsetAsync(cnt, 0, sizeof(int64_t), st);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_rowptr(const WsPtrs& w, int nprob, int64_t R, cudaStream_t st) {
+    cudaError_t e = launch_scan_inplace(w.cnt, R, w.scan_part, st);
+    if (e != cudaSuccess) return e;
+    k_write_rowptr<<<dim3(64, nprob), 256, 0, st>>>(w.probs, w.cnt, w.ctr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate(const DCsr& M, int64_t nnz, DevStatus* status, cudaStream_t st) {
+    int64_t blocks = (M.nrows + 7) / 8;
+    if (blocks < 1) blocks = 1;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_validate<<<(unsigned)blocks, 256, 0, st>>>(M, nnz, status);
+    return cudaGetLastError();
+}
+
+}  // namespace spg

@@ -1,0 +1,267 @@
+"""Python binding of the C ABI in include/spgemm.h (argument marshalling only).
+
+Every step of the multiplication runs in the CUDA library
+``_build/libspgemm.so``; this module passes device pointers (from torch CUDA
+tensors), sizes and the current CUDA stream.  There is no CPU fallback: if the
+library is missing or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libspgemm.so")
+
+# semiring ids (spg_semiring)
+PLUS_TIMES_F64, BOOL_OR_AND, MIN_PLUS_F32, OVERLAP_I32, PLUS_TIMES_I64, PLUS_TIMES_F32 = range(6)
+SEMIRING_NAMES = {PLUS_TIMES_F64: "plus_times_f64", BOOL_OR_AND: "bool_or_and",
+                  MIN_PLUS_F32: "min_plus_f32", OVERLAP_I32: "overlap_i32",
+                  PLUS_TIMES_I64: "plus_times_i64", PLUS_TIMES_F32: "plus_times_f32"}
+IN_NP = {PLUS_TIMES_F64: np.float64, BOOL_OR_AND: None, MIN_PLUS_F32: np.float32,
+         OVERLAP_I32: np.int32, PLUS_TIMES_I64: np.int64, PLUS_TIMES_F32: np.float32}
+OVERLAP_NP = np.dtype([("count", np.int32), ("a0", np.int32), ("b0", np.int32),
+                       ("a1", np.int32), ("b1", np.int32)])
+OUT_BYTES = {PLUS_TIMES_F64: 8, BOOL_OR_AND: 0, MIN_PLUS_F32: 4, OVERLAP_I32: 20,
+             PLUS_TIMES_I64: 8, PLUS_TIMES_F32: 4}
+
+STATUS = {0: "SPG_OK", 1: "SPG_ERR_INVALID_ARG", 2: "SPG_ERR_INVALID_CSR", 3: "SPG_ERR_OOM",
+          4: "SPG_ERR_CUDA", 5: "SPG_ERR_UNSUPPORTED", 6: "SPG_ERR_OVERFLOW",
+          7: "SPG_ERR_TIMEOUT", 8: "SPG_ERR_WORKSPACE"}
+
+
+class SpgemmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class spg_csr(ctypes.Structure):
+    _fields_ = [("nrows", ctypes.c_int64), ("ncols", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class spg_tuning(ctypes.Structure):
+    _fields_ = [("sym_warp_max_ub", ctypes.c_int64), ("sym_block_max_ub", ctypes.c_int64),
+                ("num_warp_max_nnz", ctypes.c_int64), ("num_block_max_nnz", ctypes.c_int64),
+                ("dense_slab_cols", ctypes.c_int64), ("sym_slab_cols", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 4)]
+
+
+class spg_stats(ctypes.Structure):
+    _fields_ = [("products", ctypes.c_int64), ("nnz_c", ctypes.c_int64),
+                ("rows_per_tier", ctypes.c_int64 * 4), ("reserved", ctypes.c_int64 * 6)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_CSR = ctypes.POINTER(spg_csr)
+
+
+def load_library(path: str = LIB_PATH):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    sig = {
+        "spgemm_create": [ctypes.POINTER(_P)],
+        "spgemm_destroy": [_P],
+        "spgemm_set_tuning": [_P, ctypes.POINTER(spg_tuning)],
+        "spgemm_get_tuning": [_P, ctypes.POINTER(spg_tuning)],
+        "spgemm_get_stats": [_P, ctypes.POINTER(spg_stats)],
+        "spgemm_workspace_size": [_P, ctypes.c_int, _CSR, _CSR, ctypes.POINTER(ctypes.c_size_t)],
+        "spgemm_symbolic": [_P, ctypes.c_int, _CSR, _CSR, _P, ctypes.POINTER(_I64), _P,
+                            ctypes.c_size_t, _P],
+        "spgemm_numeric": [_P, ctypes.c_int, _CSR, _CSR, _P, _P, _P, _P, ctypes.c_size_t, _P],
+        "spgemm_check": [_P, _P, _P],
+        "spgemm_validate_csr": [_P, _CSR, _P, ctypes.c_size_t, _P],
+        "spgemm_transpose_workspace_size": [_P, _CSR, ctypes.POINTER(ctypes.c_size_t)],
+        "spgemm_transpose": [_P, _CSR, ctypes.c_int, _P, _P, _P, _P, ctypes.c_size_t, _P],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.spgemm_last_error.argtypes = [_P]
+    lib.spgemm_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def exported_symbols() -> list[str]:
+    return ["spgemm_create", "spgemm_destroy", "spgemm_last_error", "spgemm_set_tuning",
+            "spgemm_get_tuning", "spgemm_get_stats", "spgemm_workspace_size", "spgemm_symbolic",
+            "spgemm_numeric", "spgemm_check", "spgemm_validate_csr",
+            "spgemm_transpose_workspace_size", "spgemm_transpose"]
+
+
+@dataclass
+class DeviceCSR:
+    """CSR matrix in device memory (torch CUDA tensors): int64 rp, int32 col."""
+    nrows: int
+    ncols: int
+    rp: "object"
+    col: "object"
+    val: "Optional[object]" = None
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col.numel())
+
+    def c(self) -> spg_csr:
+        return spg_csr(self.nrows, self.ncols, self.nnz, self.rp.data_ptr(),
+                       self.col.data_ptr() if self.col.numel() else None,
+                       None if self.val is None or self.val.numel() == 0 else self.val.data_ptr())
+
+    @staticmethod
+    def from_host(M, device="cuda", val_dtype=None) -> "DeviceCSR":
+        import torch
+        rp = torch.from_numpy(np.ascontiguousarray(M.rp, dtype=np.int64)).to(device)
+        col = torch.from_numpy(np.ascontiguousarray(M.col, dtype=np.int32)).to(device)
+        val = None
+        if M.val is not None and val_dtype is not None:
+            val = torch.from_numpy(np.ascontiguousarray(M.val, dtype=val_dtype)).to(device)
+        return DeviceCSR(int(M.nrows), int(M.ncols), rp, col, val)
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Handle:
+    """spg_handle wrapper; one per thread, reusable across calls."""
+
+    def __init__(self, tuning: Optional[dict] = None):
+        self.lib = load_library()
+        self._h = ctypes.c_void_p()
+        self._ok(self.lib.spgemm_create(ctypes.byref(self._h)))
+        if tuning:
+            self.set_tuning(**tuning)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and self.lib is not None:
+            self.lib.spgemm_destroy(h)
+            self._h = None
+
+    def _ok(self, st: int):
+        if st != 0:
+            msg = self.lib.spgemm_last_error(self._h).decode() if getattr(self, "_h", None) else ""
+            raise SpgemmError(st, msg)
+
+    def set_tuning(self, **kw):
+        t = spg_tuning()
+        for k, v in kw.items():
+            setattr(t, k, int(v))
+        self._ok(self.lib.spgemm_set_tuning(self._h, ctypes.byref(t)))
+
+    def stats(self) -> dict:
+        s = spg_stats()
+        self._ok(self.lib.spgemm_get_stats(self._h, ctypes.byref(s)))
+        return {"products": s.products, "nnz_c": s.nnz_c,
+                "rows_per_tier": list(s.rows_per_tier)}
+
+    def workspace_size(self, sr: int, A: DeviceCSR, B: DeviceCSR) -> int:
+        n = ctypes.c_size_t()
+        a, b = A.c(), B.c()
+        self._ok(self.lib.spgemm_workspace_size(self._h, sr, ctypes.byref(a), ctypes.byref(b),
+                                                ctypes.byref(n)))
+        return n.value
+
+    def symbolic(self, sr, A: DeviceCSR, B: DeviceCSR, c_rp, ws, stream=None) -> int:
+        nnz = ctypes.c_int64()
+        a, b = A.c(), B.c()
+        self._ok(self.lib.spgemm_symbolic(self._h, sr, ctypes.byref(a), ctypes.byref(b),
+                                          c_rp.data_ptr(), ctypes.byref(nnz), ws.data_ptr(),
+                                          ws.numel(), _stream_ptr(stream)))
+        return nnz.value
+
+    def numeric(self, sr, A: DeviceCSR, B: DeviceCSR, c_rp, c_col, c_val, ws, stream=None):
+        a, b = A.c(), B.c()
+        self._ok(self.lib.spgemm_numeric(
+            self._h, sr, ctypes.byref(a), ctypes.byref(b), c_rp.data_ptr(),
+            c_col.data_ptr() if c_col.numel() else None,
+            None if c_val is None or c_val.numel() == 0 else c_val.data_ptr(),
+            ws.data_ptr(), ws.numel(), _stream_ptr(stream)))
+
+    def check(self, ws, stream=None):
+        self._ok(self.lib.spgemm_check(self._h, ws.data_ptr(), _stream_ptr(stream)))
+
+    def transpose(self, A: DeviceCSR, value_bytes: int, stream=None) -> DeviceCSR:
+        """A^T on the GPU (values carried as raw bytes of the given width)."""
+        import torch
+        a = A.c()
+        n = ctypes.c_size_t()
+        self._ok(self.lib.spgemm_transpose_workspace_size(self._h, ctypes.byref(a),
+                                                          ctypes.byref(n)))
+        dev = A.rp.device
+        ws = torch.empty(max(n.value, 1), dtype=torch.uint8, device=dev)
+        t_rp = torch.empty(A.ncols + 1, dtype=torch.int64, device=dev)
+        t_col = torch.empty(A.nnz, dtype=torch.int32, device=dev)
+        t_val = None
+        if value_bytes:
+            t_val = torch.empty(A.nnz * value_bytes, dtype=torch.uint8, device=dev)
+            if A.val is not None:
+                t_val = t_val.view(A.val.dtype).reshape((-1,) + tuple(A.val.shape[1:]))
+        self._ok(self.lib.spgemm_transpose(
+            self._h, ctypes.byref(a), value_bytes, t_rp.data_ptr(),
+            t_col.data_ptr() if A.nnz else None,
+            t_val.data_ptr() if t_val is not None and A.nnz else None,
+            ws.data_ptr(), ws.numel(), _stream_ptr(stream)))
+        return DeviceCSR(A.ncols, A.nrows, t_rp, t_col, t_val)
+
+    def validate(self, M: DeviceCSR, ws, stream=None):
+        m = M.c()
+        self._ok(self.lib.spgemm_validate_csr(self._h, ctypes.byref(m), ws.data_ptr(),
+                                              ws.numel(), _stream_ptr(stream)))
+
+
+def out_tensor(sr: int, nnz: int, device="cuda"):
+    import torch
+    if sr == BOOL_OR_AND:
+        return None
+    if sr == OVERLAP_I32:
+        return torch.empty((nnz, 5), dtype=torch.int32, device=device)
+    dt = {PLUS_TIMES_F64: torch.float64, MIN_PLUS_F32: torch.float32,
+          PLUS_TIMES_I64: torch.int64, PLUS_TIMES_F32: torch.float32}[sr]
+    return torch.empty(nnz, dtype=dt, device=device)
+
+
+def spgemm(sr: int, A: DeviceCSR, B: DeviceCSR, handle: Optional[Handle] = None,
+           ws=None, check: bool = True) -> DeviceCSR:
+    """C = A (x).(+) B on the GPU (symbolic, allocation of C, numeric)."""
+    import torch
+    h = handle or Handle()
+    dev = A.rp.device
+    if ws is None:
+        ws = torch.empty(h.workspace_size(sr, A, B), dtype=torch.uint8, device=dev)
+    c_rp = torch.empty(A.nrows + 1, dtype=torch.int64, device=dev)
+    nnz = h.symbolic(sr, A, B, c_rp, ws)
+    c_col = torch.empty(nnz, dtype=torch.int32, device=dev)
+    c_val = out_tensor(sr, nnz, dev)
+    h.numeric(sr, A, B, c_rp, c_col, c_val, ws)
+    if check:
+        h.check(ws)
+    return DeviceCSR(A.nrows, B.ncols, c_rp, c_col, c_val)
+
+
+def to_host(C: DeviceCSR, sr: int):
+    """Copy a device result to numpy (rp, col, val) with the semiring's dtypes."""
+    from types import SimpleNamespace
+    rp = C.rp.cpu().numpy()
+    col = C.col.cpu().numpy()
+    val = None
+    if C.val is not None:
+        v = C.val.cpu().numpy()
+        val = v.view(OVERLAP_NP).reshape(-1) if sr == OVERLAP_I32 else v
+    return SimpleNamespace(nrows=C.nrows, ncols=C.ncols, rp=rp, col=col, val=val, nnz=col.size)
