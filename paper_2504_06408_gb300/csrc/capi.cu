@@ -27,7 +27,20 @@ namespace spg {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-WsLayout ws_layout(int64_t R, int64_t E) {
+// Slab-start table of B for the numeric dense tier: (nrows_b + 1) x (slabs + 1)
+// int32, kept only while it is no larger than twice B's column array (plus
+// 64 MB); otherwise the dense tier advances per-entry cursors instead.
+static size_t slab_ptr_table_bytes(int64_t nrows_b, int64_t ncols_b, int64_t nnz_b,
+                                   int64_t slab_cols) {
+    if (slab_cols <= 0 || ncols_b <= slab_cols) return 0;
+    const int64_t nslabs = (ncols_b + slab_cols - 1) / slab_cols;
+    const size_t need = (size_t)(nrows_b + 1) * (size_t)(nslabs + 1) * 4;
+    const size_t cap = (size_t)nnz_b * 8 + ((size_t)64 << 20);
+    return need <= cap ? need : 0;
+}
+
+WsLayout ws_layout(int64_t R, int64_t E, int64_t nrows_b, int64_t ncols_b, int64_t nnz_b,
+                   int64_t slab_cols) {
     WsLayout L{};
     L.R = R;
     L.E = E;
@@ -42,6 +55,8 @@ WsLayout ws_layout(int64_t R, int64_t E) {
     const int64_t nparts = (R + 2047) / 2048;
     L.scan_part = o; o = align256(o + sizeof(int64_t) * (size_t)(nparts + 1));
     L.cursor = o;    o = align256(o + sizeof(int32_t) * (size_t)E);
+    L.slab_ptr_bytes = slab_ptr_table_bytes(nrows_b, ncols_b, nnz_b, slab_cols);
+    L.slab_ptr = o;  o = align256(o + L.slab_ptr_bytes);
     L.total = o;
     return L;
 }
@@ -58,6 +73,8 @@ WsPtrs ws_ptrs(void* ws, const WsLayout& L) {
     w.rows_num = (int32_t*)(b + L.rows_num);
     w.scan_part = (int64_t*)(b + L.scan_part);
     w.cursor = (int32_t*)(b + L.cursor);
+    w.slab_ptr = L.slab_ptr_bytes ? (int32_t*)(b + L.slab_ptr) : nullptr;
+    w.slab_ptr_bytes = L.slab_ptr_bytes;
     return w;
 }
 
@@ -110,8 +127,6 @@ Tuning clamp_tuning(Tuning t, int sr) {
     if (t.dense_slab_cols > 65536 * 16) t.dense_slab_cols = 65536 * 16;
     while (num_dense_smem(sr, t.dense_slab_cols) > kSmemBudget && t.dense_slab_cols > 1024)
         t.dense_slab_cols -= 1024;
-    // the dense epilogue scans at most 64 chunks of 1024 columns
-    if (t.dense_slab_cols > 65536) t.dense_slab_cols = 65536;
     return t;
 }
 
@@ -237,7 +252,8 @@ spg_status spgemm_workspace_size(spg_handle* h, spg_semiring sr, const spg_csr* 
     spg_status s = check_pair(h, sr, A, B, false);
     if (s != SPG_OK) return s;
     if (!bytes) return fail(h, SPG_ERR_INVALID_ARG, "bytes is NULL");
-    *bytes = ws_layout(A->nrows, A->nnz).total;
+    const Tuning t = effective_tuning(h, sr);
+    *bytes = ws_layout(A->nrows, A->nnz, B->nrows, B->ncols, B->nnz, t.dense_slab_cols).total;
     return SPG_OK;
 }
 
@@ -261,12 +277,12 @@ spg_status spgemm_symbolic(spg_handle* h, spg_semiring sr, const spg_csr* A, con
     spg_status s = check_pair(h, sr, A, B, false);
     if (s != SPG_OK) return s;
     if (!c_row_ptr || !c_nnz) return fail(h, SPG_ERR_INVALID_ARG, "c_row_ptr / c_nnz is NULL");
-    const WsLayout L = ws_layout(A->nrows, A->nnz);
+    const Tuning t = effective_tuning(h, sr);
+    const WsLayout L = ws_layout(A->nrows, A->nnz, B->nrows, B->ncols, B->nnz, t.dense_slab_cols);
     if (!workspace || workspace_bytes < L.total)
         return fail(h, SPG_ERR_WORKSPACE, "workspace needs %zu bytes", L.total);
     cudaStream_t st = (cudaStream_t)stream;
     const WsPtrs w = ws_ptrs(workspace, L);
-    const Tuning t = effective_tuning(h, sr);
     cudaError_t e = cudaMemsetAsync(workspace, 0, L.probs, st);   // status + counters
     if (e != cudaSuccess) return cuda_fail(h, e, "memset");
     ProbTable* tab = new ProbTable;
@@ -301,18 +317,19 @@ spg_status spgemm_numeric(spg_handle* h, spg_semiring sr, const spg_csr* A, cons
     spg_status s = check_pair(h, sr, A, B, true);
     if (s != SPG_OK) return s;
     if (!c_row_ptr) return fail(h, SPG_ERR_INVALID_ARG, "c_row_ptr is NULL");
-    const WsLayout L = ws_layout(A->nrows, A->nnz);
+    const Tuning t = effective_tuning(h, sr);
+    const WsLayout L = ws_layout(A->nrows, A->nnz, B->nrows, B->ncols, B->nnz, t.dense_slab_cols);
     if (!workspace || workspace_bytes < L.total)
         return fail(h, SPG_ERR_WORKSPACE, "workspace needs %zu bytes", L.total);
     cudaStream_t st = (cudaStream_t)stream;
     const WsPtrs w = ws_ptrs(workspace, L);
-    const Tuning t = effective_tuning(h, sr);
     ProbTable* tab = new ProbTable;
     std::memset(tab, 0, sizeof *tab);
     tab->p[0] = Prob{to_dcsr(A), to_dcsr(B), const_cast<int64_t*>(c_row_ptr), c_col, c_val, 0, 0};
     cudaError_t e = launch_write_probs(*tab, 1, w, st);
     delete tab;
-    if (e == cudaSuccess) e = launch_numeric(sr, w, 1, A->nrows, t, B->ncols, h->dev, st);
+    if (e == cudaSuccess)
+        e = launch_numeric(sr, w, to_dcsr(B), 1, A->nrows, t, B->ncols, h->dev, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "numeric launch");
     return SPG_OK;
 }

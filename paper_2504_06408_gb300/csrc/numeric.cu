@@ -100,33 +100,44 @@ struct HashAccOp {
     typename S::Slot* vals;
     int shift;
     uint32_t mask;
-    const int32_t* bcol;
-    const typename S::In* bval;
     DevStatus* st;
     int64_t g;
-    SPG_DEV void operator()(int64_t q, typename S::In a, bool valid) {
+    SPG_DEV void any(int32_t col, typename S::In a, typename S::In b, bool valid) {
         if (!valid) return;
-        const int s = hash_slot_of(keys, shift, mask, ld_i32(bcol + q));
+        const int s = hash_slot_of(keys, shift, mask, col);
         if (s < 0) {
             flag_overflow(st, g);
             return;
         }
-        if constexpr (S::kVal) S::acc(vals + s, a, __ldg(bval + q));
+        if constexpr (S::kVal) S::acc(vals + s, a, b);
+    }
+    SPG_DEV void sorted(int32_t col, typename S::In a, typename S::In b, bool valid) {
+        any(col, a, b, valid);
     }
 };
 
+// Dense slab accumulator.  The presence bitmap is kept for every semiring:
+// semirings whose Slot cannot mark presence set the bit on every product
+// (after a read, so repeated columns cost no atomic); the others set it only
+// on a column's first product, which their Slot reveals.
 template <class S>
 struct DenseAccOp {
     typename S::Slot* vals;
     uint32_t* bm;
     int32_t lo;
-    const int32_t* bcol;
-    const typename S::In* bval;
-    SPG_DEV void operator()(int64_t q, typename S::In a, bool valid) {
+    SPG_DEV void any(int32_t col, typename S::In a, typename S::In b, bool valid) {
         if (!valid) return;
-        const int32_t c = ld_i32(bcol + q) - lo;
-        if constexpr (S::kBitmap) atomicOr(bm + (c >> 5), 1u << (c & 31));
-        if constexpr (S::kVal) S::acc(vals + c, a, __ldg(bval + q));
+        const int32_t c = col - lo;
+        const uint32_t bit = 1u << (c & 31);
+        if constexpr (S::kBitmap) {
+            if (!(bm[c >> 5] & bit)) atomicOr(bm + (c >> 5), bit);
+            if constexpr (S::kVal) S::acc(vals + c, a, b);
+        } else {
+            if (S::acc_first(vals + c, a, b)) atomicOr(bm + (c >> 5), bit);
+        }
+    }
+    SPG_DEV void sorted(int32_t col, typename S::In a, typename S::In b, bool valid) {
+        any(col, a, b, valid);
     }
 };
 
@@ -160,7 +171,7 @@ __global__ void __launch_bounds__(kWarpTierWarps * 32)
     const int beg = ctr->num_bin_off[kTierWarp * kSubBins];
     const int end = ctr->num_bin_off[(kTierWarp + 1) * kSubBins];
     const int stride = gridDim.x * kWarpTierWarps;
-    const Slab single{0, 0, true, true, true, nullptr};
+    const Slab single{0, 0, true, true, true, nullptr, nullptr, 0, 0};
     for (int r = beg + blockIdx.x * kWarpTierWarps + warp_id(); r < end; r += stride) {
         const int64_t g = rows[r];
         const Prob& P = probs[nprob == 1 ? 0 : find_prob(probs, nprob, g)];
@@ -179,8 +190,7 @@ __global__ void __launch_bounds__(kWarpTierWarps * 32)
         }
         __syncwarp();
         const int shift = 32 - log2_exact(T);
-        HashAccOp<S> op{keys, vals, shift, (uint32_t)(T - 1), P.B.col,
-                        reinterpret_cast<const In*>(P.B.val), st, g};
+        HashAccOp<S> op{keys, vals, shift, (uint32_t)(T - 1), st, g};
         const int64_t a0 = ld_i64(P.A.rp + i), a1 = ld_i64(P.A.rp + i + 1);
         for (int64_t p0 = a0; p0 < a1; p0 += 32)
             chunk_products<In, S::kVal>(P.A, P.B, p0, a1, 0, single, op);
@@ -233,15 +243,15 @@ __global__ void __launch_bounds__(kBlockThreads)
     Slot* vals = reinterpret_cast<Slot*>(smem_raw);
     int32_t* keys = reinterpret_cast<int32_t*>(smem_raw + (size_t)Tb * sizeof(Slot));
     int32_t* sbuf = keys + Tb;
-    __shared__ int s_row, s_next, s_m;
+    __shared__ BatchSmem<In> bs;
+    __shared__ int s_row, s_m;
     const int lane = lane_id();
     const int beg = ctr->num_bin_off[kTierBlock * kSubBins];
     const int end = ctr->num_bin_off[(kTierBlock + 1) * kSubBins];
-    const Slab single{0, 0, true, true, true, nullptr};
+    const Slab single{0, 0, true, true, true, nullptr, nullptr, 0, 0};
     for (;;) {
         if (threadIdx.x == 0) {
             s_row = beg + atomicAdd(&ctr->claim[2], 1);
-            s_next = 0;
             s_m = 0;
         }
         __syncthreads();
@@ -265,18 +275,9 @@ __global__ void __launch_bounds__(kBlockThreads)
         }
         __syncthreads();
         const int shift = 32 - log2_exact(T);
-        HashAccOp<S> op{keys, vals, shift, (uint32_t)(T - 1), P.B.col,
-                        reinterpret_cast<const In*>(P.B.val), st, g};
+        HashAccOp<S> op{keys, vals, shift, (uint32_t)(T - 1), st, g};
         const int64_t a0 = ld_i64(P.A.rp + i), a1 = ld_i64(P.A.rp + i + 1);
-        for (;;) {
-            int c = 0;
-            if (lane == 0) c = atomicAdd(&s_next, 1);
-            c = __shfl_sync(kFull, c, 0);
-            const int64_t p0 = a0 + (int64_t)c * 32;
-            if (p0 >= a1) break;
-            chunk_products<In, S::kVal>(P.A, P.B, p0, a1, 0, single, op);
-        }
-        __syncthreads();
+        cta_row_products<In, S::kVal>(P.A, P.B, a0, a1, 0, single, bs, op);
         // compact occupied keys (order irrelevant: sorted next)
         for (int s0 = warp_id() * 32; s0 < T; s0 += blockDim.x) {
             const int32_t k = keys[s0 + lane];
@@ -309,29 +310,112 @@ __global__ void __launch_bounds__(kBlockThreads)
 
 // ---- dense tier -----------------------------------------------------------------
 
+// vals[0, width) = S::empty(), 16-byte stores where the slot size allows
+template <class S>
+SPG_DEV void fill_slots(typename S::Slot* vals, int width) {
+    using Slot = typename S::Slot;
+    if constexpr (sizeof(Slot) == 4 || sizeof(Slot) == 8) {
+        constexpr int per = 16 / (int)sizeof(Slot);
+        Slot e[per];
+#pragma unroll
+        for (int u = 0; u < per; ++u) e[u] = S::empty();
+        const uint4 v = *reinterpret_cast<const uint4*>(e);
+        uint4* v4 = reinterpret_cast<uint4*>(vals);
+        const int n4 = width / per;
+        for (int c = threadIdx.x; c < n4; c += blockDim.x) v4[c] = v;
+        for (int c = n4 * per + threadIdx.x; c < width; c += blockDim.x) vals[c] = S::empty();
+    } else {
+        for (int c = threadIdx.x; c < width; c += blockDim.x) vals[c] = S::empty();
+    }
+}
+
 template <class S>
 __host__ __device__ inline size_t dense_val_bytes(int64_t slab_cols) {
     return S::kVal ? (size_t)slab_cols * sizeof(typename S::Slot) : 0;
 }
 
+// Segment tables of one group of up to 16 slabs for a row with at most 32 A
+// entries: warp w fills slab (group * 16 + w); lane e = entry e.
+template <class In>
+struct SmallRowSmem {
+    int64_t beg[16][32];   // segment start of entry e in the slab
+    int32_t end[16][32];   // inclusive prefix of segment lengths (products of entries <= e)
+    In a[32];
+};
+
+// Products of one slab of a row with <= 32 entries, split evenly over the
+// warps.  Lane e keeps entry e's segment start and prefix end; a 32-product
+// window inside one segment is addressed directly, a window that crosses
+// segment ends finds each lane's entry by a 5-step search over the prefixes.
+template <class S, class Op>
+SPG_DEV void small_row_slab_products(const DCsr& B, const SmallRowSmem<typename S::In>& sr,
+                                     int sl, Op& op) {
+    using In = typename S::In;
+    const int lane = lane_id(), wid = warp_id();
+    const int nwarps = blockDim.x >> 5;
+    const int64_t my_beg = sr.beg[sl][lane];
+    const int my_end = sr.end[sl][lane];
+    In my_a = In();
+    if constexpr (S::kVal) my_a = sr.a[lane];
+    const int total = __shfl_sync(kFull, my_end, 31);
+    const int lo_w = (int)((int64_t)total * wid / nwarps);
+    const int hi_w = (int)((int64_t)total * (wid + 1) / nwarps);
+    const int up = __shfl_up_sync(kFull, my_end, 1);
+    const int excl = lane ? up : 0;   // products of entries < lane
+    for (int t0 = lo_w; t0 < hi_w; t0 += 128) {   // warp-uniform
+        int64_t qv[4];
+        In av[4];
+        bool vv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int t = t0 + 32 * u + lane;
+            vv[u] = t < hi_w;
+            int k = 0;   // entry of product t: number of prefix ends <= t
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int bv = __shfl_sync(kFull, my_end, k + step - 1);
+                if (bv <= t) k += step;
+            }
+            const int64_t b = __shfl_sync(kFull, my_beg, k);
+            const int ex = __shfl_sync(kFull, excl, k);
+            qv[u] = b + (t - ex);
+            if constexpr (S::kVal) av[u] = __shfl_sync(kFull, my_a, k);
+            else av[u] = In();
+        }
+        int32_t col[4];
+        In bval[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            col[u] = vv[u] ? ld_i32(B.col + qv[u]) : 0;
+            bval[u] = vv[u] ? load_val<In, S::kVal>(B.val, qv[u]) : In();
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) op.any(col[u], av[u], bval[u], vv[u]);
+    }
+}
+
 template <class S>
-__global__ void __launch_bounds__(kBlockThreads)
+__global__ void __launch_bounds__(kBlockThreads, 2)
     k_num_dense(const Prob* __restrict__ probs, int nprob, const int32_t* __restrict__ rows,
-                Counters* ctr, DevStatus* st, int32_t* cursor, int slab_cols) {
+                Counters* ctr, DevStatus* st, int32_t* cursor, int slab_cols,
+                const int32_t* __restrict__ sp, int sp_stride) {
     using Slot = typename S::Slot;
     using In = typename S::In;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Slot* vals = reinterpret_cast<Slot*>(smem_raw);
     uint32_t* bm = reinterpret_cast<uint32_t*>(smem_raw + dense_val_bytes<S>(slab_cols));
-    int32_t* chunk_off = reinterpret_cast<int32_t*>(bm + slab_cols / 32);
-    __shared__ int s_row, s_next;
+    int32_t* word_off = reinterpret_cast<int32_t*>(bm + slab_cols / 32);   // [words + 1]
+    __shared__ BatchSmem<In> bs;
+    __shared__ SmallRowSmem<In> srs;
+    __shared__ int s_row;
+    __shared__ int s_wsum[kBlockThreads / 32];
     __shared__ int64_t s_written;
-    __shared__ int s_slab_total;
     const int lane = lane_id(), wid = warp_id(), nwarps = blockDim.x >> 5;
+    const int tid = threadIdx.x;
     const int beg = ctr->num_bin_off[kTierDense * kSubBins];
     const int end = ctr->num_bin_off[(kTierDense + 1) * kSubBins];
     for (;;) {
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
             s_row = beg + atomicAdd(&ctr->claim[3], 1);
             s_written = 0;
         }
@@ -346,80 +430,176 @@ __global__ void __launch_bounds__(kBlockThreads)
         const int64_t a0 = ld_i64(P.A.rp + i), a1 = ld_i64(P.A.rp + i + 1);
         const int64_t ncols = P.B.ncols;
         const int nslabs = (int)((ncols + slab_cols - 1) / slab_cols);
+        // small rows: <= 32 entries, slab table available (or one slab)
+        const bool small = a1 - a0 <= 32 && (sp != nullptr || nslabs == 1);
+        const bool one_batch = !small && a1 - a0 <= kBatch;
+        const Slab first{0, 0, true, nslabs == 1, nslabs == 1, cursor, sp, sp_stride, 0};
+        RowEntry<In, S::kVal> ent;
+        if (one_batch) ent.load(P.A, P.B, a0 + tid, a0 + tid < a1, first);
+        // small-row entry, the same in every warp (lane e = entry e)
+        int32_t sk = 0;
+        int64_t srs0 = 0, sre0 = 0;
+        if (small) {
+            const int64_t p = a0 + lane;
+            if (p < a1) {
+                sk = ld_i32(P.A.col + p);
+                srs0 = ld_i64(P.B.rp + sk);
+                sre0 = ld_i64(P.B.rp + sk + 1);
+                if (wid == 0) {
+                    if constexpr (S::kVal) srs.a[lane] = load_val<In, S::kVal>(P.A.val, p);
+                }
+            } else if (wid == 0) {
+                if constexpr (S::kVal) srs.a[lane] = In();
+            }
+        }
         for (int s = 0; s < nslabs; ++s) {
+            if (small && (s & 15) == 0) {
+                // warp w tabulates slab s + w of this group
+                const int ss = s + wid;
+                if (ss < nslabs) {
+                    int64_t b = srs0, e = sre0;
+                    if (nslabs > 1 && a0 + lane < a1) {
+                        const int32_t* spk = sp + (int64_t)sk * sp_stride;
+                        b = srs0 + __ldg(spk + ss);
+                        e = srs0 + __ldg(spk + ss + 1);
+                    }
+                    const int len = (int)(e - b);
+                    srs.beg[wid][lane] = b;
+                    srs.end[wid][lane] = warp_incl_scan(len);
+                }
+            }
             const int32_t lo = (int32_t)((int64_t)s * slab_cols);
             const int64_t hi64 = (int64_t)lo + slab_cols < ncols ? (int64_t)lo + slab_cols : ncols;
             const int32_t hi = (int32_t)hi64;
             const int width = hi - lo;
             const int words = (width + 31) >> 5;
-            if constexpr (S::kVal)
-                for (int c = threadIdx.x; c < width; c += blockDim.x) vals[c] = S::empty();
-            if constexpr (S::kBitmap)
-                for (int w = threadIdx.x; w < words; w += blockDim.x) bm[w] = 0u;
-            if (threadIdx.x == 0) s_next = 0;
+            if constexpr (S::kVal) fill_slots<S>(vals, width);
+            for (int w = tid; w < words; w += blockDim.x) bm[w] = 0u;
             __syncthreads();
-            const Slab slab{lo, hi, s == 0, s == nslabs - 1, nslabs == 1, cursor};
-            DenseAccOp<S> op{vals, bm, lo, P.B.col, reinterpret_cast<const In*>(P.B.val)};
-            for (;;) {
-                int c = 0;
-                if (lane == 0) c = atomicAdd(&s_next, 1);
-                c = __shfl_sync(kFull, c, 0);
-                const int64_t p0 = a0 + (int64_t)c * 32;
-                if (p0 >= a1) break;
-                chunk_products<In, S::kVal>(P.A, P.B, p0, a1, P.nnz_base + p0, slab, op);
+            const Slab slab{lo, hi, s == 0, s == nslabs - 1, nslabs == 1, cursor, sp, sp_stride, s};
+            DenseAccOp<S> op{vals, bm, lo};
+            if (small) {
+                small_row_slab_products<S>(P.B, srs, s & 15, op);
+                __syncthreads();
+            } else if (one_batch) {
+                int64_t sb, se;
+                ent.segment(P.B, slab, nslabs, sb, se);
+                cta_walk_segments<In, S::kVal>(P.B, sb, se - sb, ent.a, bs, op);
+            } else {
+                cta_row_products<In, S::kVal>(P.A, P.B, a0, a1, P.nnz_base + a0, slab, bs, op);
+            }
+            // exclusive scan of the words' popcounts (contiguous words per thread)
+            const int wpt = (words + (int)blockDim.x - 1) / (int)blockDim.x;
+            const int w0 = tid * wpt;
+            int mine = 0;
+            for (int j = 0; j < wpt; ++j)
+                if (w0 + j < words) mine += __popc(bm[w0 + j]);
+            const int incl = warp_incl_scan(mine);
+            if (lane == 31) s_wsum[wid] = incl;
+            __syncthreads();
+            if (wid == 0) {
+                const int x = lane < nwarps ? s_wsum[lane] : 0;
+                const int xi = warp_incl_scan(x);
+                if (lane < nwarps) s_wsum[lane] = xi - x;
+                if (lane == 31) word_off[words] = xi;
             }
             __syncthreads();
-            // count per 1024-column chunk (and build the bitmap if values mark presence)
-            const int nchunks = (width + 1023) >> 10;
-            for (int ch = wid; ch < nchunks; ch += nwarps) {
-                uint32_t bits = 0;
-                if constexpr (S::kBitmap) {
-                    const int w = ch * 32 + lane;
-                    bits = w < words ? bm[w] : 0u;
-                } else {
-                    for (int t = 0; t < 32; ++t) {
-                        const int c = (ch * 32 + t) * 32 + lane;
-                        const unsigned m = __ballot_sync(kFull, c < width && S::touched(vals[c]));
-                        if (lane == t) bits = m;
+            {
+                int run = s_wsum[wid] + incl - mine;
+                for (int j = 0; j < wpt; ++j)
+                    if (w0 + j < words) {
+                        word_off[w0 + j] = run;
+                        run += __popc(bm[w0 + j]);
                     }
-                    const int w = ch * 32 + lane;
-                    if (w < words) bm[w] = bits;
-                }
-                const int cc = warp_sum(__popc(bits));
-                if (lane == 0) chunk_off[ch] = cc;
             }
             __syncthreads();
-            if (wid == 0) {   // exclusive scan of chunk counts (nchunks <= 64)
-                const int v0 = 2 * lane < nchunks ? chunk_off[2 * lane] : 0;
-                const int v1 = 2 * lane + 1 < nchunks ? chunk_off[2 * lane + 1] : 0;
-                const int incl = warp_incl_scan(v0 + v1);
-                const int ex = incl - v0 - v1;
-                if (2 * lane < nchunks) chunk_off[2 * lane] = ex;
-                if (2 * lane + 1 < nchunks) chunk_off[2 * lane + 1] = ex + v0;
-                if (lane == 31) s_slab_total = incl;
-            }
-            __syncthreads();
+            // Warp w writes the outputs [T w / nwarps, T (w+1) / nwarps) of the
+            // slab: it visits the words holding them 32 at a time (lane j =
+            // word wc + j, bits outside the range masked off); output o of a
+            // group is the (o - excl)-th set bit of the lane whose prefix holds o.
+            const int T = word_off[words];
             const int64_t slab_base = off + s_written;
-            for (int ch = wid; ch < nchunks; ch += nwarps) {
-                int64_t pos = slab_base + chunk_off[ch];
-                for (int t = 0; t < 32; ++t) {
-                    const int w = ch * 32 + t;
-                    const uint32_t bits = w < words ? bm[w] : 0u;
-                    if ((bits >> lane) & 1u) {
-                        const int c = w * 32 + lane;
-                        const int64_t at = pos + __popc(bits & ((1u << lane) - 1));
-                        if (at < off + n) write_entry<S>(P, at, lo + c, vals[c]);
-                        else flag_overflow(st, g);   // counts disagree: never write past the row
+            const int o_lo = (int)((int64_t)T * wid / nwarps), o_hi = (int)((int64_t)T * (wid + 1) / nwarps);
+            if (o_lo < o_hi) {
+                int wlo = 0, whi = words - 1;   // word holding output o_lo
+                while (wlo < whi) {
+                    const int mid = (wlo + whi + 1) >> 1;
+                    if (word_off[mid] <= o_lo) wlo = mid; else whi = mid - 1;
+                }
+                for (int wc = wlo; wc < words; wc += 32) {   // warp-uniform
+                    const int wj = wc + lane;
+                    uint32_t bits = 0u;
+                    int first_out = 0;   // slab output index of the lane's first kept bit
+                    if (wj < words) {
+                        const uint32_t all = bm[wj];
+                        const int base = word_off[wj];
+                        const int nb = __popc(all);
+                        const int lo_k = min(max(o_lo - base, 0), nb);
+                        const int hi_k = min(max(o_hi - base, 0), nb);
+                        bits = all;
+                        for (int x = 0; x < lo_k; ++x) bits &= bits - 1u;   // drop lowest
+                        for (int x = hi_k; x < nb; ++x) bits &= ~(0x80000000u >> __clz(bits));
+                        first_out = base + lo_k;
                     }
-                    pos += __popc(bits);
+                    const int cnt = __popc(bits);
+                    const int incl2 = warp_incl_scan(cnt);
+                    const int ex2 = incl2 - cnt;
+                    const int TT = __shfl_sync(kFull, incl2, 31);
+                    for (int o0 = 0; o0 < TT; o0 += 32) {   // warp-uniform
+                        const int o = o0 + lane;
+                        int owner = 0;
+#pragma unroll
+                        for (int step = 16; step > 0; step >>= 1) {
+                            const int c = owner + step;
+                            if (__shfl_sync(kFull, ex2, c) <= o) owner = c;
+                        }
+                        const uint32_t ob = __shfl_sync(kFull, bits, owner);
+                        const int k = o - __shfl_sync(kFull, ex2, owner);
+                        const int fo = __shfl_sync(kFull, first_out, owner);
+                        if (o < TT) {
+                            const unsigned bit = __fns(ob, 0, k + 1);
+                            const int64_t at = slab_base + fo + k;
+                            if (bit < 32u && at < off + n) {
+                                const int c = (wc + owner) * 32 + (int)bit;
+                                write_entry<S>(P, at, lo + c, vals[c]);
+                            } else {
+                                flag_overflow(st, g);   // counts disagree: never write past the row
+                            }
+                        }
+                    }
+                    if (word_off[min(wc + 32, words)] >= o_hi) break;
                 }
             }
             __syncthreads();
-            if (threadIdx.x == 0) s_written += s_slab_total;
+            if (tid == 0) s_written += T;
             __syncthreads();
         }
-        if (threadIdx.x == 0 && s_written != n) flag_overflow(st, g);
+        if (tid == 0 && s_written != n) flag_overflow(st, g);
         __syncthreads();
+    }
+}
+
+// ---- slab starts of B's rows ------------------------------------------------------
+
+// sp[k * (nslabs + 1) + t] = offset in row k of B of its first column >= t * W
+// (t = nslabs gives the row length).  Skipped when no row is in the dense tier.
+__global__ void k_slab_ptr(DCsr B, int W, int nslabs, int32_t* sp, const Counters* ctr) {
+    if (ctr->num_bin_off[(kTierDense + 1) * kSubBins] == ctr->num_bin_off[kTierDense * kSubBins])
+        return;
+    const int lane = lane_id();
+    const int stride = nslabs + 1;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); k < B.nrows; k += nw) {
+        const int64_t rs = ld_i64(B.rp + k), re = ld_i64(B.rp + k + 1);
+        for (int t = lane; t <= nslabs; t += 32) {
+            const int64_t lim = (int64_t)t * W;
+            int64_t a = rs, b = re;
+            while (a < b) {
+                const int64_t m = (a + b) >> 1;
+                if ((int64_t)ld_i32(B.col + m) < lim) a = m + 1; else b = m;
+            }
+            sp[k * stride + t] = (int32_t)(a - rs);
+        }
     }
 }
 
@@ -443,7 +623,7 @@ size_t num_block_bytes(const Tuning& t) {
 template <class S>
 size_t num_dense_bytes(int64_t slab_cols) {
     return dense_val_bytes<S>(slab_cols) + (size_t)slab_cols / 8 +
-           ((size_t)slab_cols / 1024 + 1) * 4;
+           ((size_t)slab_cols / 32 + 1) * 4;
 }
 
 struct SizeFn {
@@ -483,6 +663,7 @@ static int occupancy_grid(const void* fn, int threads, size_t smem, const DevInf
 
 struct NumericLaunch {
     const WsPtrs* w;
+    DCsr B0;              // B of the first product (slab pointers: single product only)
     int nprob;
     const Tuning* t;
     int64_t max_ncols;
@@ -500,8 +681,16 @@ struct NumericLaunch {
                                      (int)smem);
             if (e != cudaSuccess) { err = e; return; }
             const int grid = occupancy_grid((const void*)k_num_dense<S>, kBlockThreads, smem, *dev);
+            const int nslabs = (int)((max_ncols + slab - 1) / slab);
+            const int32_t* sp = nullptr;
+            if (nprob == 1 && w->slab_ptr &&
+                (size_t)(B0.nrows + 1) * (nslabs + 1) * 4 <= w->slab_ptr_bytes && nslabs > 1) {
+                k_slab_ptr<<<dev->sms * 8, 256, 0, st>>>(B0, (int)slab, nslabs, w->slab_ptr, w->ctr);
+                sp = w->slab_ptr;
+            }
             k_num_dense<S><<<grid, kBlockThreads, smem, st>>>(w->probs, nprob, w->rows_num, w->ctr,
-                                                              w->status, w->cursor, (int)slab);
+                                                              w->status, w->cursor, (int)slab, sp,
+                                                              nslabs + 1);
         }
         {   // block tier
             int64_t T = next_pow2(2 * t->num_block_max_nnz);
@@ -530,8 +719,9 @@ struct NumericLaunch {
     }
 };
 
-cudaError_t launch_numeric(int sr, const WsPtrs& w, int nprob, int64_t R, const Tuning& t,
-                           int64_t max_ncols, const DevInfo& dev, cudaStream_t st) {
+cudaError_t launch_numeric(int sr, const WsPtrs& w, const DCsr& B0, int nprob, int64_t R,
+                           const Tuning& t, int64_t max_ncols, const DevInfo& dev,
+                           cudaStream_t st) {
     if (R == 0) return cudaSuccess;
     // reset numeric bins and claims
     cudaMemsetAsync(w.ctr->num_bin_count, 0, sizeof(w.ctr->num_bin_count), st);
@@ -544,7 +734,7 @@ cudaError_t launch_numeric(int sr, const WsPtrs& w, int nprob, int64_t R, const 
                                                                    w.ctr, w.rows_num);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    NumericLaunch f{&w, nprob, &t, max_ncols, &dev, st};
+    NumericLaunch f{&w, B0, nprob, &t, max_ncols, &dev, st};
     if (!dispatch_semiring(sr, f)) return cudaErrorInvalidValue;
     return f.err;
 }

@@ -48,12 +48,16 @@ struct Counters {
 };
 
 struct WsLayout {
-    size_t status, counters, probs, ub, cnt, rows_sym, rows_num, scan_part, cursor, total;
+    size_t status, counters, probs, ub, cnt, rows_sym, rows_num, scan_part, cursor, slab_ptr,
+        slab_ptr_bytes, total;
     int64_t R;          // flat rows
     int64_t E;          // flat entries of A (cursor array length)
 };
 
-WsLayout ws_layout(int64_t R, int64_t E);
+// R flat rows, E flat entries of A; nrows_b / ncols_b / nnz_b of B and the
+// numeric dense slab width size the optional slab-start table
+WsLayout ws_layout(int64_t R, int64_t E, int64_t nrows_b = 0, int64_t ncols_b = 0,
+                   int64_t nnz_b = 0, int64_t slab_cols = 0);
 
 struct WsPtrs {
     DevStatus* status;
@@ -65,6 +69,8 @@ struct WsPtrs {
     int32_t* rows_num;
     int64_t* scan_part;
     int32_t* cursor;
+    int32_t* slab_ptr;       // slab starts of B's rows (numeric dense tier)
+    size_t slab_ptr_bytes;
 };
 WsPtrs ws_ptrs(void* ws, const WsLayout& L);
 
@@ -88,8 +94,9 @@ cudaError_t launch_transpose(const DCsr& A, int64_t nnz, int value_bytes, int64_
                              int32_t* t_col, void* t_val, void* ws, const DevInfo& dev,
                              cudaStream_t st);
 size_t transpose_ws_bytes(int64_t ncols, int64_t nnz);
-cudaError_t launch_numeric(int sr, const WsPtrs& w, int nprob, int64_t R, const Tuning& t,
-                           int64_t max_ncols, const DevInfo& dev, cudaStream_t st);
+cudaError_t launch_numeric(int sr, const WsPtrs& w, const DCsr& B0, int nprob, int64_t R,
+                           const Tuning& t, int64_t max_ncols, const DevInfo& dev,
+                           cudaStream_t st);
 cudaError_t launch_validate(const DCsr& M, int64_t nnz, DevStatus* status, cudaStream_t st);
 
 // shared-memory bytes of each tier (for tuning clamps and launches)

@@ -41,6 +41,11 @@ struct Slab {
     bool first, last;     // first / last slab of the row
     bool single;          // the only slab: no cursors used
     int32_t* cursor;      // per entry of A (flat entry numbering), or null
+    // precomputed slab starts of B's rows: sp[k * sp_stride + s] = offset in
+    // row k of its first column >= s * slab width (null: cursor mode)
+    const int32_t* sp;
+    int sp_stride;
+    int s;
 };
 
 template <class In, bool kVal>
@@ -49,49 +54,45 @@ SPG_DEV In shfl_val(In a, int src) {
     else return In();
 }
 
-// Enumerates the products of A entries [p0, min(p0 + 32, p_end)) restricted to
-// the slab; calls op(q, a, lane_valid) for each product with q the position in
-// B (all 32 lanes call op together; lane_valid false for padding lanes).
+template <class In, bool kVal>
+SPG_DEV In load_val(const void* v, int64_t q) {
+    if constexpr (kVal) return __ldg(reinterpret_cast<const In*>(v) + q);
+    else return In();
+}
+
+// Segment of B_k (its entries inside the current slab) for one A entry p,
+// held by the calling lane.  Advances the entry's slab cursor.
+template <class In, bool kVal>
+SPG_DEV void entry_segment(const DCsr& A, const DCsr& B, int64_t p, int64_t flat_p,
+                           const Slab& slab, int64_t& beg, int64_t& end, In& a) {
+    const int32_t k = ld_i32(A.col + p);
+    a = load_val<In, kVal>(A.val, p);
+    const int64_t rs = ld_i64(B.rp + k);
+    if (slab.single) {
+        beg = rs;
+        end = ld_i64(B.rp + k + 1);
+    } else if (slab.sp) {
+        const int32_t* spk = slab.sp + (int64_t)k * slab.sp_stride + slab.s;
+        beg = rs + __ldg(spk);
+        end = rs + __ldg(spk + 1);
+    } else {
+        const int64_t re = ld_i64(B.rp + k + 1);
+        beg = slab.first ? rs : rs + slab.cursor[flat_p];
+        end = slab.last ? re : gallop_lower_bound(B.col, beg, re, slab.hi);
+        if (!slab.last) slab.cursor[flat_p] = (int32_t)(end - rs);
+    }
+}
+
+// Flattened walk over the short segments held by the 32 lanes (len < 32 each,
+// 0 for lanes without one): the warp takes 32 consecutive products of their
+// concatenation at a time; each lane finds its segment by a 5-step binary
+// search over the lanes' exclusive prefix sums.  op.any(col, a, b, valid).
 template <class In, bool kVal, class Op>
-SPG_DEV void chunk_products(const DCsr& A, const DCsr& B, int64_t p0, int64_t p_end,
-                            int64_t flat_p0, const Slab& slab, Op& op) {
+SPG_DEV void warp_short_segments(const DCsr& B, int64_t beg, int len, In a, Op& op) {
     const int lane = lane_id();
-    const int64_t p = p0 + lane;
-    const bool valid = p < p_end;
-    int64_t beg = 0, end = 0;
-    In a = In();
-    if (valid) {
-        const int32_t k = ld_i32(A.col + p);
-        if constexpr (kVal) a = __ldg(reinterpret_cast<const In*>(A.val) + p);
-        if (slab.single) {
-            beg = ld_i64(B.rp + k);
-            end = ld_i64(B.rp + k + 1);
-        } else {
-            const int64_t rowend = ld_i64(B.rp + k + 1);
-            beg = slab.first ? ld_i64(B.rp + k) : (ld_i64(B.rp + k) + slab.cursor[flat_p0 + lane]);
-            end = slab.last ? rowend : gallop_lower_bound(B.col, beg, rowend, slab.hi);
-            if (!slab.last) slab.cursor[flat_p0 + lane] = (int32_t)(end - ld_i64(B.rp + k));
-        }
-    }
-    const int len = (int)(end - beg);
-    // long segments: whole warp per segment
-    unsigned longm = __ballot_sync(kFull, len >= 32);
-    while (longm) {
-        const int src = __ffs(longm) - 1;
-        longm &= longm - 1;
-        const int64_t b0 = __shfl_sync(kFull, beg, src);
-        const int64_t e0 = __shfl_sync(kFull, end, src);
-        const In av = shfl_val<In, kVal>(a, src);
-        for (int64_t q0 = b0; q0 < e0; q0 += 32) {   // warp-uniform trip count
-            const int64_t q = q0 + lane;
-            op(q, av, q < e0);
-        }
-    }
-    // short segments: flattened
-    const int sl = (len < 32) ? len : 0;
-    const int incl = warp_incl_scan(sl);
+    const int incl = warp_incl_scan(len);
     const int total = __shfl_sync(kFull, incl, 31);
-    const int excl = incl - sl;
+    const int excl = incl - len;
     for (int base = 0; base < total; base += 32) {
         const int t = base + lane;
         int owner = 0;
@@ -104,8 +105,280 @@ SPG_DEV void chunk_products(const DCsr& A, const DCsr& B, int64_t p0, int64_t p_
         const int64_t ob = __shfl_sync(kFull, beg, owner);
         const int oex = __shfl_sync(kFull, excl, owner);
         const In oa = shfl_val<In, kVal>(a, owner);
-        op(ob + (t - oex), oa, t < total);
+        const bool v = t < total;
+        const int64_t q = ob + (t - oex);
+        const int32_t col = v ? ld_i32(B.col + q) : 0;
+        const In bv = v ? load_val<In, kVal>(B.val, q) : In();
+        op.any(col, oa, bv, v);
     }
+}
+
+// One whole segment [b0, e0) walked by the warp, 4 x 32 products in flight
+// while at least 128 remain; within one pass the lanes hold ascending columns.
+// op.sorted(col, a, b, valid).
+template <class In, bool kVal, class Op>
+SPG_DEV void warp_long_segment(const DCsr& B, int64_t b0, int64_t e0, In av, Op& op) {
+    const int lane = lane_id();
+    int64_t q0 = b0;
+    for (; q0 + 128 <= e0; q0 += 128) {
+        int32_t col[4];
+        In bv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t q = q0 + 32 * u + lane;
+            col[u] = ld_i32(B.col + q);
+            bv[u] = load_val<In, kVal>(B.val, q);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) op.sorted(col[u], av, bv[u], true);
+    }
+    for (; q0 < e0; q0 += 32) {   // warp-uniform trip count
+        const int64_t q = q0 + lane;
+        const bool v = q < e0;
+        const int32_t col = v ? ld_i32(B.col + q) : 0;
+        const In bv = v ? load_val<In, kVal>(B.val, q) : In();
+        op.sorted(col, av, bv, v);
+    }
+}
+
+// Enumerates the products of A entries [p0, min(p0 + 32, p_end)) (one warp,
+// one entry per lane) restricted to the slab.
+template <class In, bool kVal, class Op>
+SPG_DEV void chunk_products(const DCsr& A, const DCsr& B, int64_t p0, int64_t p_end,
+                            int64_t flat_p0, const Slab& slab, Op& op) {
+    const int lane = lane_id();
+    const int64_t p = p0 + lane;
+    int64_t beg = 0, end = 0;
+    In a = In();
+    if (p < p_end) entry_segment<In, kVal>(A, B, p, flat_p0 + lane, slab, beg, end, a);
+    const int len = (int)(end - beg);
+    unsigned longm = __ballot_sync(kFull, len >= 32);
+    while (longm) {
+        const int src = __ffs(longm) - 1;
+        longm &= longm - 1;
+        const int64_t b0 = __shfl_sync(kFull, beg, src);
+        const int64_t e0 = __shfl_sync(kFull, end, src);
+        warp_long_segment<In, kVal>(B, b0, e0, shfl_val<In, kVal>(a, src), op);
+    }
+    warp_short_segments<In, kVal>(B, beg, len < 32 ? len : 0, a, op);
+}
+
+// ---- CTA-wide, load-balanced enumeration (block and dense tiers) -------------
+//
+// Each thread brings the segment of one A entry (a batch of up to kBatch =
+// blockDim.x entries).  The non-empty segments are compacted and the products
+// of all of them form one flattened range (exclusive scan of the lengths);
+// warp w takes the w-th of nwarps equal contiguous parts and walks it 128
+// products (4 windows of 32 loads in flight) at a time.  A pass that lies in
+// one segment is addressed from registers; a window that crosses segment
+// boundaries loads the next 32 boundaries (one per lane) and each lane finds
+// its segment by a 5-step binary search (segments are non-empty, so 32
+// boundaries cover a window).  Every warp holds its share of the products to
+// within one pass, whatever the mix of long hub segments and short ones.
+constexpr int kBatch = 512;
+constexpr int kCountShift = 50;   // scan packs (entry count << 50) + product count
+
+template <class In>
+struct BatchSmem {
+    int64_t beg[kBatch];         // compacted non-empty segments
+    int64_t off[kBatch + 1];     // exclusive scan of their lengths
+    In a[kBatch];
+    int64_t wsum[kBatch / 32];
+    int nseg;
+};
+
+// All threads of the CTA call this with their own segment [beg, beg + len)
+// and A value (len 0 for none).  Ends with __syncthreads.
+template <class In, bool kVal, class Op>
+SPG_DEV void cta_walk_segments(const DCsr& B, int64_t beg, int64_t len, In a, BatchSmem<In>& bs,
+                               Op& op) {
+    const int lane = lane_id(), wid = warp_id();
+    const int tid = threadIdx.x;
+    const int nwarps = kBatch / 32;
+    const int64_t kLenMask = ((int64_t)1 << kCountShift) - 1;
+    const int64_t packed = len > 0 ? (((int64_t)1 << kCountShift) | len) : 0;
+    const int64_t incl = warp_incl_scan(packed);
+    if (lane == 31) bs.wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const int64_t x = lane < nwarps ? bs.wsum[lane] : 0;
+        const int64_t xi = warp_incl_scan(x);
+        if (lane < nwarps) bs.wsum[lane] = xi - x;
+        if (lane == 31) {
+            bs.off[kBatch] = xi & kLenMask;            // total products
+            bs.nseg = (int)(xi >> kCountShift);        // non-empty segments
+        }
+    }
+    __syncthreads();
+    const int64_t ex = bs.wsum[wid] + incl - packed;   // exclusive (count, length)
+    if (len > 0) {
+        const int c = (int)(ex >> kCountShift);
+        bs.beg[c] = beg;
+        bs.off[c] = ex & kLenMask;
+        if constexpr (kVal) bs.a[c] = a;
+    }
+    __syncthreads();
+    const int nseg = bs.nseg;
+    const int64_t W = bs.off[kBatch];
+    if (nseg < kBatch && tid == 0) bs.off[nseg] = W;   // end of the last segment
+    __syncthreads();
+    const int64_t lo_w = W * wid / nwarps, hi_w = W * (wid + 1) / nwarps;
+    if (lo_w < hi_w) {
+        int e;
+        {   // largest segment e with off[e] <= lo_w
+            int lo = 0, hi = nseg - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (bs.off[mid] <= lo_w) lo = mid; else hi = mid - 1;
+            }
+            e = lo;
+        }
+        int64_t ebase = bs.beg[e] - bs.off[e];   // q = ebase + t inside segment e
+        int64_t eend = bs.off[e + 1];
+        In ea = In();
+        if constexpr (kVal) ea = bs.a[e];
+        for (int64_t t0 = lo_w; t0 < hi_w; t0 += 128) {   // warp-uniform
+            int64_t qv[4];
+            In av[4];
+            bool vv[4];
+            if (eend >= t0 + 128 || eend >= hi_w) {       // the pass lies in segment e
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t t = t0 + 32 * u + lane;
+                    vv[u] = t < hi_w;
+                    qv[u] = ebase + t;
+                    av[u] = ea;
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t tu = t0 + 32 * u;
+                    const int64_t t = tu + lane;
+                    vv[u] = t < hi_w;
+                    int me = e;
+                    if (tu < hi_w) {                         // warp-uniform
+                        while (bs.off[e + 1] <= tu) ++e;     // segments are non-empty
+                        me = e;
+                        if (bs.off[e + 1] < tu + 32 && bs.off[e + 1] < hi_w) {
+                            const int ej = e + lane;       // lane j: end of segment e + j
+                            const int64_t bnd = ej < nseg ? bs.off[ej + 1] : INT64_MAX;
+                            int k = 0;                     // number of ends <= t
+#pragma unroll
+                            for (int step = 16; step > 0; step >>= 1) {
+                                const int64_t bv = __shfl_sync(kFull, bnd, k + step - 1);
+                                if (bv <= t) k += step;
+                            }
+                            me = e + k;
+                        }
+                    }
+                    qv[u] = bs.beg[me] + (t - bs.off[me]);
+                    if constexpr (kVal) av[u] = bs.a[me];
+                    else av[u] = In();
+                }
+                const int64_t tn = t0 + 128;              // segment of the next pass
+                if (tn < hi_w) {
+                    while (bs.off[e + 1] <= tn) ++e;
+                }
+                ebase = bs.beg[e] - bs.off[e];
+                eend = bs.off[e + 1];
+                if constexpr (kVal) ea = bs.a[e];
+            }
+            int32_t col[4];
+            In bval[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                col[u] = vv[u] ? ld_i32(B.col + qv[u]) : 0;
+                bval[u] = vv[u] ? load_val<In, kVal>(B.val, qv[u]) : In();
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) op.any(col[u], av[u], bval[u], vv[u]);
+        }
+    }
+    __syncthreads();
+}
+
+// One A entry per thread, kept in registers while a row is processed slab
+// after slab (rows with at most kBatch entries): its segment in each slab
+// comes from the slab-start table (next bound prefetched one slab ahead) or,
+// without a table, from a cursor advanced by galloping.
+template <class In, bool kVal>
+struct RowEntry {
+    bool v;
+    int32_t k;
+    In a;
+    int64_t rs, re, cur;
+    int32_t sp_lo, sp_hi, sp_nx;
+
+    SPG_DEV void load(const DCsr& A, const DCsr& B, int64_t p, bool valid, const Slab& first) {
+        v = valid;
+        k = 0;
+        a = In();
+        rs = re = cur = 0;
+        sp_lo = sp_hi = sp_nx = 0;
+        if (!v) return;
+        k = ld_i32(A.col + p);
+        a = load_val<In, kVal>(A.val, p);
+        rs = ld_i64(B.rp + k);
+        re = ld_i64(B.rp + k + 1);
+        cur = rs;
+        if (first.sp) {
+            const int32_t* spk = first.sp + (int64_t)k * first.sp_stride;
+            sp_lo = __ldg(spk);
+            sp_hi = __ldg(spk + 1);
+        }
+    }
+    // slabs must be visited in order s = 0, 1, ...
+    SPG_DEV void segment(const DCsr& B, const Slab& sl, int nslabs, int64_t& beg, int64_t& end) {
+        beg = end = 0;
+        if (!v) return;
+        if (sl.single) {
+            beg = rs;
+            end = re;
+        } else if (sl.sp) {
+            beg = rs + sp_lo;
+            end = rs + sp_hi;
+            sp_nx = (sl.s + 2 <= nslabs) ? __ldg(sl.sp + (int64_t)k * sl.sp_stride + sl.s + 2) : 0;
+            sp_lo = sp_hi;
+            sp_hi = sp_nx;
+        } else {
+            beg = cur;
+            end = sl.last ? re : gallop_lower_bound(B.col, cur, re, sl.hi);
+            cur = end;
+        }
+    }
+};
+
+// Products of row entries [a0, a1) restricted to the slab, spread over the CTA.
+template <class In, bool kVal, class Op>
+SPG_DEV void cta_row_products(const DCsr& A, const DCsr& B, int64_t a0, int64_t a1,
+                              int64_t flat_base, const Slab& slab, BatchSmem<In>& bs, Op& op) {
+    for (int64_t b0 = a0; b0 < a1; b0 += kBatch) {
+        const int64_t p = b0 + threadIdx.x;
+        int64_t beg = 0, end = 0;
+        In a = In();
+        if (p < a1) entry_segment<In, kVal>(A, B, p, flat_base + (p - a0), slab, beg, end, a);
+        cta_walk_segments<In, kVal>(B, beg, end - beg, a, bs, op);
+    }
+}
+
+// OR of one bit per lane into a shared bitmap, for lanes holding ascending
+// columns (c relative to the slab): lanes of one 32-bit word form a run; a
+// segmented OR-scan gives the run's last lane the word's bits, and only that
+// lane issues the atomic (one atomic per word instead of one per column).
+SPG_DEV void bitmap_or_sorted(uint32_t* bm, int32_t c, bool valid) {
+    const int lane = lane_id();
+    const int w = valid ? (c >> 5) : -1 - lane;
+    uint32_t bit = valid ? (1u << (c & 31)) : 0u;
+    const int wprev = __shfl_up_sync(kFull, w, 1);
+    const unsigned heads = __ballot_sync(kFull, lane == 0 || wprev != w);
+    const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t o = __shfl_up_sync(kFull, bit, d);
+        if (lane - d >= start) bit |= o;
+    }
+    const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+    if (valid && tail) atomicOr(bm + w, bit);
 }
 
 // ---- shared-memory hash tables (linear probing, power-of-two size) ----------

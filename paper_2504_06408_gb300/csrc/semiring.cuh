@@ -86,7 +86,18 @@ struct SrMpF32 {
     using Out = float;
     static constexpr bool kVal = true, kBitmap = false;
     static SPG_DEV Slot empty() { return 0xffffffffu; }
-    static SPG_DEV void acc(Slot* s, In a, In b) { atomicMin(s, f32_to_ordered(__fadd_rn(a, b))); }
+    // read first: once a slot is small, most products cannot lower it
+    static SPG_DEV void acc(Slot* s, In a, In b) {
+        const uint32_t m = f32_to_ordered(__fadd_rn(a, b));
+        if (m < *(volatile Slot*)s) atomicMin(s, m);
+    }
+    // as acc(); returns true if the slot was untouched before (first product)
+    static SPG_DEV bool acc_first(Slot* s, In a, In b) {
+        const uint32_t m = f32_to_ordered(__fadd_rn(a, b));
+        const uint32_t cur = *(volatile Slot*)s;
+        if (m < cur) atomicMin(s, m);
+        return cur == 0xffffffffu;
+    }
     static SPG_DEV bool touched(Slot v) { return v != 0xffffffffu; }
     static SPG_DEV Out out(Slot v) { return ordered_to_f32(v); }
     static SPG_DEV Out add(Out x, Out y) {
@@ -131,8 +142,20 @@ struct SrOverlap {
         const unsigned long long x =
             ((unsigned long long)(uint32_t)a << 32) | (unsigned long long)(uint32_t)b;
         atomicAdd(&s->count, 1u);
+        // x >= current second smallest: neither minimum can change
+        if (x >= *(volatile unsigned long long*)&s->m2) return;
         const unsigned long long old = atomicMin(&s->m1, x);
         atomicMin(&s->m2, old > x ? old : x);
+    }
+    static SPG_DEV bool acc_first(Slot* s, In a, In b) {
+        const unsigned long long x =
+            ((unsigned long long)(uint32_t)a << 32) | (unsigned long long)(uint32_t)b;
+        const unsigned int c0 = atomicAdd(&s->count, 1u);
+        if (x < *(volatile unsigned long long*)&s->m2) {
+            const unsigned long long old = atomicMin(&s->m1, x);
+            atomicMin(&s->m2, old > x ? old : x);
+        }
+        return c0 == 0u;
     }
     static SPG_DEV bool touched(const Slot& v) { return v.count != 0u; }
     static SPG_DEV Out out(const Slot& v) {

@@ -118,16 +118,16 @@ struct KeyInsertOp {
     int32_t* tab;
     int shift;
     uint32_t mask;
-    const int32_t* bcol;
     DevStatus* st;
     int64_t g;
     int mine;
-    SPG_DEV void operator()(int64_t q, char, bool valid) {
+    SPG_DEV void any(int32_t col, char, char, bool valid) {
         if (!valid) return;
-        const int r = hash_insert(tab, shift, mask, ld_i32(bcol + q));
+        const int r = hash_insert(tab, shift, mask, col);
         if (r > 0) ++mine;
         else if (r < 0) flag_overflow(st, g);
     }
+    SPG_DEV void sorted(int32_t col, char a, char b, bool valid) { any(col, a, b, valid); }
 };
 
 __global__ void __launch_bounds__(kWarpTierWarps * 32)
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(kWarpTierWarps * 32)
     const int beg = ctr->sym_bin_off[kTierWarp * kSubBins];
     const int end = ctr->sym_bin_off[(kTierWarp + 1) * kSubBins];
     const int stride = gridDim.x * kWarpTierWarps;
-    const Slab single{0, 0, true, true, true, nullptr};
+    const Slab single{0, 0, true, true, true, nullptr, nullptr, 0, 0};
     for (int r = beg + blockIdx.x * kWarpTierWarps + warp_id(); r < end; r += stride) {
         const int64_t g = rows[r];
         const Prob& P = probs[nprob == 1 ? 0 : find_prob(probs, nprob, g)];
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(kWarpTierWarps * 32)
         }
         for (int s = lane; s < T; s += 32) tab[s] = kEmptyKey;
         __syncwarp();
-        KeyInsertOp op{tab, 32 - log2_exact(T), (uint32_t)(T - 1), P.B.col, st, g, 0};
+        KeyInsertOp op{tab, 32 - log2_exact(T), (uint32_t)(T - 1), st, g, 0};
         const int64_t a0 = ld_i64(P.A.rp + i), a1 = ld_i64(P.A.rp + i + 1);
         for (int64_t p0 = a0; p0 < a1; p0 += 32)
             chunk_products<char, false>(P.A, P.B, p0, a1, 0, single, op);
@@ -171,15 +171,15 @@ __global__ void __launch_bounds__(kBlockThreads)
                 DevStatus* st, int table_slots) {
     extern __shared__ int32_t smem_i32[];
     int32_t* tab = smem_i32;
-    __shared__ int s_row, s_next, s_cnt;
+    __shared__ BatchSmem<char> bs;
+    __shared__ int s_row, s_cnt;
     const int lane = lane_id();
     const int beg = ctr->sym_bin_off[kTierBlock * kSubBins];
     const int end = ctr->sym_bin_off[(kTierBlock + 1) * kSubBins];
-    const Slab single{0, 0, true, true, true, nullptr};
+    const Slab single{0, 0, true, true, true, nullptr, nullptr, 0, 0};
     for (;;) {
         if (threadIdx.x == 0) {
             s_row = beg + atomicAdd(&ctr->claim[0], 1);
-            s_next = 0;
             s_cnt = 0;
         }
         __syncthreads();
@@ -199,16 +199,9 @@ __global__ void __launch_bounds__(kBlockThreads)
         }
         for (int s = threadIdx.x; s < T; s += blockDim.x) tab[s] = kEmptyKey;
         __syncthreads();
-        KeyInsertOp op{tab, 32 - log2_exact(T), (uint32_t)(T - 1), P.B.col, st, g, 0};
+        KeyInsertOp op{tab, 32 - log2_exact(T), (uint32_t)(T - 1), st, g, 0};
         const int64_t a0 = ld_i64(P.A.rp + i), a1 = ld_i64(P.A.rp + i + 1);
-        for (;;) {
-            int c = 0;
-            if (lane == 0) c = atomicAdd(&s_next, 1);
-            c = __shfl_sync(kFull, c, 0);
-            const int64_t p0 = a0 + (int64_t)c * 32;
-            if (p0 >= a1) break;
-            chunk_products<char, false>(P.A, P.B, p0, a1, 0, single, op);
-        }
+        cta_row_products<char, false>(P.A, P.B, a0, a1, 0, single, bs, op);
         const int tot = warp_sum(op.mine);
         if (lane == 0 && tot) atomicAdd(&s_cnt, tot);
         __syncthreads();
@@ -220,12 +213,14 @@ __global__ void __launch_bounds__(kBlockThreads)
 struct BitOrOp {
     uint32_t* bm;
     int32_t lo;
-    const int32_t* bcol;
-    SPG_DEV void operator()(int64_t q, char, bool valid) {
+    // read first: most products of a heavy row hit a bit that is already set
+    SPG_DEV void any(int32_t col, char, char, bool valid) {
         if (!valid) return;
-        const int32_t c = ld_i32(bcol + q) - lo;
-        atomicOr(bm + (c >> 5), 1u << (c & 31));
+        const int32_t c = col - lo;
+        const uint32_t bit = 1u << (c & 31);
+        if (!(bm[c >> 5] & bit)) atomicOr(bm + (c >> 5), bit);
     }
+    SPG_DEV void sorted(int32_t col, char a, char b, bool valid) { any(col, a, b, valid); }
 };
 
 __global__ void __launch_bounds__(kBlockThreads)
@@ -233,7 +228,8 @@ __global__ void __launch_bounds__(kBlockThreads)
                 Counters* ctr, int64_t* __restrict__ cnt, int32_t* cursor, int slab_cols) {
     extern __shared__ uint32_t smem_u32[];
     uint32_t* bm = smem_u32;
-    __shared__ int s_row, s_next;
+    __shared__ BatchSmem<char> bs;
+    __shared__ int s_row;
     __shared__ unsigned long long s_tot;
     const int lane = lane_id();
     const int beg = ctr->sym_bin_off[kTierDense * kSubBins];
@@ -258,19 +254,10 @@ __global__ void __launch_bounds__(kBlockThreads)
             const int32_t hi = (int32_t)hi64;
             const int words = (hi - lo + 31) >> 5;
             for (int w = threadIdx.x; w < words; w += blockDim.x) bm[w] = 0u;
-            if (threadIdx.x == 0) s_next = 0;
             __syncthreads();
-            const Slab slab{lo, hi, s == 0, s == nslabs - 1, nslabs == 1, cursor};
-            BitOrOp op{bm, lo, P.B.col};
-            for (;;) {
-                int c = 0;
-                if (lane == 0) c = atomicAdd(&s_next, 1);
-                c = __shfl_sync(kFull, c, 0);
-                const int64_t p0 = a0 + (int64_t)c * 32;
-                if (p0 >= a1) break;
-                chunk_products<char, false>(P.A, P.B, p0, a1, P.nnz_base + p0, slab, op);
-            }
-            __syncthreads();
+            const Slab slab{lo, hi, s == 0, s == nslabs - 1, nslabs == 1, cursor, nullptr, 0, s};
+            BitOrOp op{bm, lo};
+            cta_row_products<char, false>(P.A, P.B, a0, a1, P.nnz_base + a0, slab, bs, op);
             int mine = 0;
             for (int w = threadIdx.x; w < words; w += blockDim.x) mine += __popc(bm[w]);
             mine = warp_sum(mine);
