@@ -90,7 +90,9 @@ typedef struct {
     int64_t num_block_max_nnz;  /* numeric: nnz(C_i) <= this -> CTA hash + CTA sort   */
     int64_t dense_slab_cols;    /* numeric dense tier: columns per shared-memory slab   */
     int64_t sym_slab_cols;      /* symbolic dense tier: columns per bitmap slab         */
-    int64_t reserved[4];
+    int64_t bitmap_cache_bytes; /* workspace bytes that keep the symbolic phase's row
+                                   bitmaps for the numeric dense tier (< 0: none)      */
+    int64_t reserved[3];
 } spg_tuning;
 
 /* Counters of the last analysis on a handle (host copy, filled by spgemm_symbolic). */

@@ -40,7 +40,7 @@ static size_t slab_ptr_table_bytes(int64_t nrows_b, int64_t ncols_b, int64_t nnz
 }
 
 WsLayout ws_layout(int64_t R, int64_t E, int64_t nrows_b, int64_t ncols_b, int64_t nnz_b,
-                   int64_t slab_cols) {
+                   int64_t slab_cols, int64_t cache_bytes) {
     WsLayout L{};
     L.R = R;
     L.E = E;
@@ -57,6 +57,16 @@ WsLayout ws_layout(int64_t R, int64_t E, int64_t nrows_b, int64_t ncols_b, int64
     L.cursor = o;    o = align256(o + sizeof(int32_t) * (size_t)E);
     L.slab_ptr_bytes = slab_ptr_table_bytes(nrows_b, ncols_b, nnz_b, slab_cols);
     L.slab_ptr = o;  o = align256(o + L.slab_ptr_bytes);
+    // bitmap cache: one bitmap of ncols_b bits per cached row (rank kernel rows only)
+    L.bm_cache_words = (ncols_b + 1023) / 1024 * 32;
+    L.bm_cache_slots = 0;
+    if (cache_bytes > 0 && L.bm_cache_words > 0 && L.bm_cache_words * 8 + 16 < 180 * 1024) {
+        L.bm_cache_slots = cache_bytes / (L.bm_cache_words * 4);
+        if (L.bm_cache_slots > R) L.bm_cache_slots = R;
+    }
+    L.row_slot = o;  o = align256(o + (L.bm_cache_slots ? sizeof(int32_t) * (size_t)R : 0));
+    L.bm_cache_bytes = (size_t)L.bm_cache_slots * (size_t)L.bm_cache_words * 4;
+    L.bm_cache = o;  o = align256(o + L.bm_cache_bytes);
     L.total = o;
     return L;
 }
@@ -75,6 +85,10 @@ WsPtrs ws_ptrs(void* ws, const WsLayout& L) {
     w.cursor = (int32_t*)(b + L.cursor);
     w.slab_ptr = L.slab_ptr_bytes ? (int32_t*)(b + L.slab_ptr) : nullptr;
     w.slab_ptr_bytes = L.slab_ptr_bytes;
+    w.bm_cache = L.bm_cache_slots ? (uint32_t*)(b + L.bm_cache) : nullptr;
+    w.bm_cache_words = L.bm_cache_words;
+    w.bm_cache_slots = L.bm_cache_slots;
+    w.row_slot = L.bm_cache_slots ? (int32_t*)(b + L.row_slot) : nullptr;
     return w;
 }
 
@@ -89,6 +103,7 @@ Tuning default_tuning(int sr) {
     t.sym_slab_cols = 1 << 20;
     t.num_warp_max_nnz = 128;
     t.num_block_max_nnz = 2048;
+    t.bitmap_cache_bytes = (int64_t)4 << 30;
     switch (sr) {
         case SR_BOOL: t.dense_slab_cols = 1 << 18; break;
         case SR_MP_F32: case SR_PT_F32: t.dense_slab_cols = 16384; break;
@@ -161,7 +176,16 @@ static Tuning effective_tuning(const spg_handle* h, int sr) {
     if (u.num_block_max_nnz > 0) t.num_block_max_nnz = u.num_block_max_nnz;
     if (u.dense_slab_cols > 0) t.dense_slab_cols = u.dense_slab_cols;
     if (u.sym_slab_cols > 0) t.sym_slab_cols = u.sym_slab_cols;
+    if (u.bitmap_cache_bytes != 0) t.bitmap_cache_bytes = u.bitmap_cache_bytes;
     return clamp_tuning(t, sr);
+}
+
+// workspace of one product: the bitmap cache is kept only when the symbolic
+// dense tier sees whole rows in one slab and SR is not pattern-free of use
+static WsLayout layout_for(const spg_csr* A, const spg_csr* B, const Tuning& t) {
+    const int64_t cache = (t.bitmap_cache_bytes > 0 && B->ncols <= t.sym_slab_cols)
+                              ? t.bitmap_cache_bytes : 0;
+    return ws_layout(A->nrows, A->nnz, B->nrows, B->ncols, B->nnz, t.dense_slab_cols, cache);
 }
 
 static DCsr to_dcsr(const spg_csr* M) {
@@ -253,7 +277,7 @@ spg_status spgemm_workspace_size(spg_handle* h, spg_semiring sr, const spg_csr* 
     if (s != SPG_OK) return s;
     if (!bytes) return fail(h, SPG_ERR_INVALID_ARG, "bytes is NULL");
     const Tuning t = effective_tuning(h, sr);
-    *bytes = ws_layout(A->nrows, A->nnz, B->nrows, B->ncols, B->nnz, t.dense_slab_cols).total;
+    *bytes = layout_for(A, B, t).total;
     return SPG_OK;
 }
 
@@ -278,12 +302,14 @@ spg_status spgemm_symbolic(spg_handle* h, spg_semiring sr, const spg_csr* A, con
     if (s != SPG_OK) return s;
     if (!c_row_ptr || !c_nnz) return fail(h, SPG_ERR_INVALID_ARG, "c_row_ptr / c_nnz is NULL");
     const Tuning t = effective_tuning(h, sr);
-    const WsLayout L = ws_layout(A->nrows, A->nnz, B->nrows, B->ncols, B->nnz, t.dense_slab_cols);
+    const WsLayout L = layout_for(A, B, t);
     if (!workspace || workspace_bytes < L.total)
         return fail(h, SPG_ERR_WORKSPACE, "workspace needs %zu bytes", L.total);
     cudaStream_t st = (cudaStream_t)stream;
     const WsPtrs w = ws_ptrs(workspace, L);
     cudaError_t e = cudaMemsetAsync(workspace, 0, L.probs, st);   // status + counters
+    if (e == cudaSuccess && w.row_slot)
+        e = cudaMemsetAsync(w.row_slot, 0xff, sizeof(int32_t) * (size_t)A->nrows, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "memset");
     ProbTable* tab = new ProbTable;
     std::memset(tab, 0, sizeof *tab);
@@ -318,7 +344,7 @@ spg_status spgemm_numeric(spg_handle* h, spg_semiring sr, const spg_csr* A, cons
     if (s != SPG_OK) return s;
     if (!c_row_ptr) return fail(h, SPG_ERR_INVALID_ARG, "c_row_ptr is NULL");
     const Tuning t = effective_tuning(h, sr);
-    const WsLayout L = ws_layout(A->nrows, A->nnz, B->nrows, B->ncols, B->nnz, t.dense_slab_cols);
+    const WsLayout L = layout_for(A, B, t);
     if (!workspace || workspace_bytes < L.total)
         return fail(h, SPG_ERR_WORKSPACE, "workspace needs %zu bytes", L.total);
     cudaStream_t st = (cudaStream_t)stream;

@@ -84,6 +84,22 @@ SPG_DEV uint32_t hash_slot(int32_t key, int shift) {
 
 SPG_DEV int log2_exact(int64_t pow2) { return 63 - __clzll(pow2); }
 
+// Position of the k-th (0-based) set bit of x, by halving on popcounts;
+// requires k < popc(x).
+SPG_DEV int select_bit(uint32_t x, int k) {
+    int pos = 0;
+    int c = __popc(x & 0xffffu);
+    if (k >= c) { k -= c; x >>= 16; pos += 16; }
+    c = __popc(x & 0xffu);
+    if (k >= c) { k -= c; x >>= 8; pos += 8; }
+    c = __popc(x & 0xfu);
+    if (k >= c) { k -= c; x >>= 4; pos += 4; }
+    c = __popc(x & 0x3u);
+    if (k >= c) { k -= c; x >>= 2; pos += 2; }
+    if (k >= (int)(x & 1u)) pos += 1;
+    return pos;
+}
+
 __host__ __device__ inline int64_t next_pow2(int64_t x) {
     int64_t p = 1;
     while (p < x) p <<= 1;

@@ -557,7 +557,7 @@ __global__ void __launch_bounds__(kBlockThreads, 2)
                         const int k = o - __shfl_sync(kFull, ex2, owner);
                         const int fo = __shfl_sync(kFull, first_out, owner);
                         if (o < TT) {
-                            const unsigned bit = __fns(ob, 0, k + 1);
+                            const unsigned bit = (unsigned)select_bit(ob, k);
                             const int64_t at = slab_base + fo + k;
                             if (bit < 32u && at < off + n) {
                                 const int c = (wc + owner) * 32 + (int)bit;
@@ -575,6 +575,271 @@ __global__ void __launch_bounds__(kBlockThreads, 2)
             __syncthreads();
         }
         if (tid == 0 && s_written != n) flag_overflow(st, g);
+        __syncthreads();
+    }
+}
+
+// ---- dense tier, rank-indexed (rows whose bitmap fits in shared memory) ----------
+//
+// Per row: (1) a presence bitmap over all ncols columns is built from the
+// products (read before atomicOr); (2) a block-wide prefix of the words'
+// popcounts gives every present column its rank = its position in the
+// output row; (3) C.col is written from the bitmap, coalesced; (4) values are
+// accumulated into a shared array indexed by rank, in passes over groups of
+// consecutive column slabs whose outputs fit the array, and each pass writes
+// its stretch of C.val in order.  Ranks of ascending columns are consecutive,
+// so the accumulation atomics are free of bank conflicts, and a row is walked
+// 1 + (number of value passes) times instead of once per column slab.
+
+// one A entry per lane, the same in every warp (rows with <= 32 entries)
+template <class In, bool kVal>
+struct LaneEntry {
+    bool v;
+    int32_t k;
+    In a;
+    int64_t rs, re;
+    SPG_DEV void load(const DCsr& A, const DCsr& B, int64_t p, bool valid) {
+        v = valid;
+        k = 0;
+        a = In();
+        rs = re = 0;
+        if (!v) return;
+        k = ld_i32(A.col + p);
+        a = load_val<In, kVal>(A.val, p);
+        rs = ld_i64(B.rp + k);
+        re = ld_i64(B.rp + k + 1);
+    }
+    // segment of slabs [s0, s1) (nslabs slabs in the row; sp may be null only
+    // when the range is the whole row)
+    SPG_DEV void range(const int32_t* sp, int sp_stride, int nslabs, int s0, int s1,
+                       int64_t& b, int64_t& e) const {
+        b = e = 0;
+        if (!v) return;
+        b = (s0 == 0) ? rs : rs + __ldg(sp + (int64_t)k * sp_stride + s0);
+        e = (s1 >= nslabs) ? re : rs + __ldg(sp + (int64_t)k * sp_stride + s1);
+    }
+};
+
+// Products of the <= 32 lane entries' segments [b, e) split evenly over the
+// warps: each warp holds the whole 32-entry table in registers.
+template <class In, bool kVal, class Op>
+SPG_DEV void warp_table_walk(const DCsr& B, int64_t b, int64_t e, In a, Op& op) {
+    const int lane = lane_id(), wid = warp_id();
+    const int nwarps = blockDim.x >> 5;
+    const int64_t len = e - b;
+    const int64_t my_end = warp_incl_scan(len);
+    const int64_t excl = my_end - len;
+    const int64_t total = __shfl_sync(kFull, my_end, 31);
+    const int64_t lo_w = total * wid / nwarps, hi_w = total * (wid + 1) / nwarps;
+    for (int64_t t0 = lo_w; t0 < hi_w; t0 += 128) {   // warp-uniform
+        int64_t qv[4];
+        In av[4];
+        bool vv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t t = t0 + 32 * u + lane;
+            vv[u] = t < hi_w;
+            int k = 0;   // entry of product t: number of prefix ends <= t
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int64_t bv = __shfl_sync(kFull, my_end, k + step - 1);
+                if (bv <= t) k += step;
+            }
+            qv[u] = __shfl_sync(kFull, b, k) + (t - __shfl_sync(kFull, excl, k));
+            av[u] = shfl_val<In, kVal>(a, k);
+        }
+        int32_t col[4];
+        In bval[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            col[u] = vv[u] ? ld_i32(B.col + qv[u]) : 0;
+            bval[u] = vv[u] ? load_val<In, kVal>(B.val, qv[u]) : In();
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) op.any(col[u], av[u], bval[u], vv[u]);
+    }
+}
+
+// Products of row entries [a0, a1) restricted to slabs [s0, s1), spread over the CTA.
+template <class In, bool kVal, class Op, int NT>
+SPG_DEV void cta_range_products(const DCsr& A, const DCsr& B, int64_t a0, int64_t a1,
+                                const LaneEntry<In, kVal>& le, bool small, const int32_t* sp,
+                                int sp_stride, int nslabs, int s0, int s1,
+                                BatchSmem<In, NT>& bs, Op& op) {
+    if (small) {
+        int64_t b, e;
+        le.range(sp, sp_stride, nslabs, s0, s1, b, e);
+        warp_table_walk<In, kVal>(B, b, e, le.a, op);
+        __syncthreads();
+        return;
+    }
+    for (int64_t b0 = a0; b0 < a1; b0 += NT) {
+        const int64_t p = b0 + threadIdx.x;
+        LaneEntry<In, kVal> ent;
+        ent.load(A, B, p, p < a1);
+        int64_t b, e;
+        ent.range(sp, sp_stride, nslabs, s0, s1, b, e);
+        cta_walk_segments<In, kVal>(B, b, e - b, ent.a, bs, op);
+    }
+}
+
+struct BitSetOp {
+    uint32_t* bm;
+    template <class In> SPG_DEV void any(int32_t col, In, In, bool valid) {
+        if (!valid) return;
+        const uint32_t bit = 1u << (col & 31);
+        if (!(bm[col >> 5] & bit)) atomicOr(bm + (col >> 5), bit);
+    }
+};
+
+template <class S>
+struct RankAccOp {
+    typename S::Slot* vals;
+    const uint32_t* bm;
+    const int32_t* word_off;
+    int32_t r0;
+    SPG_DEV void any(int32_t col, typename S::In a, typename S::In b, bool valid) {
+        if (!valid) return;
+        const int w = col >> 5;
+        const int r = word_off[w] + __popc(bm[w] & ((1u << (col & 31)) - 1u)) - r0;
+        S::acc(vals + r, a, b);
+    }
+};
+
+constexpr int kRankThreads = 1024;
+
+template <class S>
+__global__ void __launch_bounds__(kRankThreads, 1)
+    k_num_rank(const Prob* __restrict__ probs, int nprob, const int32_t* __restrict__ rows,
+               Counters* ctr, DevStatus* st, const int32_t* __restrict__ sp, int sp_stride,
+               int slab_cols, int bm_words, int cap, const uint32_t* __restrict__ bm_cache,
+               const int32_t* __restrict__ row_slot, int cache_words) {
+    using Slot = typename S::Slot;
+    using In = typename S::In;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Slot* vals = reinterpret_cast<Slot*>(smem_raw);                          // [cap]
+    uint32_t* bm = reinterpret_cast<uint32_t*>(smem_raw + (S::kVal ? (size_t)cap * sizeof(Slot) : 0));
+    int32_t* word_off = reinterpret_cast<int32_t*>(bm + bm_words);           // [words + 1]
+    __shared__ BatchSmem<In, kRankThreads> bs;
+    __shared__ int s_row;
+    __shared__ int s_wsum[kRankThreads / 32];
+    const int lane = lane_id(), wid = warp_id(), nwarps = blockDim.x >> 5;
+    const int tid = threadIdx.x;
+    const int tbeg = ctr->num_bin_off[kTierDense * kSubBins];
+    const int tend = ctr->num_bin_off[(kTierDense + 1) * kSubBins];
+    for (;;) {
+        if (tid == 0) s_row = tbeg + atomicAdd(&ctr->claim[3], 1);
+        __syncthreads();
+        const int r = s_row;
+        if (r >= tend) break;
+        const int64_t g = rows[r];
+        const Prob& P = probs[nprob == 1 ? 0 : find_prob(probs, nprob, g)];
+        const int64_t i = g - P.row_base;
+        const int64_t off = P.c_rp[i];
+        const int64_t n = P.c_rp[i + 1] - off;
+        const int64_t a0 = ld_i64(P.A.rp + i), a1 = ld_i64(P.A.rp + i + 1);
+        const int ncols = (int)P.B.ncols;
+        const int words = (ncols + 31) >> 5;
+        const int nslabs = (ncols + slab_cols - 1) / slab_cols;
+        const bool small = a1 - a0 <= 32;
+        LaneEntry<In, S::kVal> le;
+        if (small) le.load(P.A, P.B, a0 + lane, a0 + lane < a1);
+        // (1) presence bitmap of the whole row: the symbolic phase's copy if it
+        //     kept one, else rebuilt from the products
+        const int slot = row_slot ? row_slot[g] : -1;
+        if (slot >= 0 && words <= cache_words) {
+            const uint4* src = reinterpret_cast<const uint4*>(bm_cache + (int64_t)slot * cache_words);
+            uint4* dst = reinterpret_cast<uint4*>(bm);
+            for (int w = tid; w < (words + 3) / 4; w += blockDim.x) dst[w] = __ldg(src + w);
+            __syncthreads();
+        } else {
+            for (int w = tid; w < words; w += blockDim.x) bm[w] = 0u;
+            __syncthreads();
+            BitSetOp op{bm};
+            cta_range_products<In, S::kVal>(P.A, P.B, a0, a1, le, small, sp, sp_stride, nslabs, 0,
+                                            nslabs, bs, op);
+        }
+        // (2) ranks: exclusive prefix of the words' popcounts.  Warp w scans a
+        //     contiguous block of words, lane l reading word base + l + 32 j
+        //     (no bank conflicts); block offsets come from a scan of the warps.
+        {
+            const int per_warp = ((words + nwarps - 1) / nwarps + 31) & ~31;
+            const int wb = wid * per_warp;
+            int run = 0;
+            for (int j = 0; j < per_warp; j += 32) {
+                const int w = wb + j + lane;
+                const int c = w < words ? __popc(bm[w]) : 0;
+                const int inc = warp_incl_scan(c);
+                if (w < words) word_off[w] = run + inc - c;
+                run += __shfl_sync(kFull, inc, 31);
+            }
+            if (lane == 0) s_wsum[wid] = run;
+            __syncthreads();
+            if (wid == 0) {
+                const int x = lane < nwarps ? s_wsum[lane] : 0;
+                const int xi = warp_incl_scan(x);
+                if (lane < nwarps) s_wsum[lane] = xi - x;
+                if (lane == 31) word_off[words] = xi;
+            }
+            __syncthreads();
+            const int add = s_wsum[wid];
+            for (int j = 0; j < per_warp; j += 32) {
+                const int w = wb + j + lane;
+                if (w < words) word_off[w] += add;
+            }
+            __syncthreads();
+        }
+        const int T = word_off[words];
+        if (T != n) {   // symbolic and numeric disagree: leave the row
+            if (tid == 0) flag_overflow(st, g);
+            __syncthreads();
+            continue;
+        }
+        // (3) C.col from the bitmap: warp w takes a contiguous block of words,
+        //     32 at a time (lane = word); each lane writes its word's columns
+        //     at word_off[w] + 0, 1, ... (the warp's stores stay inside a
+        //     contiguous stretch of C.col)
+        {
+            const int per_warp = ((words + nwarps - 1) / nwarps + 31) & ~31;
+            const int wb = wid * per_warp;
+            for (int j = 0; j < per_warp; j += 32) {
+                const int w = wb + j + lane;
+                if (w < words) {
+                    uint32_t bits = bm[w];
+                    int32_t* dst = P.c_col + off + word_off[w];
+                    const int cbase = w * 32;
+                    while (bits) {
+                        const int b = __ffs(bits) - 1;
+                        bits &= bits - 1u;
+                        *dst++ = cbase + b;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // (4) values, in passes over groups of column slabs that fit `cap` outputs
+        if constexpr (S::kVal) {
+            int s0 = 0;
+            while (s0 < nslabs) {
+                const int r0 = word_off[(s0 * slab_cols) >> 5];
+                int s1 = s0 + 1;
+                while (s1 < nslabs && word_off[min((s1 + 1) * slab_cols, ncols + 31) >> 5] - r0 <= cap)
+                    ++s1;
+                const int r1 = word_off[min(s1 * slab_cols, ncols + 31) >> 5];
+                const int cnt = r1 - r0;
+                if (cnt > 0) {
+                    fill_slots<S>(vals, cnt);
+                    __syncthreads();
+                    RankAccOp<S> op{vals, bm, word_off, r0};
+                    cta_range_products<In, S::kVal>(P.A, P.B, a0, a1, le, small, sp, sp_stride,
+                                                    nslabs, s0, s1, bs, op);
+                    typename S::Out* cv = reinterpret_cast<typename S::Out*>(P.c_val) + off + r0;
+                    for (int t = tid; t < cnt; t += blockDim.x) cv[t] = S::out(vals[t]);
+                    __syncthreads();
+                }
+                s0 = s1;
+            }
+        }
         __syncthreads();
     }
 }
@@ -680,7 +945,6 @@ struct NumericLaunch {
             e = cudaFuncSetAttribute(k_num_dense<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem);
             if (e != cudaSuccess) { err = e; return; }
-            const int grid = occupancy_grid((const void*)k_num_dense<S>, kBlockThreads, smem, *dev);
             const int nslabs = (int)((max_ncols + slab - 1) / slab);
             const int32_t* sp = nullptr;
             if (nprob == 1 && w->slab_ptr &&
@@ -688,9 +952,34 @@ struct NumericLaunch {
                 k_slab_ptr<<<dev->sms * 8, 256, 0, st>>>(B0, (int)slab, nslabs, w->slab_ptr, w->ctr);
                 sp = w->slab_ptr;
             }
-            k_num_dense<S><<<grid, kBlockThreads, smem, st>>>(w->probs, nprob, w->rows_num, w->ctr,
-                                                              w->status, w->cursor, (int)slab, sp,
-                                                              nslabs + 1);
+            // rank-indexed kernel when the row bitmap, its prefix and a value
+            // array of at least one slab fit in shared memory
+            const int64_t bm_words = (max_ncols + 1023) / 1024 * 32;
+            const size_t fixed = (size_t)bm_words * 8 + 16;
+            const size_t budget = 200 * 1024 - sizeof(BatchSmem<typename S::In, kRankThreads>) + 12 * 1024;
+            int64_t cap = 0;
+            if (fixed < budget)
+                cap = S::kVal ? (int64_t)((budget - fixed) / sizeof(typename S::Slot)) : 0;
+            if (cap > (int64_t)1 << 30) cap = (int64_t)1 << 30;
+            const bool rank_ok = nprob == 1 && fixed < budget && (sp != nullptr || nslabs == 1) &&
+                                 (!S::kVal || cap >= slab) && max_ncols < INT32_MAX;
+            if (rank_ok) {
+                const size_t rsmem = (S::kVal ? (size_t)cap * sizeof(typename S::Slot) : 0) + fixed;
+                e = cudaFuncSetAttribute(k_num_rank<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)rsmem);
+                if (e != cudaSuccess) { err = e; return; }
+                const int grid = occupancy_grid((const void*)k_num_rank<S>, kRankThreads, rsmem, *dev);
+                const bool cached = w->bm_cache && w->bm_cache_words >= bm_words;
+                k_num_rank<S><<<grid, kRankThreads, rsmem, st>>>(
+                    w->probs, nprob, w->rows_num, w->ctr, w->status, sp, nslabs + 1, (int)slab,
+                    (int)bm_words, (int)cap, cached ? w->bm_cache : nullptr,
+                    cached ? w->row_slot : nullptr, (int)w->bm_cache_words);
+            } else {
+                const int grid = occupancy_grid((const void*)k_num_dense<S>, kBlockThreads, smem, *dev);
+                k_num_dense<S><<<grid, kBlockThreads, smem, st>>>(w->probs, nprob, w->rows_num, w->ctr,
+                                                                  w->status, w->cursor, (int)slab, sp,
+                                                                  nslabs + 1);
+            }
         }
         {   // block tier
             int64_t T = next_pow2(2 * t->num_block_max_nnz);

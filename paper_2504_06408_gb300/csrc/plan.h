@@ -23,6 +23,7 @@ struct Tuning {
     int64_t num_block_max_nnz;
     int64_t dense_slab_cols;
     int64_t sym_slab_cols;
+    int64_t bitmap_cache_bytes;   // < 0: no bitmap cache
 };
 
 // Per-semiring defaults chosen so that every tier's shared memory fits.
@@ -43,13 +44,15 @@ struct Counters {
     int32_t num_bin_off[kNumBins + 1];
     int32_t num_bin_cursor[kNumBins];
     int32_t claim[16];                  // per-kernel dynamic row counters
+    int32_t bm_next;                    // next free bitmap cache slot
     unsigned long long products;        // sum of ub over all rows
     int64_t nnz[kMaxProb];              // per-product nnz(C)
 };
 
 struct WsLayout {
     size_t status, counters, probs, ub, cnt, rows_sym, rows_num, scan_part, cursor, slab_ptr,
-        slab_ptr_bytes, total;
+        slab_ptr_bytes, row_slot, bm_cache, bm_cache_bytes, total;
+    int64_t bm_cache_words, bm_cache_slots;
     int64_t R;          // flat rows
     int64_t E;          // flat entries of A (cursor array length)
 };
@@ -57,7 +60,7 @@ struct WsLayout {
 // R flat rows, E flat entries of A; nrows_b / ncols_b / nnz_b of B and the
 // numeric dense slab width size the optional slab-start table
 WsLayout ws_layout(int64_t R, int64_t E, int64_t nrows_b = 0, int64_t ncols_b = 0,
-                   int64_t nnz_b = 0, int64_t slab_cols = 0);
+                   int64_t nnz_b = 0, int64_t slab_cols = 0, int64_t cache_bytes = 0);
 
 struct WsPtrs {
     DevStatus* status;
@@ -71,6 +74,10 @@ struct WsPtrs {
     int32_t* cursor;
     int32_t* slab_ptr;       // slab starts of B's rows (numeric dense tier)
     size_t slab_ptr_bytes;
+    uint32_t* bm_cache;      // row bitmaps kept by the symbolic dense tier, or null
+    int64_t bm_cache_words;  // words per cached bitmap
+    int64_t bm_cache_slots;  // cached bitmaps that fit
+    int32_t* row_slot;       // per flat row: cache slot or -1
 };
 WsPtrs ws_ptrs(void* ws, const WsLayout& L);
 

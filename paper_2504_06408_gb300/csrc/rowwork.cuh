@@ -178,20 +178,22 @@ SPG_DEV void chunk_products(const DCsr& A, const DCsr& B, int64_t p0, int64_t p_
 constexpr int kBatch = 512;
 constexpr int kCountShift = 50;   // scan packs (entry count << 50) + product count
 
-template <class In>
+template <class In, int NT = kBatch>
 struct BatchSmem {
-    int64_t beg[kBatch];         // compacted non-empty segments
-    int64_t off[kBatch + 1];     // exclusive scan of their lengths
-    In a[kBatch];
-    int64_t wsum[kBatch / 32];
+    static constexpr int kN = NT;  // entries per batch = threads of the CTA
+    int64_t beg[NT];               // compacted non-empty segments
+    int64_t off[NT + 1];           // exclusive scan of their lengths
+    In a[NT];
+    int64_t wsum[NT / 32];
     int nseg;
 };
 
 // All threads of the CTA call this with their own segment [beg, beg + len)
 // and A value (len 0 for none).  Ends with __syncthreads.
-template <class In, bool kVal, class Op>
-SPG_DEV void cta_walk_segments(const DCsr& B, int64_t beg, int64_t len, In a, BatchSmem<In>& bs,
-                               Op& op) {
+template <class In, bool kVal, class Op, int NT>
+SPG_DEV void cta_walk_segments(const DCsr& B, int64_t beg, int64_t len, In a,
+                               BatchSmem<In, NT>& bs, Op& op) {
+    constexpr int kBatch = NT;
     const int lane = lane_id(), wid = warp_id();
     const int tid = threadIdx.x;
     const int nwarps = kBatch / 32;
@@ -349,10 +351,10 @@ struct RowEntry {
 };
 
 // Products of row entries [a0, a1) restricted to the slab, spread over the CTA.
-template <class In, bool kVal, class Op>
+template <class In, bool kVal, class Op, int NT>
 SPG_DEV void cta_row_products(const DCsr& A, const DCsr& B, int64_t a0, int64_t a1,
-                              int64_t flat_base, const Slab& slab, BatchSmem<In>& bs, Op& op) {
-    for (int64_t b0 = a0; b0 < a1; b0 += kBatch) {
+                              int64_t flat_base, const Slab& slab, BatchSmem<In, NT>& bs, Op& op) {
+    for (int64_t b0 = a0; b0 < a1; b0 += NT) {
         const int64_t p = b0 + threadIdx.x;
         int64_t beg = 0, end = 0;
         In a = In();

@@ -225,11 +225,12 @@ struct BitOrOp {
 
 __global__ void __launch_bounds__(kBlockThreads)
     k_sym_dense(const Prob* __restrict__ probs, int nprob, const int32_t* __restrict__ rows,
-                Counters* ctr, int64_t* __restrict__ cnt, int32_t* cursor, int slab_cols) {
+                Counters* ctr, int64_t* __restrict__ cnt, int32_t* cursor, int slab_cols,
+                uint32_t* bm_cache, int32_t* row_slot, int64_t cache_words, int64_t cache_slots) {
     extern __shared__ uint32_t smem_u32[];
     uint32_t* bm = smem_u32;
     __shared__ BatchSmem<char> bs;
-    __shared__ int s_row;
+    __shared__ int s_row, s_slot;
     __shared__ unsigned long long s_tot;
     const int lane = lane_id();
     const int beg = ctr->sym_bin_off[kTierDense * kSubBins];
@@ -258,6 +259,20 @@ __global__ void __launch_bounds__(kBlockThreads)
             const Slab slab{lo, hi, s == 0, s == nslabs - 1, nslabs == 1, cursor, nullptr, 0, s};
             BitOrOp op{bm, lo};
             cta_row_products<char, false>(P.A, P.B, a0, a1, P.nnz_base + a0, slab, bs, op);
+            if (nslabs == 1 && cache_slots > 0 && words <= cache_words) {
+                // keep the row's bitmap for the numeric phase while cache slots last
+                if (threadIdx.x == 0) {
+                    const int sl = atomicAdd(&ctr->bm_next, 1);
+                    s_slot = sl < cache_slots ? sl : -1;
+                    row_slot[g] = s_slot;
+                }
+                __syncthreads();
+                if (s_slot >= 0) {
+                    uint4* dst = reinterpret_cast<uint4*>(bm_cache + (int64_t)s_slot * cache_words);
+                    const uint4* src = reinterpret_cast<const uint4*>(bm);
+                    for (int w = threadIdx.x; w < (words + 3) / 4; w += blockDim.x) dst[w] = src[w];
+                }
+            }
             int mine = 0;
             for (int w = threadIdx.x; w < words; w += blockDim.x) mine += __popc(bm[w]);
             mine = warp_sum(mine);
@@ -423,7 +438,8 @@ cudaError_t launch_symbolic(const WsPtrs& w, int nprob, int64_t R, const Tuning&
         if (e != cudaSuccess) return e;
         const int grid = occupancy((const void*)k_sym_dense, kBlockThreads, smem, dev);
         k_sym_dense<<<grid, kBlockThreads, smem, st>>>(w.probs, nprob, w.rows_sym, w.ctr, w.cnt,
-                                                       w.cursor, (int)slab);
+                                                       w.cursor, (int)slab, w.bm_cache, w.row_slot,
+                                                       w.bm_cache_words, w.bm_cache_slots);
     }
     {
         int64_t T = next_pow2(2 * t.sym_block_max_ub);
