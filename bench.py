@@ -1,0 +1,399 @@
+#!/usr/bin/env python3
+"""Benchmark of the semiring SpGEMM hot path on GB300.
+
+Workload: C = A * A over the min-plus FP32 semiring for a symmetric R-MAT
+graph of scale 18 (262,144 vertices, edge factor 16, a, b, c, d = .57, .19,
+.19, .05, self loops and duplicates removed, weights U[1, 100), seed 1): a
+synthetic stand-in of the paper's graph workloads (Table 2 "rmat").
+
+One step = the whole path on resident device inputs: row analysis and
+binning, symbolic phase, scan into C's row pointers, numeric phase with sorted
+compacted output (spgemm_symbolic + spgemm_numeric).  value = 2 * products /
+time (GFLOPS).  The inputs (61 MB) fit in L2, so a 256 MiB buffer is written
+before every timed step to flush it.
+
+Also reported: e2e (the same metric through the host-memory C ABI call,
+host->device copies of A and the device->host copy of C inside the timed
+region), the roofline of the dominant kernel, the CPU oracle on a bounded row
+sample (cpu_baseline), clocks sampled during the timed steps, and the number
+of library kernel launches.
+
+--impl reference runs the CPU oracle (the plain sorted-map definition) as the
+reference arm on a bounded row sample per step.
+
+Multi-GPU: one process per GPU (torchrun); every rank runs the full product
+(independent replicas, no data-path collective), value = total products of
+all ranks / max time over ranks ("scaling": "weak").
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "semiring SpGEMM GFLOPS (2*products/s), R-MAT scale 18 A^2 over min-plus FP32"
+UNIT = "GFLOPS"
+SCALE = 18
+L2_FLUSH_BYTES = 256 << 20
+
+
+def workload_config(P=None, nnz_c=None, nnz_a=None):
+    cfg = {"workload": "R-MAT scale 18 (262,144 vertices, edge factor 16, a=.57 b=.19 c=.19 "
+                       "d=.05), symmetrised, self-loops and duplicates removed, FP32 weights "
+                       "U[1,100), seed 1; C = A*A over min-plus FP32",
+           "semiring": "min_plus_f32", "n": 1 << SCALE,
+           "l2": "256 MiB buffer written before every timed step"}
+    if nnz_a is not None:
+        cfg["nnz_A"] = int(nnz_a)
+    if P is not None:
+        cfg["products"] = int(P)
+    if nnz_c is not None:
+        cfg["nnz_C"] = int(nnz_c)
+    return cfg
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def row_stats(A, c_rp):
+    """Per-row products (ub), nnz(A_i) and nnz(C_i) on the host (metrics only)."""
+    deg = np.diff(A.rp)
+    blen = deg  # B = A
+    per_entry = blen[A.col.astype(np.int64)]
+    ub = np.add.reduceat(np.r_[per_entry, 0], np.minimum(A.rp[:-1], A.col.size)) * (deg > 0)
+    cnt = np.diff(c_rp)
+    return ub.astype(np.int64), deg.astype(np.int64), cnt.astype(np.int64)
+
+
+def traffic_from_profiles(kernel_src_hash):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "num_rank_minplus_rmat18_traffic.txt")
+    try:
+        kv = {}
+        for line in open(path):
+            if "=" in line and not line.startswith("#"):
+                k, v = line.strip().split("=", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("source_sha256") == kernel_src_hash:
+            return int(kv["traffic_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2504_06408_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, name), "rb").read())
+    return h.hexdigest()
+
+
+def cpu_oracle_sample(A, target_s=12.0, seed=7):
+    """Time the CPU oracle on a random row sample sized for ~target_s seconds."""
+    import oracle
+    ub, deg, _ = row_stats(A, np.zeros(A.nrows + 1, np.int64))
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(np.nonzero(ub > 0)[0])
+    threads = oracle.default_threads()
+    # calibrate on a small sample
+    csum = np.cumsum(ub[order])
+    k = int(np.searchsorted(csum, 2e7)) + 1
+    t0 = time.perf_counter()
+    oracle.spgemm(oracle.SR_MP_F32, A, A, rows=order[:k], threads=threads)
+    dt = time.perf_counter() - t0
+    rate = csum[k - 1] / max(dt, 1e-3)
+    want = rate * target_s
+    k2 = int(np.searchsorted(csum, want)) + 1
+    k2 = min(k2, order.size)
+    rows = np.sort(order[:k2])
+    P = int(ub[rows].sum())
+    t0 = time.perf_counter()
+    oracle.spgemm(oracle.SR_MP_F32, A, A, rows=rows, threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": 2.0 * P / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{rows.size} random non-empty rows of the same product "
+                      f"({P} of {int(ub.sum())} products), {dt:.1f} s wall"}, dt, P
+
+
+def run_reference(args, rank):
+    """Reference arm: the CPU oracle on a bounded row sample per step."""
+    if rank != 0:
+        return 0
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    from paper_2504_06408_gb300 import inputs as I
+    A = I.rmat(SCALE, dtype=np.float32, seed=1)
+    ub, _, _ = row_stats(A, np.zeros(A.nrows + 1, np.int64))
+    threads = oracle.default_threads()
+    rng = np.random.default_rng(11)
+    nz = np.nonzero(ub > 0)[0]
+    # per-step sample sized for ~6 s of oracle work
+    probe = np.sort(rng.choice(nz, 2000, replace=False))
+    t0 = time.perf_counter()
+    oracle.spgemm(oracle.SR_MP_F32, A, A, rows=probe, threads=threads)
+    rate = ub[probe].sum() / max(time.perf_counter() - t0, 1e-3)
+    times, prods = [], []
+    for step in range(args.warmup + args.steps):
+        order = rng.permutation(nz)
+        csum = np.cumsum(ub[order])
+        k = int(np.searchsorted(csum, rate * 6.0)) + 1
+        rows = np.sort(order[:k])
+        t0 = time.perf_counter()
+        oracle.spgemm(oracle.SR_MP_F32, A, A, rows=rows, threads=threads)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+            prods.append(int(ub[rows].sum()))
+    value = 2.0 * sum(prods) / sum(times) / 1e9
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": workload_config(P=int(ub.sum()), nnz_a=A.nnz),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                            "sample": f"per step a random row sample of ~6 s "
+                                      f"({int(np.mean(prods))} products on average)"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_info()
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2504_06408_gb300 import inputs as I
+    from paper_2504_06408_gb300 import spgemm as api
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    sr = api.MIN_PLUS_F32
+    A = I.rmat(SCALE, dtype=np.float32, seed=1)
+    h = api.Handle()
+    dA = api.DeviceCSR.from_host(A, val_dtype=np.float32)
+    ws = torch.empty(h.workspace_size(sr, dA, dA), dtype=torch.uint8, device="cuda")
+    c_rp = torch.empty(A.nrows + 1, dtype=torch.int64, device="cuda")
+    nnz = h.symbolic(sr, dA, dA, c_rp, ws)
+    stats = h.stats()
+    P = stats["products"]
+    c_col = torch.empty(nnz, dtype=torch.int32, device="cuda")
+    c_val = torch.empty(nnz, dtype=torch.float32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        h.symbolic(sr, dA, dA, c_rp, ws)
+        h.numeric(sr, dA, dA, c_rp, c_col, c_val, ws)
+
+    for _ in range(args.warmup):
+        step()
+    h.check(ws)
+    torch.cuda.synchronize()
+    h.set_timing(True)
+    times, dense_ms, launches = [], [], 0
+    sampler = ClockSampler(torch.cuda.current_device())
+    with sampler:
+        barrier()
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h.symbolic(sr, dA, dA, c_rp, ws)
+            launches += h.stats()["launches"]
+            h.numeric(sr, dA, dA, c_rp, c_col, c_val, ws)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            launches += h.stats()["launches"]
+            dense_ms.append(h.stage_times()["num_dense"])
+            times.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+        barrier()
+    h.set_timing(False)
+    h.check(ws)
+    total_ms = sum(times)
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * 2.0 * P / (ms_per_step * 1e-3) / 1e9
+
+    # roofline of the dominant kernel (numeric dense tier) by the Gustavson
+    # traffic model restricted to the rows it processes
+    hc_rp = c_rp.cpu().numpy()
+    ub, deg, cnt = row_stats(A, hc_rp)
+    dense = cnt > 2048      # numeric dense tier: nnz(C_i) above the block-tier limit
+    s_in, s_out = 4, 4
+    t_alg = (16 * int(dense.sum()) + int(deg[dense].sum()) * (4 + s_in) + 8 * int(deg[dense].sum())
+             + int(ub[dense].sum()) * (4 + s_in) + int(cnt[dense].sum()) * (4 + s_out))
+    d_ms = statistics.mean(dense_ms)
+    achieved = t_alg / (d_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = traffic_from_profiles(kernel_source_hash())
+    roofline = {"bound": "hbm", "kernel": "k_num_rank<SrMpF32> (numeric dense tier)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_kind": peak_kind, "traffic": traffic, "kernel_ms": d_ms,
+                "algorithmic_bytes": t_alg}
+
+    # whole-step fraction of the HBM roofline by the same model
+    t_alg_all = (16 * A.nrows + A.nnz * (8 + 8) + P * 8 + nnz * 8)
+
+    # e2e through the host-memory C ABI call: H2D of A, D2H of C every step
+    e2e = None
+    if args.e2e_steps > 0:
+        pin = lambda n, dt: torch.empty(n, dtype=dt, pin_memory=True).numpy()
+        hA = I.CSR(A.nrows, A.ncols, pin(A.nrows + 1, torch.int64), pin(A.nnz, torch.int32),
+                   pin(A.nnz, torch.float32))
+        hA.rp[:] = A.rp
+        hA.col[:] = A.col
+        hA.val[:] = A.val
+        out = {"rp": pin(A.nrows + 1, torch.int64), "col": pin(nnz, torch.int32),
+               "val": pin(nnz * 4, torch.uint8)}
+        h2 = api.Handle()
+        h2.host_multiply(sr, hA, hA, out=out)         # warm-up (device buffers allocated)
+        et = []
+        for _ in range(args.e2e_steps):
+            barrier()
+            t0 = time.perf_counter()
+            _, _, _, n2 = h2.host_multiply(sr, hA, hA, out=out)
+            et.append(time.perf_counter() - t0)
+        assert n2 == nnz
+        e_s = statistics.mean(et)
+        if dist is not None:
+            t = torch.tensor([e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_s = float(t.item())
+        h2d = (A.nrows + 1) * 8 + A.nnz * 8
+        d2h = (A.nrows + 1) * 8 + nnz * 8
+        e2e = {"value": world * 2.0 * P / e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e_s}
+        del h2
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu, _, _ = cpu_oracle_sample(A)
+
+    if rank == 0:
+        res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic",
+               "config": dict(workload_config(P=P, nnz_c=nnz, nnz_a=A.nnz),
+                              parallelism=f"replicas x{world}"),
+               "hbm_roofline_frac_step": (t_alg_all / (ms_per_step * 1e-3) / 1e9) / peak,
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+               "clocks": sampler.summary(), "gpu_launches": launches,
+               "step_ms": times}
+        print(json.dumps(res), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

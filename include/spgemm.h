@@ -100,7 +100,8 @@ typedef struct {
     int64_t products;           /* P = sum_i sum_{k in A_i} nnz(B_k)                      */
     int64_t nnz_c;              /* nnz(C)                                                */
     int64_t rows_per_tier[4];   /* symbolic rows: dense, block, warp, empty              */
-    int64_t reserved[6];
+    int64_t launches;           /* kernels launched by the last symbolic / numeric call   */
+    int64_t reserved[5];
 } spg_stats;
 
 typedef struct spg_handle spg_handle;
@@ -163,6 +164,42 @@ spg_status spgemm_check(spg_handle* handle, void* workspace, void* stream);
  */
 spg_status spgemm_validate_csr(spg_handle* handle, const spg_csr* M, void* workspace,
                                size_t workspace_bytes, void* stream);
+
+/*
+ * Optional per-stage timing with CUDA events recorded on the call's stream
+ * (stages: see spgemm_get_stage_times).  enable = 0 turns it off.
+ */
+spg_status spgemm_set_timing(spg_handle* handle, int enable);
+
+/*
+ * Milliseconds per stage of the last spgemm_symbolic or spgemm_numeric call
+ * (waits for its last event).  ms must hold SPG_STAGE_COUNT floats, indexed:
+ *  1 analysis+binning  2 symbolic dense  3 symbolic block  4 symbolic warp
+ *  5 scan              6 numeric binning 7 slab table      8 numeric dense
+ *  9 numeric block    10 numeric warp   11 stage merge     (0 unused)
+ */
+#define SPG_STAGE_COUNT 12
+spg_status spgemm_get_stage_times(spg_handle* handle, float* ms, int n);
+
+/*
+ * Host-memory API: A and B in HOST memory (pinned memory makes the copies
+ * asynchronous and fast; pageable memory works).  The handle uploads them
+ * to device buffers it owns (kept and reused across calls, freed by
+ * spgemm_destroy), runs spgemm_symbolic, and copies C's row pointers back.
+ *   c_row_ptr : HOST int64 [A.nrows + 1], written;  c_nnz : HOST, written.
+ * If A and B are the same host arrays, they are uploaded once.
+ * Synchronous (returns when the host copies are complete).
+ */
+spg_status spgemm_host_symbolic(spg_handle* handle, spg_semiring sr, const spg_csr* A,
+                                const spg_csr* B, int64_t* c_row_ptr, int64_t* c_nnz);
+
+/*
+ * Numeric phase of the inputs of the last spgemm_host_symbolic call on this
+ * handle (same semiring); copies C.col and C.val to HOST memory.
+ *   c_col : HOST int32 [nnz(C)];  c_val : HOST [nnz(C)] of the output type.
+ * Synchronous; returns kernel-detected errors (as spgemm_check).
+ */
+spg_status spgemm_host_numeric(spg_handle* handle, spg_semiring sr, int32_t* c_col, void* c_val);
 
 /*
  * CSR transpose T = A^T with values carried (Section 3.1: the identity

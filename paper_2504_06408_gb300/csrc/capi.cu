@@ -14,6 +14,12 @@ using namespace spg;
 
 static constexpr size_t kPinnedBytes = 16384;
 
+// Device buffers owned by the handle for the host-memory API.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
 struct spg_handle {
     spg_tuning user;               // user overrides (0 = default)
     DevInfo dev;
@@ -21,6 +27,15 @@ struct spg_handle {
     std::string err;
     spg_stats stats;
     void* pinned;                  // small pinned staging buffer for device counters
+    int64_t launches = 0;          // kernels launched by the last symbolic/numeric call
+    StageTimer timer;
+    bool timer_events = false;
+    // host-memory API state
+    cudaStream_t hstream = nullptr;
+    DevBuf a_rp, a_col, a_val, b_rp, b_col, b_val, ws, c_rp, c_col, c_val;
+    spg_csr hA{}, hB{};            // device descriptors of the last host-API inputs
+    int host_sr = -1;
+    int64_t host_nnz = -1;
 };
 
 namespace spg {
@@ -239,6 +254,8 @@ spg_status spgemm_create(spg_handle** handle) {
         delete h;
         return SPG_ERR_CUDA;
     }
+    h->dev.launches = &h->launches;
+    h->dev.timer = &h->timer;
     *handle = h;
     return SPG_OK;
 }
@@ -246,7 +263,43 @@ spg_status spgemm_create(spg_handle** handle) {
 spg_status spgemm_destroy(spg_handle* h) {
     if (!h) return SPG_ERR_INVALID_ARG;
     if (h->pinned) cudaFreeHost(h->pinned);
+    if (h->timer_events)
+        for (int i = 0; i < StageTimer::kMax; ++i) cudaEventDestroy(h->timer.ev[i]);
+    for (DevBuf* b : {&h->a_rp, &h->a_col, &h->a_val, &h->b_rp, &h->b_col, &h->b_val, &h->ws,
+                      &h->c_rp, &h->c_col, &h->c_val})
+        if (b->p) cudaFree(b->p);
+    if (h->hstream) cudaStreamDestroy(h->hstream);
     delete h;
+    return SPG_OK;
+}
+
+spg_status spgemm_set_timing(spg_handle* h, int enable) {
+    if (!h) return SPG_ERR_INVALID_ARG;
+    if (enable && !h->timer_events) {
+        for (int i = 0; i < StageTimer::kMax; ++i) {
+            cudaError_t e = cudaEventCreate(&h->timer.ev[i]);
+            if (e != cudaSuccess) return cuda_fail(h, e, "event create");
+        }
+        h->timer_events = true;
+    }
+    h->timer.on = enable != 0;
+    h->timer.n = 0;
+    return SPG_OK;
+}
+
+spg_status spgemm_get_stage_times(spg_handle* h, float* ms, int n) {
+    if (!h || !ms || n < kStCount) return SPG_ERR_INVALID_ARG;
+    for (int i = 0; i < kStCount; ++i) ms[i] = 0.f;
+    StageTimer& t = h->timer;
+    if (!h->timer_events || t.n == 0) return SPG_OK;
+    cudaError_t e = cudaEventSynchronize(t.ev[t.n - 1]);
+    if (e != cudaSuccess) return cuda_fail(h, e, "event sync");
+    for (int i = 1; i < t.n; ++i) {
+        float d = 0.f;
+        e = cudaEventElapsedTime(&d, t.ev[i - 1], t.ev[i]);
+        if (e != cudaSuccess) return cuda_fail(h, e, "event time");
+        ms[t.tag[i]] += d;
+    }
     return SPG_OK;
 }
 
@@ -268,6 +321,7 @@ spg_status spgemm_get_tuning(const spg_handle* h, spg_tuning* t) {
 spg_status spgemm_get_stats(const spg_handle* h, spg_stats* s) {
     if (!h || !s) return SPG_ERR_INVALID_ARG;
     *s = h->stats;
+    s->launches = h->launches;
     return SPG_OK;
 }
 
@@ -307,6 +361,8 @@ spg_status spgemm_symbolic(spg_handle* h, spg_semiring sr, const spg_csr* A, con
         return fail(h, SPG_ERR_WORKSPACE, "workspace needs %zu bytes", L.total);
     cudaStream_t st = (cudaStream_t)stream;
     const WsPtrs w = ws_ptrs(workspace, L);
+    h->launches = 0;
+    h->timer.n = 0;
     cudaError_t e = cudaMemsetAsync(workspace, 0, L.probs, st);   // status + counters
     if (e == cudaSuccess && w.row_slot)
         e = cudaMemsetAsync(w.row_slot, 0xff, sizeof(int32_t) * (size_t)A->nrows, st);
@@ -314,11 +370,11 @@ spg_status spgemm_symbolic(spg_handle* h, spg_semiring sr, const spg_csr* A, con
     ProbTable* tab = new ProbTable;
     std::memset(tab, 0, sizeof *tab);
     tab->p[0] = Prob{to_dcsr(A), to_dcsr(B), c_row_ptr, nullptr, nullptr, 0, 0};
-    e = launch_write_probs(*tab, 1, w, st);
+    e = launch_write_probs(*tab, 1, w, h->dev, st);
     delete tab;
-    if (e == cudaSuccess) e = launch_analyze(w, 1, A->nrows, t, st);
+    if (e == cudaSuccess) e = launch_analyze(w, 1, A->nrows, t, h->dev, st);
     if (e == cudaSuccess) e = launch_symbolic(w, 1, A->nrows, t, B->ncols, h->dev, st);
-    if (e == cudaSuccess) e = launch_scan_rowptr(w, 1, A->nrows, st);
+    if (e == cudaSuccess) e = launch_scan_rowptr(w, 1, A->nrows, h->dev, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "symbolic launch");
     // bring back nnz, products, bin counts and the status in one copy
     Counters* hc = (Counters*)((char*)h->pinned);
@@ -349,10 +405,12 @@ spg_status spgemm_numeric(spg_handle* h, spg_semiring sr, const spg_csr* A, cons
         return fail(h, SPG_ERR_WORKSPACE, "workspace needs %zu bytes", L.total);
     cudaStream_t st = (cudaStream_t)stream;
     const WsPtrs w = ws_ptrs(workspace, L);
+    h->launches = 0;
+    h->timer.n = 0;
     ProbTable* tab = new ProbTable;
     std::memset(tab, 0, sizeof *tab);
     tab->p[0] = Prob{to_dcsr(A), to_dcsr(B), const_cast<int64_t*>(c_row_ptr), c_col, c_val, 0, 0};
-    cudaError_t e = launch_write_probs(*tab, 1, w, st);
+    cudaError_t e = launch_write_probs(*tab, 1, w, h->dev, st);
     delete tab;
     if (e == cudaSuccess)
         e = launch_numeric(sr, w, to_dcsr(B), 1, A->nrows, t, B->ncols, h->dev, st);
@@ -395,6 +453,93 @@ spg_status spgemm_transpose(spg_handle* h, const spg_csr* A, int value_bytes,
                                      workspace, h->dev, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "transpose");
     return SPG_OK;
+}
+
+// ---- host-memory API ------------------------------------------------------------
+
+static cudaError_t ensure(DevBuf& b, size_t bytes) {
+    if (bytes <= b.bytes && b.p) return cudaSuccess;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    const size_t n = bytes ? bytes : 16;
+    cudaError_t e = cudaMalloc(&b.p, n);
+    if (e == cudaSuccess) b.bytes = n;
+    return e;
+}
+
+static cudaError_t upload(DevBuf& b, const void* src, size_t bytes, cudaStream_t st) {
+    cudaError_t e = ensure(b, bytes);
+    if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(b.p, src, bytes, cudaMemcpyHostToDevice, st);
+    return e;
+}
+
+spg_status spgemm_host_symbolic(spg_handle* h, spg_semiring sr, const spg_csr* A,
+                                const spg_csr* B, int64_t* c_row_ptr, int64_t* c_nnz) {
+    spg_status s = check_pair(h, sr, A, B, false);
+    if (s != SPG_OK) return s;
+    if (!c_row_ptr || !c_nnz) return fail(h, SPG_ERR_INVALID_ARG, "c_row_ptr / c_nnz is NULL");
+    cudaError_t e = cudaSuccess;
+    if (!h->hstream) e = cudaStreamCreateWithFlags(&h->hstream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(h, e, "stream");
+    cudaStream_t st = h->hstream;
+    const int vb = in_bytes(sr);
+    const bool same = A->row_ptr == B->row_ptr && A->col == B->col && A->val == B->val &&
+                      A->nrows == B->nrows && A->nnz == B->nnz;
+    e = upload(h->a_rp, A->row_ptr, sizeof(int64_t) * (size_t)(A->nrows + 1), st);
+    if (e == cudaSuccess) e = upload(h->a_col, A->col, sizeof(int32_t) * (size_t)A->nnz, st);
+    if (e == cudaSuccess && vb) e = upload(h->a_val, A->val, (size_t)vb * (size_t)A->nnz, st);
+    if (!same) {
+        if (e == cudaSuccess) e = upload(h->b_rp, B->row_ptr, sizeof(int64_t) * (size_t)(B->nrows + 1), st);
+        if (e == cudaSuccess) e = upload(h->b_col, B->col, sizeof(int32_t) * (size_t)B->nnz, st);
+        if (e == cudaSuccess && vb) e = upload(h->b_val, B->val, (size_t)vb * (size_t)B->nnz, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "upload");
+    h->hA = spg_csr{A->nrows, A->ncols, A->nnz, (const int64_t*)h->a_rp.p,
+                    (const int32_t*)h->a_col.p, vb ? h->a_val.p : nullptr};
+    h->hB = same ? h->hA
+                 : spg_csr{B->nrows, B->ncols, B->nnz, (const int64_t*)h->b_rp.p,
+                           (const int32_t*)h->b_col.p, vb ? h->b_val.p : nullptr};
+    size_t wsb = 0;
+    s = spgemm_workspace_size(h, sr, &h->hA, &h->hB, &wsb);
+    if (s != SPG_OK) return s;
+    e = ensure(h->ws, wsb);
+    if (e == cudaSuccess) e = ensure(h->c_rp, sizeof(int64_t) * (size_t)(A->nrows + 1));
+    if (e != cudaSuccess) return cuda_fail(h, e, "allocation");
+    s = spgemm_symbolic(h, sr, &h->hA, &h->hB, (int64_t*)h->c_rp.p, c_nnz, h->ws.p, h->ws.bytes, st);
+    if (s != SPG_OK) return s;
+    e = cudaMemcpyAsync(c_row_ptr, h->c_rp.p, sizeof(int64_t) * (size_t)(A->nrows + 1),
+                        cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "row_ptr download");
+    h->host_sr = sr;
+    h->host_nnz = *c_nnz;
+    return SPG_OK;
+}
+
+spg_status spgemm_host_numeric(spg_handle* h, spg_semiring sr, int32_t* c_col, void* c_val) {
+    if (!h) return SPG_ERR_INVALID_ARG;
+    if (h->host_sr != (int)sr || h->host_nnz < 0)
+        return fail(h, SPG_ERR_INVALID_ARG, "call spgemm_host_symbolic with this semiring first");
+    const int64_t nnz = h->host_nnz;
+    const int ob = out_bytes(sr);
+    if (nnz > 0 && (!c_col || (ob && !c_val)))
+        return fail(h, SPG_ERR_INVALID_ARG, "c_col / c_val is NULL");
+    cudaStream_t st = h->hstream;
+    cudaError_t e = ensure(h->c_col, sizeof(int32_t) * (size_t)nnz);
+    if (e == cudaSuccess && ob) e = ensure(h->c_val, (size_t)ob * (size_t)nnz);
+    if (e != cudaSuccess) return cuda_fail(h, e, "allocation");
+    spg_status s = spgemm_numeric(h, sr, &h->hA, &h->hB, (const int64_t*)h->c_rp.p,
+                                  (int32_t*)h->c_col.p, ob ? h->c_val.p : nullptr, h->ws.p,
+                                  h->ws.bytes, st);
+    if (s != SPG_OK) return s;
+    if (nnz > 0) {
+        e = cudaMemcpyAsync(c_col, h->c_col.p, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess && ob)
+            e = cudaMemcpyAsync(c_val, h->c_val.p, (size_t)ob * (size_t)nnz, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "download");
+    }
+    return spgemm_check(h, h->ws.p, st);
 }
 
 spg_status spgemm_validate_csr(spg_handle* h, const spg_csr* M, void* workspace,

@@ -950,8 +950,10 @@ struct NumericLaunch {
             if (nprob == 1 && w->slab_ptr &&
                 (size_t)(B0.nrows + 1) * (nslabs + 1) * 4 <= w->slab_ptr_bytes && nslabs > 1) {
                 k_slab_ptr<<<dev->sms * 8, 256, 0, st>>>(B0, (int)slab, nslabs, w->slab_ptr, w->ctr);
+                count_launch(*dev);
                 sp = w->slab_ptr;
             }
+            mark_stage(*dev, kStSlabPtr, st);
             // rank-indexed kernel when the row bitmap, its prefix and a value
             // array of at least one slab fit in shared memory
             const int64_t bm_words = (max_ncols + 1023) / 1024 * 32;
@@ -974,12 +976,15 @@ struct NumericLaunch {
                     w->probs, nprob, w->rows_num, w->ctr, w->status, sp, nslabs + 1, (int)slab,
                     (int)bm_words, (int)cap, cached ? w->bm_cache : nullptr,
                     cached ? w->row_slot : nullptr, (int)w->bm_cache_words);
+                count_launch(*dev);
             } else {
                 const int grid = occupancy_grid((const void*)k_num_dense<S>, kBlockThreads, smem, *dev);
                 k_num_dense<S><<<grid, kBlockThreads, smem, st>>>(w->probs, nprob, w->rows_num, w->ctr,
                                                                   w->status, w->cursor, (int)slab, sp,
                                                                   nslabs + 1);
+                count_launch(*dev);
             }
+            mark_stage(*dev, kStNumDense, st);
         }
         {   // block tier
             int64_t T = next_pow2(2 * t->num_block_max_nnz);
@@ -991,6 +996,8 @@ struct NumericLaunch {
             const int grid = occupancy_grid((const void*)k_num_block<S>, kBlockThreads, smem, *dev);
             k_num_block<S><<<grid, kBlockThreads, smem, st>>>(w->probs, nprob, w->rows_num, w->ctr,
                                                               w->status, (int)T);
+            count_launch(*dev);
+            mark_stage(*dev, kStNumBlock, st);
         }
         {   // warp tier
             int64_t T = next_pow2(2 * t->num_warp_max_nnz);
@@ -1003,6 +1010,8 @@ struct NumericLaunch {
                 occupancy_grid((const void*)k_num_warp<S>, kWarpTierWarps * 32, smem, *dev);
             k_num_warp<S><<<grid, kWarpTierWarps * 32, smem, st>>>(w->probs, nprob, w->rows_num,
                                                                    w->ctr, w->status, (int)T);
+            count_launch(*dev);
+            mark_stage(*dev, kStNumWarp, st);
         }
         err = cudaGetLastError();
     }
@@ -1016,11 +1025,13 @@ cudaError_t launch_numeric(int sr, const WsPtrs& w, const DCsr& B0, int nprob, i
     cudaMemsetAsync(w.ctr->num_bin_count, 0, sizeof(w.ctr->num_bin_count), st);
     cudaMemsetAsync(&w.ctr->claim[2], 0, 2 * sizeof(int32_t), st);
     int64_t blocks = (R + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks > (int64_t)dev.sms * 8) blocks = (int64_t)dev.sms * 8;
     k_num_hist<<<(unsigned)blocks, 256, 0, st>>>(w.probs, nprob, R, t, w.ub, w.ctr);
     k_num_bin_offsets<<<1, 32, 0, st>>>(w.ctr);
     k_num_scatter<<<(unsigned)((R + 1023) / 1024), 1024, 0, st>>>(w.probs, nprob, R, t, w.ub,
                                                                    w.ctr, w.rows_num);
+    count_launch(dev, 3);
+    mark_stage(dev, kStNumBin, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     NumericLaunch f{&w, B0, nprob, &t, max_ncols, &dev, st};

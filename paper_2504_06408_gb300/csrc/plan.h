@@ -81,18 +81,46 @@ struct WsPtrs {
 };
 WsPtrs ws_ptrs(void* ws, const WsLayout& L);
 
+// Optional per-stage CUDA-event timing: an event is recorded on the launch
+// stream after each stage; stage time = its event minus the previous one.
+enum StageTag : int {
+    kStBegin = 0, kStAnalyze, kStSymDense, kStSymBlock, kStSymWarp, kStScan,
+    kStNumBin, kStSlabPtr, kStNumDense, kStNumBlock, kStNumWarp, kStMerge, kStCount
+};
+struct StageTimer {
+    static constexpr int kMax = 32;
+    cudaEvent_t ev[kMax];
+    int tag[kMax];
+    int n = 0;
+    bool on = false;
+};
+
 struct DevInfo {
     int sms;
     int max_smem_optin;
+    int64_t* launches = nullptr;   // kernels launched (incremented by the launchers)
+    StageTimer* timer = nullptr;
 };
 
+inline void count_launch(const DevInfo& d, int k = 1) {
+    if (d.launches) *d.launches += k;
+}
+inline void mark_stage(const DevInfo& d, int tag, cudaStream_t st) {
+    if (d.timer && d.timer->on && d.timer->n < StageTimer::kMax) {
+        cudaEventRecord(d.timer->ev[d.timer->n], st);
+        d.timer->tag[d.timer->n++] = tag;
+    }
+}
+
 // ---- launchers (asynchronous on `st`; return the launch error) ----
-cudaError_t launch_write_probs(const ProbTable& tab, int nprob, const WsPtrs& w, cudaStream_t st);
+cudaError_t launch_write_probs(const ProbTable& tab, int nprob, const WsPtrs& w,
+                               const DevInfo& dev, cudaStream_t st);
 cudaError_t launch_analyze(const WsPtrs& w, int nprob, int64_t R, const Tuning& t,
-                           cudaStream_t st);
+                           const DevInfo& dev, cudaStream_t st);
 cudaError_t launch_symbolic(const WsPtrs& w, int nprob, int64_t R, const Tuning& t,
                             int64_t max_ncols, const DevInfo& dev, cudaStream_t st);
-cudaError_t launch_scan_rowptr(const WsPtrs& w, int nprob, int64_t R, cudaStream_t st);
+cudaError_t launch_scan_rowptr(const WsPtrs& w, int nprob, int64_t R, const DevInfo& dev,
+                               cudaStream_t st);
 // in-place exclusive scan of cnt[0, R) (int64), cnt[R] = total; part holds
 // scan_parts_needed(R) int64
 cudaError_t launch_scan_inplace(int64_t* cnt, int64_t R, int64_t* part, cudaStream_t st);

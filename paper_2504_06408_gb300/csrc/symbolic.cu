@@ -390,23 +390,31 @@ __global__ void k_validate(DCsr M, int64_t nnz, DevStatus* st) {
 
 // ---- launchers -------------------------------------------------------------------
 
-cudaError_t launch_write_probs(const ProbTable& tab, int nprob, const WsPtrs& w, cudaStream_t st) {
+cudaError_t launch_write_probs(const ProbTable& tab, int nprob, const WsPtrs& w,
+                               const DevInfo& dev, cudaStream_t st) {
+    mark_stage(dev, kStBegin, st);
     k_write_probs<<<1, kMaxProb, 0, st>>>(tab, nprob, w.probs);
+    count_launch(dev);
     return cudaGetLastError();
 }
 
 cudaError_t launch_analyze(const WsPtrs& w, int nprob, int64_t R, const Tuning& t,
-                           cudaStream_t st) {
+                           const DevInfo& dev, cudaStream_t st) {
     if (R > 0) {
         int64_t blocks = (R + 7) / 8;
-        if (blocks > 152 * 16) blocks = 152 * 16;
+        if (blocks > (int64_t)dev.sms * 16) blocks = (int64_t)dev.sms * 16;
         k_analyze<<<(unsigned)blocks, 256, 0, st>>>(w.probs, nprob, R, t, w.ub, w.cnt, w.ctr);
+        count_launch(dev);
     }
     k_bin_offsets<<<1, 32, 0, st>>>(w.ctr->sym_bin_count, w.ctr->sym_bin_off,
                                     w.ctr->sym_bin_cursor);
-    if (R > 0)
+    count_launch(dev);
+    if (R > 0) {
         k_scatter_sym<<<(unsigned)((R + 1023) / 1024), 1024, 0, st>>>(R, t, w.ub, w.ctr,
                                                                        w.rows_sym);
+        count_launch(dev);
+    }
+    mark_stage(dev, kStAnalyze, st);
     return cudaGetLastError();
 }
 
@@ -440,6 +448,8 @@ cudaError_t launch_symbolic(const WsPtrs& w, int nprob, int64_t R, const Tuning&
         k_sym_dense<<<grid, kBlockThreads, smem, st>>>(w.probs, nprob, w.rows_sym, w.ctr, w.cnt,
                                                        w.cursor, (int)slab, w.bm_cache, w.row_slot,
                                                        w.bm_cache_words, w.bm_cache_slots);
+        count_launch(dev);
+        mark_stage(dev, kStSymDense, st);
     }
     {
         int64_t T = next_pow2(2 * t.sym_block_max_ub);
@@ -451,6 +461,8 @@ cudaError_t launch_symbolic(const WsPtrs& w, int nprob, int64_t R, const Tuning&
         const int grid = occupancy((const void*)k_sym_block, kBlockThreads, smem, dev);
         k_sym_block<<<grid, kBlockThreads, smem, st>>>(w.probs, nprob, w.rows_sym, w.ctr, w.ub,
                                                        w.cnt, w.status, (int)T);
+        count_launch(dev);
+        mark_stage(dev, kStSymBlock, st);
     }
     {
         const size_t per_warp = sym_warp_smem_per_warp(t);
@@ -462,6 +474,8 @@ cudaError_t launch_symbolic(const WsPtrs& w, int nprob, int64_t R, const Tuning&
         k_sym_warp<<<grid, kWarpTierWarps * 32, smem, st>>>(
             w.probs, nprob, w.rows_sym, w.ctr, w.ub, w.cnt, w.status,
             (int)(per_warp / sizeof(int32_t)));
+        count_launch(dev);
+        mark_stage(dev, kStSymWarp, st);
     }
     return cudaGetLastError();
 }
@@ -480,10 +494,14 @@ cudaError_t launch_scan_inplace(int64_t* cnt, int64_t R, int64_t* part, cudaStre
     return cudaGetLastError();
 }
 
-cudaError_t launch_scan_rowptr(const WsPtrs& w, int nprob, int64_t R, cudaStream_t st) {
+cudaError_t launch_scan_rowptr(const WsPtrs& w, int nprob, int64_t R, const DevInfo& dev,
+                               cudaStream_t st) {
     cudaError_t e = launch_scan_inplace(w.cnt, R, w.scan_part, st);
     if (e != cudaSuccess) return e;
+    count_launch(dev, R > 0 ? 3 : 0);
     k_write_rowptr<<<dim3(64, nprob), 256, 0, st>>>(w.probs, w.cnt, w.ctr);
+    count_launch(dev);
+    mark_stage(dev, kStScan, st);
     return cudaGetLastError();
 }
 

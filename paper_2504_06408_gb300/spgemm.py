@@ -54,7 +54,13 @@ class spg_tuning(ctypes.Structure):
 
 class spg_stats(ctypes.Structure):
     _fields_ = [("products", ctypes.c_int64), ("nnz_c", ctypes.c_int64),
-                ("rows_per_tier", ctypes.c_int64 * 4), ("reserved", ctypes.c_int64 * 6)]
+                ("rows_per_tier", ctypes.c_int64 * 4), ("launches", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 5)]
+
+
+# stage indices of spgemm_get_stage_times
+STAGES = ["", "analysis", "sym_dense", "sym_block", "sym_warp", "scan", "num_binning",
+          "slab_table", "num_dense", "num_block", "num_warp", "merge"]
 
 
 _lib = None
@@ -85,6 +91,10 @@ def load_library(path: str = LIB_PATH):
         "spgemm_validate_csr": [_P, _CSR, _P, ctypes.c_size_t, _P],
         "spgemm_transpose_workspace_size": [_P, _CSR, ctypes.POINTER(ctypes.c_size_t)],
         "spgemm_transpose": [_P, _CSR, ctypes.c_int, _P, _P, _P, _P, ctypes.c_size_t, _P],
+        "spgemm_set_timing": [_P, ctypes.c_int],
+        "spgemm_get_stage_times": [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int],
+        "spgemm_host_symbolic": [_P, ctypes.c_int, _CSR, _CSR, _P, ctypes.POINTER(_I64)],
+        "spgemm_host_numeric": [_P, ctypes.c_int, _P, _P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -100,7 +110,8 @@ def exported_symbols() -> list[str]:
     return ["spgemm_create", "spgemm_destroy", "spgemm_last_error", "spgemm_set_tuning",
             "spgemm_get_tuning", "spgemm_get_stats", "spgemm_workspace_size", "spgemm_symbolic",
             "spgemm_numeric", "spgemm_check", "spgemm_validate_csr",
-            "spgemm_transpose_workspace_size", "spgemm_transpose"]
+            "spgemm_transpose_workspace_size", "spgemm_transpose", "spgemm_set_timing",
+            "spgemm_get_stage_times", "spgemm_host_symbolic", "spgemm_host_numeric"]
 
 
 @dataclass
@@ -169,7 +180,44 @@ class Handle:
         s = spg_stats()
         self._ok(self.lib.spgemm_get_stats(self._h, ctypes.byref(s)))
         return {"products": s.products, "nnz_c": s.nnz_c,
-                "rows_per_tier": list(s.rows_per_tier)}
+                "rows_per_tier": list(s.rows_per_tier), "launches": s.launches}
+
+    def set_timing(self, enable: bool = True):
+        self._ok(self.lib.spgemm_set_timing(self._h, 1 if enable else 0))
+
+    def stage_times(self) -> dict:
+        """Milliseconds per stage of the last symbolic or numeric call."""
+        buf = (ctypes.c_float * len(STAGES))()
+        self._ok(self.lib.spgemm_get_stage_times(self._h, buf, len(STAGES)))
+        return {name: buf[i] for i, name in enumerate(STAGES) if name}
+
+    def host_multiply(self, sr: int, A, B, out=None):
+        """C = A (x).(+) B for HOST matrices (numpy arrays, ideally pinned torch
+        tensors' numpy views).  ``out`` = optional dict of preallocated host arrays
+        {"rp", "col", "val"} large enough for C.  Returns (rp, col, val, nnz)."""
+        def host_csr(M):
+            vb = IN_NP[sr]
+            val = None if vb is None else np.ascontiguousarray(M.val, dtype=vb)
+            rp = np.ascontiguousarray(M.rp, dtype=np.int64)
+            col = np.ascontiguousarray(M.col, dtype=np.int32)
+            return spg_csr(M.nrows, M.ncols, col.size, rp.ctypes.data,
+                           col.ctypes.data if col.size else None,
+                           None if val is None or val.size == 0 else val.ctypes.data), (rp, col, val)
+        a, ka = host_csr(A)
+        b, kb = (a, ka) if B is A else host_csr(B)
+        rp = out["rp"] if out else np.empty(A.nrows + 1, dtype=np.int64)
+        nnz = ctypes.c_int64()
+        self._ok(self.lib.spgemm_host_symbolic(self._h, sr, ctypes.byref(a), ctypes.byref(b),
+                                               rp.ctypes.data, ctypes.byref(nnz)))
+        n = nnz.value
+        if out:
+            col, val = out["col"], out.get("val")
+        else:
+            col = np.empty(n, dtype=np.int32)
+            val = None if OUT_BYTES[sr] == 0 else np.empty(n * OUT_BYTES[sr], dtype=np.uint8)
+        self._ok(self.lib.spgemm_host_numeric(self._h, sr, col.ctypes.data if n else None,
+                                              None if val is None or n == 0 else val.ctypes.data))
+        return rp, col, val, n
 
     def workspace_size(self, sr: int, A: DeviceCSR, B: DeviceCSR) -> int:
         n = ctypes.c_size_t()
