@@ -215,6 +215,31 @@ spg_status spgemm_transpose(spg_handle* handle, const spg_csr* A, int value_byte
                             int64_t* t_row_ptr, int32_t* t_col, void* t_val, void* workspace,
                             size_t workspace_bytes, void* stream);
 
+/*
+ * spgemm_transpose without any allocation.  The paper has no counterpart:
+ * this entry point is for callers that cannot call cudaMalloc where they
+ * need a transpose (inside allocation-free graph-building frameworks, custom
+ * allocators' own callbacks, processes whose device memory is reserved by a
+ * pool they do not own).  It runs the kernels of spgemm_transpose (same
+ * arguments and output) with their scratch in a 32 MiB device array that
+ * the library holds on every GPU that loads it, until the process exits.
+ *   - No handle; no cudaMalloc / cudaFree or allocating library call.
+ *   - Limit: 4 * A.ncols + 8 * A.nnz (plus ~8 bytes per 2048 columns and
+ *     alignment) must fit in 32 MiB; larger inputs return SPG_ERR_UNSUPPORTED
+ *     before any GPU work.
+ *   - The first call on a device looks the array's address up (once per
+ *     device, with that device current); make that first call before any
+ *     stream capture.
+ *   - Every call shares the one array: calls whose work overlaps on the GPU
+ *     (other streams, other host threads) race and corrupt each other; order
+ *     them on one stream.  Each call clears what it needs; the array keeps
+ *     the last call's contents.
+ * Asynchronous on `stream`.  Errors: SPG_ERR_INVALID_ARG, SPG_ERR_UNSUPPORTED,
+ * SPG_ERR_CUDA.
+ */
+spg_status spgemm_transpose_noalloc(const spg_csr* A, int value_bytes, int64_t* t_row_ptr,
+                                    int32_t* t_col, void* t_val, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

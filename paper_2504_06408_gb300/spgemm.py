@@ -95,6 +95,7 @@ def load_library(path: str = LIB_PATH):
         "spgemm_get_stage_times": [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int],
         "spgemm_host_symbolic": [_P, ctypes.c_int, _CSR, _CSR, _P, ctypes.POINTER(_I64)],
         "spgemm_host_numeric": [_P, ctypes.c_int, _P, _P],
+        "spgemm_transpose_noalloc": [_CSR, ctypes.c_int, _P, _P, _P, _P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -111,7 +112,8 @@ def exported_symbols() -> list[str]:
             "spgemm_get_tuning", "spgemm_get_stats", "spgemm_workspace_size", "spgemm_symbolic",
             "spgemm_numeric", "spgemm_check", "spgemm_validate_csr",
             "spgemm_transpose_workspace_size", "spgemm_transpose", "spgemm_set_timing",
-            "spgemm_get_stage_times", "spgemm_host_symbolic", "spgemm_host_numeric"]
+            "spgemm_get_stage_times", "spgemm_host_symbolic", "spgemm_host_numeric",
+            "spgemm_transpose_noalloc"]
 
 
 @dataclass
