@@ -153,6 +153,71 @@ spg_status spgemm_numeric(spg_handle* handle, spg_semiring sr, const spg_csr* A,
                           void* c_val, void* workspace, size_t workspace_bytes,
                           void* stream);
 
+/*
+ * Batched form: nprob independent products C_p = A_p (x).(+) B_p (1 <= nprob
+ * <= 128) in one call, e.g. the uneven block products of all stages of an
+ * emulated Sparse-SUMMA grid (Section 2.1).  The rows of all products are
+ * binned together and each tier runs as ONE persistent launch over all of
+ * them, heaviest rows first.  Arrays of nprob descriptors / pointers:
+ *   c_row_ptr[p] : device int64 [A_p.nrows + 1];  c_nnz : HOST int64 [nprob].
+ * Same workspace rules as the single form (spgemm_workspace_size_batched).
+ */
+spg_status spgemm_workspace_size_batched(spg_handle* handle, spg_semiring sr, int nprob,
+                                         const spg_csr* A, const spg_csr* B, size_t* bytes);
+spg_status spgemm_symbolic_batched(spg_handle* handle, spg_semiring sr, int nprob,
+                                   const spg_csr* A, const spg_csr* B,
+                                   int64_t* const* c_row_ptr, int64_t* c_nnz, void* workspace,
+                                   size_t workspace_bytes, void* stream);
+spg_status spgemm_numeric_batched(spg_handle* handle, spg_semiring sr, int nprob,
+                                  const spg_csr* A, const spg_csr* B,
+                                  const int64_t* const* c_row_ptr, int32_t* const* c_col,
+                                  void* const* c_val, void* workspace, size_t workspace_bytes,
+                                  void* stream);
+
+/*
+ * Merge of per-stage partial products (Sections 2.1 and 3.4):
+ *     C[i,j] = P_0[i,j] (+) P_1[i,j] (+) ... (+) P_{S-1}[i,j]
+ * over the entries present, folded in stage order (deterministic).  The S
+ * partials (1 <= S <= 16) share C's shape; their values have the semiring's
+ * OUTPUT type (spg_overlap records for the overlap semiring).
+ * Two calls with the same workspace:
+ *   1. c_col == NULL: writes c_row_ptr (device int64 [nrows + 1]) and c_nnz
+ *      (HOST); synchronises `stream`.
+ *   2. c_col != NULL: writes C.col / C.val (c_row_ptr from call 1).
+ */
+spg_status spgemm_merge_workspace_size(spg_handle* handle, spg_semiring sr, int nmerge,
+                                       const int* nparts, const spg_csr* parts, size_t* bytes);
+spg_status spgemm_merge_stages(spg_handle* handle, spg_semiring sr, int nstages,
+                               const spg_csr* parts, int64_t* c_row_ptr, int64_t* c_nnz,
+                               int32_t* c_col, void* c_val, void* workspace,
+                               size_t workspace_bytes, void* stream);
+/* Batched merges (1 <= nmerge <= 32): merge m combines parts[off_m ..
+ * off_m + nparts[m]) with off_m = nparts[0] + ... + nparts[m-1].  Count call:
+ * c_col == NULL (the array); c_nnz HOST [nmerge]. */
+spg_status spgemm_merge_stages_batched(spg_handle* handle, spg_semiring sr, int nmerge,
+                                       const int* nparts, const spg_csr* parts,
+                                       int64_t* const* c_row_ptr, int64_t* c_nnz,
+                                       int32_t* const* c_col, void* const* c_val,
+                                       void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Column split (the block layout of Sparse SUMMA, Section 2.1): part p keeps
+ * columns [cuts[p], cuts[p+1]) of every row of M, renumbered from 0.  Row
+ * blocks of a CSR are views (row_ptr + first row, same col/val base).
+ *   cuts          : HOST int32 [nparts + 1], cuts[0] = 0, cuts[nparts] = ncols,
+ *                   non-decreasing
+ *   part_row_ptr  : device int64 [nparts * (M.nrows + 1)], part p at p*(nrows+1),
+ *                   offsets relative to part p's first entry
+ *   part_col/val  : device [M.nnz] (values value_bytes each), part after part
+ *   part_nnz      : HOST int64 [nparts], written; synchronises `stream`.
+ */
+spg_status spgemm_split_workspace_size(spg_handle* handle, const spg_csr* M, int nparts,
+                                       size_t* bytes);
+spg_status spgemm_split_columns(spg_handle* handle, const spg_csr* M, int nparts,
+                                const int32_t* cuts, int value_bytes, int64_t* part_row_ptr,
+                                int32_t* part_col, void* part_val, int64_t* part_nnz,
+                                void* workspace, size_t workspace_bytes, void* stream);
+
 /* Synchronises `stream` and returns the first kernel-detected error recorded
  * in `workspace` since the last spgemm_symbolic (SPG_OK if none). */
 spg_status spgemm_check(spg_handle* handle, void* workspace, void* stream);

@@ -349,32 +349,76 @@ static spg_status read_status(spg_handle* h, const WsPtrs& w, cudaStream_t st) {
     return SPG_OK;
 }
 
-spg_status spgemm_symbolic(spg_handle* h, spg_semiring sr, const spg_csr* A, const spg_csr* B,
-                           int64_t* c_row_ptr, int64_t* c_nnz, void* workspace,
-                           size_t workspace_bytes, void* stream) {
-    spg_status s = check_pair(h, sr, A, B, false);
-    if (s != SPG_OK) return s;
-    if (!c_row_ptr || !c_nnz) return fail(h, SPG_ERR_INVALID_ARG, "c_row_ptr / c_nnz is NULL");
+// ---- symbolic / numeric, single and batched ---------------------------------------
+
+static spg_status check_batch(spg_handle* h, int sr, int nprob, const spg_csr* A,
+                              const spg_csr* B, bool need_val) {
+    if (!h) return SPG_ERR_INVALID_ARG;
+    if (nprob < 1 || nprob > kMaxProb)
+        return fail(h, SPG_ERR_INVALID_ARG, "batch of %d products (1..%d)", nprob, kMaxProb);
+    if (!A || !B) return fail(h, SPG_ERR_INVALID_ARG, "A / B is NULL");
+    int64_t R = 0;
+    for (int p = 0; p < nprob; ++p) {
+        spg_status s = check_pair(h, sr, A + p, B + p, need_val);
+        if (s != SPG_OK) return s;
+        R += A[p].nrows;
+    }
+    if (R >= INT32_MAX) return fail(h, SPG_ERR_UNSUPPORTED, "batch has >= 2^31 rows");
+    return SPG_OK;
+}
+
+static WsLayout layout_batch(int nprob, const spg_csr* A, const spg_csr* B, const Tuning& t) {
+    if (nprob == 1) return layout_for(A, B, t);
+    int64_t R = 0, E = 0, maxc = 0;
+    for (int p = 0; p < nprob; ++p) {
+        R += A[p].nrows;
+        E += A[p].nnz;
+        if (B[p].ncols > maxc) maxc = B[p].ncols;
+    }
+    // no slab table for batches (segments come from per-entry cursors)
+    const int64_t cache = (t.bitmap_cache_bytes > 0 && maxc <= t.sym_slab_cols) ? t.bitmap_cache_bytes : 0;
+    return ws_layout(R, E, 0, maxc, 0, t.dense_slab_cols, cache);
+}
+
+static void fill_probs(ProbTable* tab, int nprob, const spg_csr* A, const spg_csr* B,
+                       int64_t* const* c_rp, int32_t* const* c_col, void* const* c_val) {
+    std::memset(tab, 0, sizeof *tab);
+    int64_t rb = 0, eb = 0;
+    for (int p = 0; p < nprob; ++p) {
+        tab->p[p] = Prob{to_dcsr(A + p), to_dcsr(B + p), c_rp[p], c_col ? c_col[p] : nullptr,
+                         c_val ? c_val[p] : nullptr, rb, eb};
+        rb += A[p].nrows;
+        eb += A[p].nnz;
+    }
+}
+
+static int64_t max_ncols(int nprob, const spg_csr* B) {
+    int64_t m = 0;
+    for (int p = 0; p < nprob; ++p) m = B[p].ncols > m ? B[p].ncols : m;
+    return m;
+}
+
+static spg_status symbolic_impl(spg_handle* h, int sr, int nprob, const spg_csr* A,
+                                const spg_csr* B, int64_t* const* c_row_ptr, int64_t* c_nnz,
+                                void* workspace, size_t workspace_bytes, cudaStream_t st) {
     const Tuning t = effective_tuning(h, sr);
-    const WsLayout L = layout_for(A, B, t);
+    const WsLayout L = layout_batch(nprob, A, B, t);
     if (!workspace || workspace_bytes < L.total)
         return fail(h, SPG_ERR_WORKSPACE, "workspace needs %zu bytes", L.total);
-    cudaStream_t st = (cudaStream_t)stream;
     const WsPtrs w = ws_ptrs(workspace, L);
     h->launches = 0;
     h->timer.n = 0;
     cudaError_t e = cudaMemsetAsync(workspace, 0, L.probs, st);   // status + counters
     if (e == cudaSuccess && w.row_slot)
-        e = cudaMemsetAsync(w.row_slot, 0xff, sizeof(int32_t) * (size_t)A->nrows, st);
+        e = cudaMemsetAsync(w.row_slot, 0xff, sizeof(int32_t) * (size_t)L.R, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "memset");
     ProbTable* tab = new ProbTable;
-    std::memset(tab, 0, sizeof *tab);
-    tab->p[0] = Prob{to_dcsr(A), to_dcsr(B), c_row_ptr, nullptr, nullptr, 0, 0};
-    e = launch_write_probs(*tab, 1, w, h->dev, st);
+    fill_probs(tab, nprob, A, B, c_row_ptr, nullptr, nullptr);
+    e = launch_write_probs(*tab, nprob, w, h->dev, st);
     delete tab;
-    if (e == cudaSuccess) e = launch_analyze(w, 1, A->nrows, t, h->dev, st);
-    if (e == cudaSuccess) e = launch_symbolic(w, 1, A->nrows, t, B->ncols, h->dev, st);
-    if (e == cudaSuccess) e = launch_scan_rowptr(w, 1, A->nrows, h->dev, st);
+    if (e == cudaSuccess) e = launch_analyze(w, nprob, L.R, t, h->dev, st);
+    if (e == cudaSuccess) e = launch_symbolic(w, nprob, L.R, t, max_ncols(nprob, B), h->dev, st);
+    if (e == cudaSuccess) e = launch_scan_rowptr(w, nprob, L.R, h->dev, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "symbolic launch");
     // bring back nnz, products, bin counts and the status in one copy
     Counters* hc = (Counters*)((char*)h->pinned);
@@ -382,9 +426,13 @@ spg_status spgemm_symbolic(spg_handle* h, spg_semiring sr, const spg_csr* A, con
     e = cudaMemcpyAsync(hc, w.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(h, e, "symbolic");
-    *c_nnz = hc->nnz[0];
+    int64_t tot = 0;
+    for (int p = 0; p < nprob; ++p) {
+        c_nnz[p] = hc->nnz[p];
+        tot += hc->nnz[p];
+    }
     h->stats.products = (int64_t)hc->products;
-    h->stats.nnz_c = hc->nnz[0];
+    h->stats.nnz_c = tot;
     for (int tier = 0; tier < kTiers; ++tier) {
         int64_t n = 0;
         for (int b = 0; b < kSubBins; ++b) n += hc->sym_bin_count[tier * kSubBins + b];
@@ -393,28 +441,256 @@ spg_status spgemm_symbolic(spg_handle* h, spg_semiring sr, const spg_csr* A, con
     return read_status(h, w, st);
 }
 
+static spg_status numeric_impl(spg_handle* h, int sr, int nprob, const spg_csr* A,
+                               const spg_csr* B, const int64_t* const* c_row_ptr,
+                               int32_t* const* c_col, void* const* c_val, void* workspace,
+                               size_t workspace_bytes, cudaStream_t st) {
+    const Tuning t = effective_tuning(h, sr);
+    const WsLayout L = layout_batch(nprob, A, B, t);
+    if (!workspace || workspace_bytes < L.total)
+        return fail(h, SPG_ERR_WORKSPACE, "workspace needs %zu bytes", L.total);
+    const WsPtrs w = ws_ptrs(workspace, L);
+    h->launches = 0;
+    h->timer.n = 0;
+    ProbTable* tab = new ProbTable;
+    fill_probs(tab, nprob, A, B, const_cast<int64_t* const*>(c_row_ptr), c_col, c_val);
+    cudaError_t e = launch_write_probs(*tab, nprob, w, h->dev, st);
+    delete tab;
+    if (e == cudaSuccess)
+        e = launch_numeric(sr, w, to_dcsr(B), nprob, L.R, t, max_ncols(nprob, B), h->dev, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "numeric launch");
+    return SPG_OK;
+}
+
+spg_status spgemm_symbolic(spg_handle* h, spg_semiring sr, const spg_csr* A, const spg_csr* B,
+                           int64_t* c_row_ptr, int64_t* c_nnz, void* workspace,
+                           size_t workspace_bytes, void* stream) {
+    spg_status s = check_pair(h, sr, A, B, false);
+    if (s != SPG_OK) return s;
+    if (!c_row_ptr || !c_nnz) return fail(h, SPG_ERR_INVALID_ARG, "c_row_ptr / c_nnz is NULL");
+    return symbolic_impl(h, sr, 1, A, B, &c_row_ptr, c_nnz, workspace, workspace_bytes,
+                         (cudaStream_t)stream);
+}
+
 spg_status spgemm_numeric(spg_handle* h, spg_semiring sr, const spg_csr* A, const spg_csr* B,
                           const int64_t* c_row_ptr, int32_t* c_col, void* c_val,
                           void* workspace, size_t workspace_bytes, void* stream) {
     spg_status s = check_pair(h, sr, A, B, true);
     if (s != SPG_OK) return s;
     if (!c_row_ptr) return fail(h, SPG_ERR_INVALID_ARG, "c_row_ptr is NULL");
-    const Tuning t = effective_tuning(h, sr);
-    const WsLayout L = layout_for(A, B, t);
-    if (!workspace || workspace_bytes < L.total)
-        return fail(h, SPG_ERR_WORKSPACE, "workspace needs %zu bytes", L.total);
+    return numeric_impl(h, sr, 1, A, B, &c_row_ptr, &c_col, &c_val, workspace, workspace_bytes,
+                        (cudaStream_t)stream);
+}
+
+spg_status spgemm_workspace_size_batched(spg_handle* h, spg_semiring sr, int nprob,
+                                         const spg_csr* A, const spg_csr* B, size_t* bytes) {
+    spg_status s = check_batch(h, sr, nprob, A, B, false);
+    if (s != SPG_OK) return s;
+    if (!bytes) return fail(h, SPG_ERR_INVALID_ARG, "bytes is NULL");
+    *bytes = layout_batch(nprob, A, B, effective_tuning(h, sr)).total;
+    return SPG_OK;
+}
+
+spg_status spgemm_symbolic_batched(spg_handle* h, spg_semiring sr, int nprob, const spg_csr* A,
+                                   const spg_csr* B, int64_t* const* c_row_ptr, int64_t* c_nnz,
+                                   void* workspace, size_t workspace_bytes, void* stream) {
+    spg_status s = check_batch(h, sr, nprob, A, B, false);
+    if (s != SPG_OK) return s;
+    if (!c_row_ptr || !c_nnz) return fail(h, SPG_ERR_INVALID_ARG, "c_row_ptr / c_nnz is NULL");
+    for (int p = 0; p < nprob; ++p)
+        if (!c_row_ptr[p]) return fail(h, SPG_ERR_INVALID_ARG, "c_row_ptr[%d] is NULL", p);
+    return symbolic_impl(h, sr, nprob, A, B, c_row_ptr, c_nnz, workspace, workspace_bytes,
+                         (cudaStream_t)stream);
+}
+
+spg_status spgemm_numeric_batched(spg_handle* h, spg_semiring sr, int nprob, const spg_csr* A,
+                                  const spg_csr* B, const int64_t* const* c_row_ptr,
+                                  int32_t* const* c_col, void* const* c_val, void* workspace,
+                                  size_t workspace_bytes, void* stream) {
+    spg_status s = check_batch(h, sr, nprob, A, B, true);
+    if (s != SPG_OK) return s;
+    if (!c_row_ptr || !c_col) return fail(h, SPG_ERR_INVALID_ARG, "c_row_ptr / c_col is NULL");
+    return numeric_impl(h, sr, nprob, A, B, c_row_ptr, c_col, c_val, workspace, workspace_bytes,
+                        (cudaStream_t)stream);
+}
+
+// ---- merge of stage partials ---------------------------------------------------------
+
+static spg_status merge_check(spg_handle* h, int sr, int nmerge, const int* nparts,
+                              const spg_csr* parts, int64_t* R, int64_t* T, int64_t* maxp,
+                              int* maxs) {
+    if (!h) return SPG_ERR_INVALID_ARG;
+    if (!sr_valid(sr)) return fail(h, SPG_ERR_INVALID_ARG, "unknown semiring id %d", sr);
+    if (nmerge < 1 || nmerge > kMaxMerge || !nparts || !parts)
+        return fail(h, SPG_ERR_INVALID_ARG, "merges: 1..%d, nparts and parts non-NULL", kMaxMerge);
+    *R = *T = *maxp = 0;
+    *maxs = 0;
+    int off = 0;
+    for (int m = 0; m < nmerge; ++m) {
+        if (nparts[m] < 1 || nparts[m] > kMaxStages)
+            return fail(h, SPG_ERR_INVALID_ARG, "merge %d: 1..%d partials", m, kMaxStages);
+        for (int s = 0; s < nparts[m]; ++s) {
+            const spg_csr* P = parts + off + s;
+            spg_status st = check_csr_arg(h, P, "partial", sr, true);
+            if (st != SPG_OK) return st;
+            if (P->nrows != parts[off].nrows || P->ncols != parts[off].ncols)
+                return fail(h, SPG_ERR_INVALID_ARG, "merge %d: partials differ in shape", m);
+            *T += P->nnz;
+            if (P->nnz > *maxp) *maxp = P->nnz;
+        }
+        *R += parts[off].nrows;
+        if (nparts[m] > *maxs) *maxs = nparts[m];
+        off += nparts[m];
+    }
+    if (*R >= INT32_MAX) return fail(h, SPG_ERR_UNSUPPORTED, "too many rows");
+    return SPG_OK;
+}
+
+static void fill_merge_probs(MergeProbTable* tab, int nmerge, const int* nparts,
+                             const spg_csr* parts, int64_t* const* c_rp, int32_t* const* c_col,
+                             void* const* c_val) {
+    std::memset(tab, 0, sizeof *tab);
+    int off = 0;
+    int64_t rb = 0;
+    for (int m = 0; m < nmerge; ++m) {
+        MergeProb& M = tab->p[m];
+        M.nrows = parts[off].nrows;
+        M.ncols = parts[off].ncols;
+        M.nparts = nparts[m];
+        for (int s = 0; s < nparts[m]; ++s) {
+            M.rp[s] = parts[off + s].row_ptr;
+            M.col[s] = parts[off + s].col;
+            M.val[s] = parts[off + s].val;
+        }
+        M.c_rp = c_rp[m];
+        M.c_col = c_col ? c_col[m] : nullptr;
+        M.c_val = c_val ? c_val[m] : nullptr;
+        M.row_base = rb;
+        rb += M.nrows;
+        off += nparts[m];
+    }
+}
+
+spg_status spgemm_merge_workspace_size(spg_handle* h, spg_semiring sr, int nmerge,
+                                       const int* nparts, const spg_csr* parts, size_t* bytes) {
+    int64_t R, T, mp;
+    int ms;
+    spg_status s = merge_check(h, sr, nmerge, nparts, parts, &R, &T, &mp, &ms);
+    if (s != SPG_OK) return s;
+    if (!bytes) return fail(h, SPG_ERR_INVALID_ARG, "bytes is NULL");
+    *bytes = merge_ws_layout(nullptr, R, T, out_bytes(sr)).total;
+    return SPG_OK;
+}
+
+spg_status spgemm_merge_stages_batched(spg_handle* h, spg_semiring sr, int nmerge,
+                                       const int* nparts, const spg_csr* parts,
+                                       int64_t* const* c_row_ptr, int64_t* c_nnz,
+                                       int32_t* const* c_col, void* const* c_val,
+                                       void* workspace, size_t workspace_bytes, void* stream) {
+    int64_t R, T, maxp;
+    int maxs;
+    spg_status s = merge_check(h, sr, nmerge, nparts, parts, &R, &T, &maxp, &maxs);
+    if (s != SPG_OK) return s;
+    if (!c_row_ptr) return fail(h, SPG_ERR_INVALID_ARG, "c_row_ptr is NULL");
+    for (int m = 0; m < nmerge; ++m)
+        if (!c_row_ptr[m]) return fail(h, SPG_ERR_INVALID_ARG, "c_row_ptr[%d] is NULL", m);
+    const MergeWs w = merge_ws_layout(workspace, R, T, out_bytes(sr));
+    if (!workspace || workspace_bytes < w.total)
+        return fail(h, SPG_ERR_WORKSPACE, "workspace needs %zu bytes", w.total);
     cudaStream_t st = (cudaStream_t)stream;
-    const WsPtrs w = ws_ptrs(workspace, L);
     h->launches = 0;
     h->timer.n = 0;
-    ProbTable* tab = new ProbTable;
-    std::memset(tab, 0, sizeof *tab);
-    tab->p[0] = Prob{to_dcsr(A), to_dcsr(B), const_cast<int64_t*>(c_row_ptr), c_col, c_val, 0, 0};
-    cudaError_t e = launch_write_probs(*tab, 1, w, h->dev, st);
+    MergeProbTable* tab = new MergeProbTable;
+    fill_merge_probs(tab, nmerge, nparts, parts, c_row_ptr, c_col, c_val);
+    cudaError_t e;
+    if (!c_col) {   // count: C row pointers and nnz
+        if (!c_nnz) {
+            delete tab;
+            return fail(h, SPG_ERR_INVALID_ARG, "c_nnz is NULL");
+        }
+        e = cudaMemsetAsync(workspace, 0, (char*)w.probs - (char*)workspace, st);
+        if (e == cudaSuccess) e = launch_merge_count(sr, *tab, nmerge, R, maxp, maxs, w, h->dev, st);
+        if (e == cudaSuccess) e = launch_merge_rowptr(w, nmerge, h->dev, st);
+        delete tab;
+        if (e != cudaSuccess) return cuda_fail(h, e, "merge count");
+        Counters* hc = (Counters*)h->pinned;
+        e = cudaMemcpyAsync(hc, w.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "merge count");
+        for (int m = 0; m < nmerge; ++m) c_nnz[m] = hc->nnz[m];
+        return SPG_OK;
+    }
+    for (int m = 0; m < nmerge; ++m)
+        if (!c_col[m] || (out_bytes(sr) && (!c_val || !c_val[m]))) {
+            delete tab;
+            return fail(h, SPG_ERR_INVALID_ARG, "c_col / c_val of merge %d is NULL", m);
+        }
+    e = launch_merge_write(sr, *tab, nmerge, R, w, h->dev, st);
     delete tab;
+    if (e != cudaSuccess) return cuda_fail(h, e, "merge write");
+    return SPG_OK;
+}
+
+spg_status spgemm_merge_stages(spg_handle* h, spg_semiring sr, int nstages, const spg_csr* parts,
+                               int64_t* c_row_ptr, int64_t* c_nnz, int32_t* c_col, void* c_val,
+                               void* workspace, size_t workspace_bytes, void* stream) {
+    return spgemm_merge_stages_batched(h, sr, 1, &nstages, parts, &c_row_ptr, c_nnz,
+                                       c_col ? &c_col : nullptr, c_col ? &c_val : nullptr,
+                                       workspace, workspace_bytes, stream);
+}
+
+// ---- column split -----------------------------------------------------------------
+
+static size_t split_ws_bytes(int64_t nrows, int nparts) {
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    return al(sizeof(int32_t) * (size_t)(nparts + 1)) + al(sizeof(int64_t) * (size_t)(nparts + 1)) +
+           al(sizeof(int64_t) * (size_t)scan_parts_needed(nrows));
+}
+
+spg_status spgemm_split_workspace_size(spg_handle* h, const spg_csr* M, int nparts, size_t* bytes) {
+    if (!h) return SPG_ERR_INVALID_ARG;
+    spg_status s = check_csr_arg(h, M, "M", SR_BOOL, false);
+    if (s != SPG_OK) return s;
+    if (nparts < 1 || !bytes) return fail(h, SPG_ERR_INVALID_ARG, "nparts >= 1 and bytes");
+    *bytes = split_ws_bytes(M->nrows, nparts);
+    return SPG_OK;
+}
+
+spg_status spgemm_split_columns(spg_handle* h, const spg_csr* M, int nparts, const int32_t* cuts,
+                                int value_bytes, int64_t* part_row_ptr, int32_t* part_col,
+                                void* part_val, int64_t* part_nnz, void* workspace,
+                                size_t workspace_bytes, void* stream) {
+    if (!h) return SPG_ERR_INVALID_ARG;
+    spg_status s = check_csr_arg(h, M, "M", SR_BOOL, false);
+    if (s != SPG_OK) return s;
+    if (nparts < 1 || !cuts || !part_row_ptr || !part_nnz || (M->nnz > 0 && !part_col))
+        return fail(h, SPG_ERR_INVALID_ARG, "split: NULL argument or nparts < 1");
+    if (value_bytes < 0 || value_bytes > 64 || (value_bytes && M->nnz > 0 && (!M->val || !part_val)))
+        return fail(h, SPG_ERR_INVALID_ARG, "split: bad value_bytes or NULL values");
+    if (cuts[0] != 0 || cuts[nparts] != M->ncols)
+        return fail(h, SPG_ERR_INVALID_ARG, "split: cuts must run from 0 to ncols");
+    for (int p = 0; p < nparts; ++p)
+        if (cuts[p + 1] < cuts[p]) return fail(h, SPG_ERR_INVALID_ARG, "split: cuts must not decrease");
+    if (!workspace || workspace_bytes < split_ws_bytes(M->nrows, nparts))
+        return fail(h, SPG_ERR_WORKSPACE, "split workspace too small");
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    char* b = (char*)workspace;
+    int32_t* cuts_dev = (int32_t*)b;
+    int64_t* base_dev = (int64_t*)(b + al(sizeof(int32_t) * (size_t)(nparts + 1)));
+    int64_t* part = (int64_t*)((char*)base_dev + al(sizeof(int64_t) * (size_t)(nparts + 1)));
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(cuts_dev, cuts, sizeof(int32_t) * (size_t)(nparts + 1),
+                                    cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-        e = launch_numeric(sr, w, to_dcsr(B), 1, A->nrows, t, B->ncols, h->dev, st);
-    if (e != cudaSuccess) return cuda_fail(h, e, "numeric launch");
+        e = launch_split_columns(to_dcsr(M), nparts, cuts_dev, part_row_ptr, base_dev, part_col,
+                                 part_val, value_bytes, part, h->dev, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "split");
+    int64_t* hb = (int64_t*)h->pinned;
+    if ((size_t)(nparts + 1) * 8 > kPinnedBytes) return fail(h, SPG_ERR_UNSUPPORTED, "too many parts");
+    e = cudaMemcpyAsync(hb, base_dev, sizeof(int64_t) * (size_t)(nparts + 1), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "split");
+    for (int p = 0; p < nparts; ++p) part_nnz[p] = hb[p + 1] - hb[p];
     return SPG_OK;
 }
 

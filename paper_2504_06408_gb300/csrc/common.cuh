@@ -29,7 +29,8 @@ struct Prob {
     int32_t* c_col;      // output columns [nnz(C)]
     void* c_val;         // output values  [nnz(C)]
     int64_t row_base;    // first flat row
-    int64_t nnz_base;    // first entry of A in the flat entry numbering (cursors)
+    int64_t nnz_base;    // first entry of A in the flat entry numbering (cursors); entry p
+                         // of row-view A is flat entry nnz_base + (p - A.rp[0])
 };
 
 // Kernel-detected errors, kept in the workspace.

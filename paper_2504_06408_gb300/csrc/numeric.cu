@@ -486,7 +486,7 @@ __global__ void __launch_bounds__(kBlockThreads, 2)
                 ent.segment(P.B, slab, nslabs, sb, se);
                 cta_walk_segments<In, S::kVal>(P.B, sb, se - sb, ent.a, bs, op);
             } else {
-                cta_row_products<In, S::kVal>(P.A, P.B, a0, a1, P.nnz_base + a0, slab, bs, op);
+                cta_row_products<In, S::kVal>(P.A, P.B, a0, a1, P.nnz_base + (a0 - ld_i64(P.A.rp)), slab, bs, op);
             }
             // exclusive scan of the words' popcounts (contiguous words per thread)
             const int wpt = (words + (int)blockDim.x - 1) / (int)blockDim.x;

@@ -143,4 +143,57 @@ size_t num_dense_smem(int sr, int64_t slab_cols);
 constexpr int kWarpTierWarps = 8;     // warps per CTA in the warp tiers
 constexpr int kBlockThreads = 512;    // CTA size of the block and dense tiers
 
+// ---- merge of stage partials (batched) and column split ----
+
+constexpr int kMaxStages = 16;     // partials per merge
+constexpr int kMaxMerge = 32;      // merges per batched call
+
+struct MergeProb {
+    int64_t nrows, ncols;
+    int nparts;
+    const int64_t* rp[kMaxStages];
+    const int32_t* col[kMaxStages];
+    const void* val[kMaxStages];
+    int64_t* c_rp;
+    int32_t* c_col;
+    void* c_val;
+    int64_t row_base;   // first flat row
+};
+struct MergeProbTable {
+    MergeProb p[kMaxMerge];
+};
+
+SPG_DEV int find_merge_prob(const MergeProb* mp, int nprob, int64_t g) {
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (mp[mid].row_base <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+struct MergeWs {
+    DevStatus* status;
+    Counters* ctr;
+    MergeProb* probs;
+    int64_t* trp;    // [R + 1] merged-row starts (with duplicates)
+    int64_t* cnt;    // [R + 1] distinct counts -> flat C row starts
+    int32_t* tcol;   // [T] merged columns
+    void* tval;      // [T] merged values
+    int64_t* part;   // scan partials
+    size_t total;
+};
+MergeWs merge_ws_layout(void* base, int64_t R, int64_t T, int out_bytes);
+
+cudaError_t launch_merge_count(int sr, const MergeProbTable& tab, int nprob, int64_t R,
+                               int64_t max_part_nnz, int max_parts, const MergeWs& w,
+                               const DevInfo& dev, cudaStream_t st);
+cudaError_t launch_merge_rowptr(const MergeWs& w, int nprob, const DevInfo& dev, cudaStream_t st);
+cudaError_t launch_merge_write(int sr, const MergeProbTable& tab, int nprob, int64_t R,
+                               const MergeWs& w, const DevInfo& dev, cudaStream_t st);
+cudaError_t launch_split_columns(const DCsr& M, int nparts, const int32_t* cuts_dev,
+                                 int64_t* prp, int64_t* part_base_dev, int32_t* pcol, void* pval,
+                                 int vbytes, int64_t* part, const DevInfo& dev, cudaStream_t st);
+
+
 }  // namespace spg

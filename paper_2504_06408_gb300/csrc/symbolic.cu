@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(kBlockThreads)
             __syncthreads();
             const Slab slab{lo, hi, s == 0, s == nslabs - 1, nslabs == 1, cursor, nullptr, 0, s};
             BitOrOp op{bm, lo};
-            cta_row_products<char, false>(P.A, P.B, a0, a1, P.nnz_base + a0, slab, bs, op);
+            cta_row_products<char, false>(P.A, P.B, a0, a1, P.nnz_base + (a0 - ld_i64(P.A.rp)), slab, bs, op);
             if (nslabs == 1 && cache_slots > 0 && words <= cache_words) {
                 // keep the row's bitmap for the numeric phase while cache slots last
                 if (threadIdx.x == 0) {

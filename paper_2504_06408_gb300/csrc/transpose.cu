@@ -17,15 +17,18 @@ namespace spg {
 
 constexpr int kTSmemKeys = 16384;
 
+// entries of A are A.col[A.rp[0] .. A.rp[0] + nnz) (A may be a row view)
 __global__ void k_t_count(DCsr A, int64_t nnz, int64_t* t_rp) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz;
+    const int64_t e0 = A.rp[0];
+    for (int64_t e = e0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < e0 + nnz;
          e += (int64_t)gridDim.x * blockDim.x)
         atomicAdd((unsigned long long*)(t_rp + A.col[e]), 1ull);
 }
 
 __global__ void k_t_scatter(DCsr A, int64_t nnz, const int64_t* t_rp, int32_t* cursor,
                             int32_t* t_col) {
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz;
+    const int64_t e0 = A.rp[0];
+    for (int64_t e = e0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < e0 + nnz;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int32_t j = A.col[e];
         const int32_t r = atomicAdd(cursor + j, 1);

@@ -96,6 +96,21 @@ def load_library(path: str = LIB_PATH):
         "spgemm_host_symbolic": [_P, ctypes.c_int, _CSR, _CSR, _P, ctypes.POINTER(_I64)],
         "spgemm_host_numeric": [_P, ctypes.c_int, _P, _P],
         "spgemm_transpose_noalloc": [_CSR, ctypes.c_int, _P, _P, _P, _P],
+        "spgemm_workspace_size_batched": [_P, ctypes.c_int, ctypes.c_int, _CSR, _CSR,
+                                          ctypes.POINTER(ctypes.c_size_t)],
+        "spgemm_symbolic_batched": [_P, ctypes.c_int, ctypes.c_int, _CSR, _CSR, _P, _P, _P,
+                                    ctypes.c_size_t, _P],
+        "spgemm_numeric_batched": [_P, ctypes.c_int, ctypes.c_int, _CSR, _CSR, _P, _P, _P, _P,
+                                   ctypes.c_size_t, _P],
+        "spgemm_merge_workspace_size": [_P, ctypes.c_int, ctypes.c_int, _P, _CSR,
+                                        ctypes.POINTER(ctypes.c_size_t)],
+        "spgemm_merge_stages": [_P, ctypes.c_int, ctypes.c_int, _CSR, _P, ctypes.POINTER(_I64),
+                                _P, _P, _P, ctypes.c_size_t, _P],
+        "spgemm_merge_stages_batched": [_P, ctypes.c_int, ctypes.c_int, _P, _CSR, _P, _P, _P, _P,
+                                        _P, ctypes.c_size_t, _P],
+        "spgemm_split_workspace_size": [_P, _CSR, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)],
+        "spgemm_split_columns": [_P, _CSR, ctypes.c_int, _P, ctypes.c_int, _P, _P, _P, _P, _P,
+                                 ctypes.c_size_t, _P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -113,7 +128,10 @@ def exported_symbols() -> list[str]:
             "spgemm_numeric", "spgemm_check", "spgemm_validate_csr",
             "spgemm_transpose_workspace_size", "spgemm_transpose", "spgemm_set_timing",
             "spgemm_get_stage_times", "spgemm_host_symbolic", "spgemm_host_numeric",
-            "spgemm_transpose_noalloc"]
+            "spgemm_transpose_noalloc", "spgemm_workspace_size_batched",
+            "spgemm_symbolic_batched", "spgemm_numeric_batched", "spgemm_merge_workspace_size",
+            "spgemm_merge_stages", "spgemm_merge_stages_batched", "spgemm_split_workspace_size",
+            "spgemm_split_columns"]
 
 
 @dataclass
@@ -124,10 +142,17 @@ class DeviceCSR:
     rp: "object"
     col: "object"
     val: "Optional[object]" = None
+    _nnz: "Optional[int]" = None   # entries of a row view (col/val are shared)
 
     @property
     def nnz(self) -> int:
-        return int(self.col.numel())
+        return int(self.col.numel()) if self._nnz is None else self._nnz
+
+    def rows(self, r0: int, r1: int) -> "DeviceCSR":
+        """Row view [r0, r1): row pointers offset, same column/value arrays
+        (the kernels address entries by the absolute offsets in row_ptr)."""
+        return DeviceCSR(r1 - r0, self.ncols, self.rp[r0:r1 + 1], self.col, self.val,
+                         _nnz=int((self.rp[r1] - self.rp[r0]).item()) if r1 > r0 else 0)
 
     def c(self) -> spg_csr:
         return spg_csr(self.nrows, self.ncols, self.nnz, self.rp.data_ptr(),
@@ -270,6 +295,105 @@ class Handle:
             ws.data_ptr(), ws.numel(), _stream_ptr(stream)))
         return DeviceCSR(A.ncols, A.nrows, t_rp, t_col, t_val)
 
+    # ---- batched products, merges, splits -------------------------------------
+
+    @staticmethod
+    def _ptrs(tensors):
+        arr = (ctypes.c_void_p * len(tensors))()
+        for i, t in enumerate(tensors):
+            arr[i] = None if t is None or t.numel() == 0 else t.data_ptr()
+        return arr
+
+    def workspace_size_batched(self, sr, As, Bs) -> int:
+        a = (spg_csr * len(As))(*[x.c() for x in As])
+        b = (spg_csr * len(Bs))(*[x.c() for x in Bs])
+        n = ctypes.c_size_t()
+        self._ok(self.lib.spgemm_workspace_size_batched(self._h, sr, len(As), a, b,
+                                                        ctypes.byref(n)))
+        return n.value
+
+    def symbolic_batched(self, sr, As, Bs, c_rps, ws, stream=None):
+        a = (spg_csr * len(As))(*[x.c() for x in As])
+        b = (spg_csr * len(Bs))(*[x.c() for x in Bs])
+        nnz = (ctypes.c_int64 * len(As))()
+        self._ok(self.lib.spgemm_symbolic_batched(self._h, sr, len(As), a, b, self._ptrs(c_rps),
+                                                  nnz, ws.data_ptr(), ws.numel(),
+                                                  _stream_ptr(stream)))
+        return list(nnz)
+
+    def numeric_batched(self, sr, As, Bs, c_rps, c_cols, c_vals, ws, stream=None):
+        a = (spg_csr * len(As))(*[x.c() for x in As])
+        b = (spg_csr * len(Bs))(*[x.c() for x in Bs])
+        self._ok(self.lib.spgemm_numeric_batched(
+            self._h, sr, len(As), a, b, self._ptrs(c_rps), self._ptrs(c_cols),
+            self._ptrs(c_vals) if c_vals is not None else None, ws.data_ptr(), ws.numel(),
+            _stream_ptr(stream)))
+
+    def merge_workspace_size(self, sr, groups) -> int:
+        flat = [p for g in groups for p in g]
+        parts = (spg_csr * len(flat))(*[p.c() for p in flat])
+        npart = (ctypes.c_int * len(groups))(*[len(g) for g in groups])
+        n = ctypes.c_size_t()
+        self._ok(self.lib.spgemm_merge_workspace_size(self._h, sr, len(groups), npart, parts,
+                                                      ctypes.byref(n)))
+        return n.value
+
+    def merge_count(self, sr, groups, c_rps, ws, stream=None):
+        flat = [p for g in groups for p in g]
+        parts = (spg_csr * len(flat))(*[p.c() for p in flat])
+        npart = (ctypes.c_int * len(groups))(*[len(g) for g in groups])
+        nnz = (ctypes.c_int64 * len(groups))()
+        self._ok(self.lib.spgemm_merge_stages_batched(
+            self._h, sr, len(groups), npart, parts, self._ptrs(c_rps), nnz, None, None,
+            ws.data_ptr(), ws.numel(), _stream_ptr(stream)))
+        return list(nnz)
+
+    def merge_write(self, sr, groups, c_rps, c_cols, c_vals, ws, stream=None):
+        flat = [p for g in groups for p in g]
+        parts = (spg_csr * len(flat))(*[p.c() for p in flat])
+        npart = (ctypes.c_int * len(groups))(*[len(g) for g in groups])
+        self._ok(self.lib.spgemm_merge_stages_batched(
+            self._h, sr, len(groups), npart, parts, self._ptrs(c_rps), None, self._ptrs(c_cols),
+            self._ptrs(c_vals) if c_vals is not None else None, ws.data_ptr(), ws.numel(),
+            _stream_ptr(stream)))
+
+    def split_columns(self, M: DeviceCSR, cuts, value_bytes: int, stream=None):
+        """Column parts of M (local column ids); returns a list of DeviceCSR."""
+        import torch
+        nparts = len(cuts) - 1
+        m = M.c()
+        n = ctypes.c_size_t()
+        self._ok(self.lib.spgemm_split_workspace_size(self._h, ctypes.byref(m), nparts,
+                                                      ctypes.byref(n)))
+        dev = M.rp.device
+        ws = torch.empty(max(n.value, 1), dtype=torch.uint8, device=dev)
+        prp = torch.empty(nparts * (M.nrows + 1), dtype=torch.int64, device=dev)
+        pcol = torch.empty(max(M.nnz, 1), dtype=torch.int32, device=dev)
+        pval = None
+        if value_bytes:
+            pval = torch.empty(max(M.nnz, 1) * value_bytes, dtype=torch.uint8, device=dev)
+        cuts_arr = (ctypes.c_int32 * len(cuts))(*[int(c) for c in cuts])
+        pnnz = (ctypes.c_int64 * nparts)()
+        self._ok(self.lib.spgemm_split_columns(
+            self._h, ctypes.byref(m), nparts, cuts_arr, value_bytes, prp.data_ptr(),
+            pcol.data_ptr(), None if pval is None else pval.data_ptr(), pnnz, ws.data_ptr(),
+            ws.numel(), _stream_ptr(stream)))
+        out, base = [], 0
+        for p in range(nparts):
+            k = int(pnnz[p])
+            rp = prp[p * (M.nrows + 1):(p + 1) * (M.nrows + 1)]
+            col = pcol[base:base + k]
+            val = None
+            if pval is not None:
+                val = pval[base * value_bytes:(base + k) * value_bytes]
+                if M.val is not None:
+                    val = val.view(M.val.dtype)
+                    if M.val.dim() > 1:
+                        val = val.reshape((-1,) + tuple(M.val.shape[1:]))
+            out.append(DeviceCSR(M.nrows, int(cuts[p + 1] - cuts[p]), rp, col, val))
+            base += k
+        return out
+
     def validate(self, M: DeviceCSR, ws, stream=None):
         m = M.c()
         self._ok(self.lib.spgemm_validate_csr(self._h, ctypes.byref(m), ws.data_ptr(),
@@ -303,6 +427,18 @@ def spgemm(sr: int, A: DeviceCSR, B: DeviceCSR, handle: Optional[Handle] = None,
     if check:
         h.check(ws)
     return DeviceCSR(A.nrows, B.ncols, c_rp, c_col, c_val)
+
+
+def typed_out(sr: int, raw):
+    """View a raw uint8 device buffer as the semiring's output values."""
+    import torch
+    if raw is None or sr == BOOL_OR_AND:
+        return None
+    if sr == OVERLAP_I32:
+        return raw.view(torch.int32).reshape(-1, 5)
+    dt = {PLUS_TIMES_F64: torch.float64, MIN_PLUS_F32: torch.float32,
+          PLUS_TIMES_I64: torch.int64, PLUS_TIMES_F32: torch.float32}[sr]
+    return raw.view(dt)
 
 
 def to_host(C: DeviceCSR, sr: int):

@@ -1,0 +1,187 @@
+"""Sparse SUMMA on one GPU: the block-grid emulation of the paper's distributed
+multiply (Section 2.1, Fig. "2.5D" for the grid; merge of stage partials:
+Section 3.4).
+
+A q x q process grid owns block (I, J) of C.  At stage s, block A(I, s) is
+broadcast along grid row I and B(s, J) along grid column J, and every grid
+point multiplies them; C(I, J) is the (+)-merge of its q stage partials.
+Here the q^3 block products of all stages are one batched call (one
+persistent launch per kernel tier over every block's rows, heaviest first),
+and the q^2 merges are one batched merge call.  The numeric phase and the
+merge can be captured once into a CUDA graph and replayed.
+
+Blocks are views: A's columns are split into the q stage ranges and B's into
+the q column ranges (spgemm_split_columns, on the GPU); block (I, s) is the
+row range I of column part s (row views need no copy).
+
+This module only orders library calls and allocates their buffers with
+torch; every step runs in the library's kernels.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+from typing import List, Optional
+
+import numpy as np
+
+from . import spgemm as api
+
+
+def even_cuts(n: int, q: int) -> List[int]:
+    return [(n * t) // q for t in range(q + 1)]
+
+
+@dataclass
+class Block:
+    I: int
+    J: int
+    s: int
+
+
+class Summa:
+    """C = A (x).(+) B emulated on a q x q Sparse-SUMMA grid.
+
+    row_cuts split A's rows (grid rows), inner_cuts split the inner dimension
+    (stages), col_cuts split B's columns (grid columns); defaults are even.
+    batched=False runs one library call per block product and per merge (the
+    plain form); batched=True one call for all of them.
+    """
+
+    def __init__(self, handle: api.Handle, sr: int, A: api.DeviceCSR, B: api.DeviceCSR,
+                 q: int = 4, row_cuts=None, inner_cuts=None, col_cuts=None,
+                 batched: bool = True):
+        import torch
+        self.h, self.sr, self.q, self.batched = handle, sr, q, batched
+        self.A, self.B = A, B
+        self.row_cuts = list(row_cuts or even_cuts(A.nrows, q))
+        self.inner_cuts = list(inner_cuts or even_cuts(A.ncols, q))
+        self.col_cuts = list(col_cuts or even_cuts(B.ncols, q))
+        vb = api.IN_NP[sr] and np.dtype(api.IN_NP[sr]).itemsize or 0
+        self.vb = vb
+        self.Ap = handle.split_columns(A, self.inner_cuts, vb)   # stage parts of A
+        self.Bp = handle.split_columns(B, self.col_cuts, vb)     # column parts of B
+        self.blocks = [Block(I, J, s) for s in range(q) for I in range(q) for J in range(q)]
+        self.As = [self.Ap[b.s].rows(self.row_cuts[b.I], self.row_cuts[b.I + 1]) for b in self.blocks]
+        self.Bs = [self.Bp[b.J].rows(self.inner_cuts[b.s], self.inner_cuts[b.s + 1])
+                   for b in self.blocks]
+        self.dev = A.rp.device
+        self._torch = torch
+        self.graph = None
+
+    # ---- phase 1: block products -------------------------------------------------
+
+    def symbolic(self):
+        torch = self._torch
+        self.p_rp = [torch.empty(a.nrows + 1, dtype=torch.int64, device=self.dev) for a in self.As]
+        if self.batched:
+            self.ws = torch.empty(self.h.workspace_size_batched(self.sr, self.As, self.Bs),
+                                  dtype=torch.uint8, device=self.dev)
+            self.p_nnz = self.h.symbolic_batched(self.sr, self.As, self.Bs, self.p_rp, self.ws)
+        else:
+            size = max(self.h.workspace_size(self.sr, a, b) for a, b in zip(self.As, self.Bs))
+            self.ws = torch.empty(size, dtype=torch.uint8, device=self.dev)
+            self.p_nnz = [self.h.symbolic(self.sr, a, b, rp, self.ws)
+                          for a, b, rp in zip(self.As, self.Bs, self.p_rp)]
+        self.products = self.h.stats()["products"] if self.batched else None
+        # one buffer for all partials, sliced per block
+        tot = int(sum(self.p_nnz))
+        self._pcol = torch.empty(max(tot, 1), dtype=torch.int32, device=self.dev)
+        ob = api.OUT_BYTES[self.sr]
+        self._pval = torch.empty(max(tot, 1) * ob, dtype=torch.uint8, device=self.dev) if ob else None
+        self.p_col, self.p_val, off = [], [], 0
+        for n in self.p_nnz:
+            self.p_col.append(self._pcol[off:off + n])
+            self.p_val.append(None if ob == 0 else self._pval[off * ob:(off + n) * ob])
+            off += n
+        self.partials = [api.DeviceCSR(a.nrows, b.ncols, rp, c, v)
+                         for a, b, rp, c, v in zip(self.As, self.Bs, self.p_rp, self.p_col,
+                                                    self.p_val)]
+
+    def numeric(self):
+        if self.batched:
+            self.h.numeric_batched(self.sr, self.As, self.Bs, self.p_rp, self.p_col,
+                                   self.p_val if self._pval is not None else None, self.ws)
+        else:
+            for a, b, rp, c, v in zip(self.As, self.Bs, self.p_rp, self.p_col, self.p_val):
+                self.h.numeric(self.sr, a, b, rp, c, v, self.ws)
+
+    # ---- phase 2: merge of the stage partials of every C block ------------------
+
+    def _groups(self):
+        q = self.q
+        idx = {(b.I, b.J, b.s): k for k, b in enumerate(self.blocks)}
+        return [[self.partials[idx[(I, J, s)]] for s in range(q)]
+                for I in range(q) for J in range(q)]
+
+    def merge_count(self):
+        torch = self._torch
+        groups = self._groups()
+        self.groups = groups
+        self.c_rp = [torch.empty(g[0].nrows + 1, dtype=torch.int64, device=self.dev) for g in groups]
+        if self.batched:
+            self.mws = torch.empty(self.h.merge_workspace_size(self.sr, groups), dtype=torch.uint8,
+                                   device=self.dev)
+            self.c_nnz = self.h.merge_count(self.sr, groups, self.c_rp, self.mws)
+            self._mws_per_group = None
+        else:
+            self._mws_per_group = [torch.empty(self.h.merge_workspace_size(self.sr, [g]),
+                                               dtype=torch.uint8, device=self.dev) for g in groups]
+            self.c_nnz = [self.h.merge_count(self.sr, [g], [rp], w)[0]
+                          for g, rp, w in zip(groups, self.c_rp, self._mws_per_group)]
+        ob = api.OUT_BYTES[self.sr]
+        self.c_col = [torch.empty(max(n, 1), dtype=torch.int32, device=self.dev) for n in self.c_nnz]
+        self.c_val = [torch.empty(max(n, 1) * ob, dtype=torch.uint8, device=self.dev) if ob else None
+                      for n in self.c_nnz]
+
+    def merge_write(self):
+        if self.batched:
+            self.h.merge_write(self.sr, self.groups, self.c_rp, self.c_col,
+                               self.c_val if api.OUT_BYTES[self.sr] else None, self.mws)
+        else:
+            for g, rp, c, v, w in zip(self.groups, self.c_rp, self.c_col, self.c_val,
+                                      self._mws_per_group):
+                self.h.merge_write(self.sr, [g], [rp], [c], [v] if v is not None else None, w)
+
+    # ---- whole product ---------------------------------------------------------
+
+    def plan(self):
+        """Symbolic phase of the blocks and of the merges (sizes every buffer)."""
+        self.symbolic()
+        self.numeric()          # partial values are needed by nothing in the count,
+        self.merge_count()      # but running them once warms the kernels up
+
+    def run(self):
+        """Numeric phase of every block product and the merges (replays the
+        CUDA graph if one was captured)."""
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self.numeric()
+            self.merge_write()
+
+    def capture(self):
+        """Capture numeric + merge write into one CUDA graph."""
+        torch = self._torch
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.numeric()        # warm-up outside the graph
+            self.merge_write()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.numeric()
+            self.merge_write()
+        self.graph = g
+        return g
+
+    def block(self, I: int, J: int) -> api.DeviceCSR:
+        k = I * self.q + J
+        ob = api.OUT_BYTES[self.sr]
+        val = self.c_val[k]
+        if val is not None:
+            val = api.typed_out(self.sr, val[:self.c_nnz[k] * ob])
+        return api.DeviceCSR(self.row_cuts[I + 1] - self.row_cuts[I],
+                             self.col_cuts[J + 1] - self.col_cuts[J], self.c_rp[k],
+                             self.c_col[k][:self.c_nnz[k]], val)
