@@ -1,0 +1,129 @@
+"""Autotuner of the kernel tier limits (the counterpart of the paper's GALATIC
+configuration knobs, Section 3.3: threads, threads per nonzero and chunk
+limits were set by hand there).
+
+Coordinate descent over the spg_tuning fields on a calibration product: each
+field in turn is tried at a few values around the current one, the whole
+symbolic + numeric call is timed with CUDA events (median of a few runs),
+and the best value is kept; sweeps repeat until no field improves.  The
+tuning changes only which kernel tier handles a row and how wide the
+shared-memory slabs are, never C.  Results are cached in a JSON file keyed
+by GPU name, semiring and workload tag.
+"""
+from __future__ import annotations
+
+import json
+import os
+import statistics
+from typing import Dict, Optional
+
+from . import spgemm as api
+
+# candidate values per field (0 = library default)
+SPACE = {
+    "sym_warp_max_ub": [128, 256, 512, 1024, 2048],
+    "sym_block_max_ub": [2048, 4096, 8192, 16384],
+    "num_warp_max_nnz": [32, 64, 128, 256, 512],
+    "num_block_max_nnz": [512, 1024, 2048, 4096],
+    "dense_slab_cols": [8192, 16384, 32768],
+}
+
+DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "spgemm_gb300_tuning.json")
+
+
+def _time_call(h: api.Handle, sr, dA, dB, ws, c_rp, c_col, c_val, reps: int) -> float:
+    import torch
+    ts = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        h.symbolic(sr, dA, dB, c_rp, ws)
+        h.numeric(sr, dA, dB, c_rp, c_col, c_val, ws)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def tune(sr: int, dA: api.DeviceCSR, dB: api.DeviceCSR, reps: int = 3, sweeps: int = 2,
+         start: Optional[Dict[str, int]] = None, log=None) -> Dict[str, int]:
+    """Coordinate descent; returns the best tuning found (dict of spg_tuning fields)."""
+    import torch
+    best = dict(start or {})
+    h = api.Handle(tuning=best or None)
+    c_rp = torch.empty(dA.nrows + 1, dtype=torch.int64, device=dA.rp.device)
+    # buffers sized once (nnz(C) does not depend on the tuning)
+    ws_size = max(h.workspace_size(sr, dA, dB), 1)
+    ws = torch.empty(ws_size, dtype=torch.uint8, device=dA.rp.device)
+    nnz = h.symbolic(sr, dA, dB, c_rp, ws)
+    c_col = torch.empty(max(nnz, 1), dtype=torch.int32, device=dA.rp.device)
+    c_val = api.out_tensor(sr, max(nnz, 1), dA.rp.device)
+
+    def measure(cfg):
+        hh = api.Handle(tuning=cfg or None)
+        need = hh.workspace_size(sr, dA, dB)
+        nonlocal ws
+        if need > ws.numel():
+            ws = torch.empty(need, dtype=torch.uint8, device=dA.rp.device)
+        _time_call(hh, sr, dA, dB, ws, c_rp, c_col, c_val, 1)   # warm-up
+        return _time_call(hh, sr, dA, dB, ws, c_rp, c_col, c_val, reps)
+
+    best_t = measure(best)
+    if log:
+        log(f"start {best} {best_t:.3f} ms")
+    for _ in range(sweeps):
+        improved = False
+        for field, cands in SPACE.items():
+            for v in cands:
+                if best.get(field) == v:
+                    continue
+                cfg = dict(best, **{field: v})
+                t = measure(cfg)
+                if log:
+                    log(f"  {field}={v}: {t:.3f} ms")
+                if t < best_t * 0.99:
+                    best, best_t, improved = cfg, t, True
+        if not improved:
+            break
+    if log:
+        log(f"best {best} {best_t:.3f} ms")
+    return best
+
+
+def cache_key(sr: int, tag: str) -> str:
+    import torch
+    return f"{torch.cuda.get_device_name()}|{api.SEMIRING_NAMES[sr]}|{tag}"
+
+
+def load(sr: int, tag: str, path: str = DEFAULT_CACHE) -> Optional[Dict[str, int]]:
+    try:
+        with open(path) as f:
+            return json.load(f).get(cache_key(sr, tag))
+    except (OSError, ValueError):
+        return None
+
+
+def save(sr: int, tag: str, tuning: Dict[str, int], path: str = DEFAULT_CACHE) -> None:
+    os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+    data = {}
+    try:
+        with open(path) as f:
+            data = json.load(f)
+    except (OSError, ValueError):
+        pass
+    data[cache_key(sr, tag)] = tuning
+    tmp = path + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def tuned_handle(sr: int, dA, dB, tag: str, path: str = DEFAULT_CACHE, **kw) -> api.Handle:
+    """Handle with the cached tuning for (GPU, semiring, tag), tuning first if absent."""
+    t = load(sr, tag, path)
+    if t is None:
+        t = tune(sr, dA, dB, **kw)
+        save(sr, tag, t, path)
+    return api.Handle(tuning=t or None)

@@ -316,10 +316,11 @@ SPG_DEV void fill_slots(typename S::Slot* vals, int width) {
     using Slot = typename S::Slot;
     if constexpr (sizeof(Slot) == 4 || sizeof(Slot) == 8) {
         constexpr int per = 16 / (int)sizeof(Slot);
-        Slot e[per];
+        alignas(16) Slot e[per];
 #pragma unroll
         for (int u = 0; u < per; ++u) e[u] = S::empty();
-        const uint4 v = *reinterpret_cast<const uint4*>(e);
+        uint4 v;
+        memcpy(&v, e, sizeof v);
         uint4* v4 = reinterpret_cast<uint4*>(vals);
         const int n4 = width / per;
         for (int c = threadIdx.x; c < n4; c += blockDim.x) v4[c] = v;
@@ -698,8 +699,9 @@ struct RankAccOp {
     const uint32_t* bm;
     const int32_t* word_off;
     int32_t r0;
+    int32_t clo, chi;   // columns of this pass (products outside are skipped)
     SPG_DEV void any(int32_t col, typename S::In a, typename S::In b, bool valid) {
-        if (!valid) return;
+        if (!valid || col < clo || col >= chi) return;
         const int w = col >> 5;
         const int r = word_off[w] + __popc(bm[w] & ((1u << (col & 31)) - 1u)) - r0;
         S::acc(vals + r, a, b);
@@ -707,6 +709,12 @@ struct RankAccOp {
 };
 
 constexpr int kRankThreads = 1024;
+
+// bytes of the rank kernel's value array, rounded up to 16
+template <class S>
+__host__ __device__ inline size_t rank_val_bytes(int64_t cap) {
+    return S::kVal ? (((size_t)cap * sizeof(typename S::Slot) + 15) & ~(size_t)15) : 0;
+}
 
 template <class S>
 __global__ void __launch_bounds__(kRankThreads, 1)
@@ -718,7 +726,8 @@ __global__ void __launch_bounds__(kRankThreads, 1)
     using In = typename S::In;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Slot* vals = reinterpret_cast<Slot*>(smem_raw);                          // [cap]
-    uint32_t* bm = reinterpret_cast<uint32_t*>(smem_raw + (S::kVal ? (size_t)cap * sizeof(Slot) : 0));
+    // the bitmap is filled with 16-byte copies: its offset must be 16-aligned
+    uint32_t* bm = reinterpret_cast<uint32_t*>(smem_raw + rank_val_bytes<S>(cap));
     int32_t* word_off = reinterpret_cast<int32_t*>(bm + bm_words);           // [words + 1]
     __shared__ BatchSmem<In, kRankThreads> bs;
     __shared__ int s_row;
@@ -830,9 +839,17 @@ __global__ void __launch_bounds__(kRankThreads, 1)
                 if (cnt > 0) {
                     fill_slots<S>(vals, cnt);
                     __syncthreads();
-                    RankAccOp<S> op{vals, bm, word_off, r0};
-                    cta_range_products<In, S::kVal>(P.A, P.B, a0, a1, le, small, sp, sp_stride,
-                                                    nslabs, s0, s1, bs, op);
+                    const int clo = s0 * slab_cols;
+                    const int chi = s1 >= nslabs ? ncols : s1 * slab_cols;
+                    RankAccOp<S> op{vals, bm, word_off, r0, clo, chi};
+                    // with the slab table the walk covers only the pass's slabs;
+                    // without it every product is visited and filtered
+                    if (sp != nullptr || (s0 == 0 && s1 >= nslabs))
+                        cta_range_products<In, S::kVal>(P.A, P.B, a0, a1, le, small, sp, sp_stride,
+                                                        nslabs, s0, s1, bs, op);
+                    else
+                        cta_range_products<In, S::kVal>(P.A, P.B, a0, a1, le, small, sp, sp_stride,
+                                                        nslabs, 0, nslabs, bs, op);
                     typename S::Out* cv = reinterpret_cast<typename S::Out*>(P.c_val) + off + r0;
                     for (int t = tid; t < cnt; t += blockDim.x) cv[t] = S::out(vals[t]);
                     __syncthreads();
@@ -960,13 +977,13 @@ struct NumericLaunch {
             const size_t fixed = (size_t)bm_words * 8 + 16;
             const size_t budget = 200 * 1024 - sizeof(BatchSmem<typename S::In, kRankThreads>) + 12 * 1024;
             int64_t cap = 0;
-            if (fixed < budget)
-                cap = S::kVal ? (int64_t)((budget - fixed) / sizeof(typename S::Slot)) : 0;
+            if (fixed + 16 < budget)
+                cap = S::kVal ? (int64_t)((budget - fixed - 16) / sizeof(typename S::Slot)) : 0;
             if (cap > (int64_t)1 << 30) cap = (int64_t)1 << 30;
-            const bool rank_ok = nprob == 1 && fixed < budget && (sp != nullptr || nslabs == 1) &&
-                                 (!S::kVal || cap >= slab) && max_ncols < INT32_MAX;
+            const bool rank_ok = fixed < budget && (!S::kVal || cap >= slab) &&
+                                 max_ncols < INT32_MAX;
             if (rank_ok) {
-                const size_t rsmem = (S::kVal ? (size_t)cap * sizeof(typename S::Slot) : 0) + fixed;
+                const size_t rsmem = rank_val_bytes<S>(cap) + fixed;
                 e = cudaFuncSetAttribute(k_num_rank<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)rsmem);
                 if (e != cudaSuccess) { err = e; return; }

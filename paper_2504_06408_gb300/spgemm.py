@@ -441,6 +441,66 @@ def typed_out(sr: int, raw):
     return raw.view(dt)
 
 
+def panel_product(sr: int, A: DeviceCSR, B: DeviceCSR, budget_bytes: int, on_panel,
+                  handle: Optional[Handle] = None):
+    """C = A (x).(+) B in row panels whose output fits in budget_bytes of device
+    memory (for products larger than HBM).  One symbolic call on all of A gives
+    the row counts; each panel (a row view of A) then runs symbolic + numeric
+    into a reused buffer and on_panel(r0, r1, C_panel) is called.  Returns
+    (nnz(C), number of panels)."""
+    import torch
+    h = handle or Handle()
+    dev = A.rp.device
+    c_rp = torch.empty(A.nrows + 1, dtype=torch.int64, device=dev)
+    ws = torch.empty(h.workspace_size(sr, A, B), dtype=torch.uint8, device=dev)
+    total = h.symbolic(sr, A, B, c_rp, ws)
+    del ws
+    per = 4 + OUT_BYTES[sr]
+    cap = max(1, budget_bytes // per)
+    rp = c_rp.cpu().numpy()
+    cuts, r0 = [0], 0
+    while r0 < A.nrows:
+        r1 = int(np.searchsorted(rp, rp[r0] + cap, side="right")) - 1
+        r1 = max(r1, r0 + 1)
+        r1 = min(r1, A.nrows)
+        cuts.append(r1)
+        r0 = r1
+    biggest = max(int(rp[b] - rp[a]) for a, b in zip(cuts[:-1], cuts[1:]))
+    col = torch.empty(max(biggest, 1), dtype=torch.int32, device=dev)
+    val = out_tensor(sr, max(biggest, 1), dev)
+    for a, b in zip(cuts[:-1], cuts[1:]):
+        Av = A.rows(a, b) if (a, b) != (0, A.nrows) else A
+        wsp = torch.empty(h.workspace_size(sr, Av, B), dtype=torch.uint8, device=dev)
+        prp = torch.empty(b - a + 1, dtype=torch.int64, device=dev)
+        n = h.symbolic(sr, Av, B, prp, wsp)
+        h.numeric(sr, Av, B, prp, col, val, wsp)
+        h.check(wsp)
+        on_panel(a, b, DeviceCSR(b - a, B.ncols, prp, col[:n], None if val is None else val[:n]))
+        del wsp
+    return total, len(cuts) - 1
+
+
+def to_host_rows(C: DeviceCSR, sr: int, rows):
+    """Rows `rows` (ascending) of a device result copied to numpy as one CSR."""
+    from types import SimpleNamespace
+    rp = C.rp.cpu().numpy()
+    rows = np.asarray(rows, dtype=np.int64)
+    lens = rp[rows + 1] - rp[rows]
+    orp = np.zeros(rows.size + 1, dtype=np.int64)
+    np.cumsum(lens, out=orp[1:])
+    cols, vals = [], []
+    for r in rows:
+        a, b = int(rp[r]), int(rp[r + 1])
+        cols.append(C.col[a:b].cpu().numpy())
+        if C.val is not None:
+            v = C.val[a:b].cpu().numpy()
+            vals.append(v.view(OVERLAP_NP).reshape(-1) if sr == OVERLAP_I32 else v)
+    col = np.concatenate(cols) if cols else np.zeros(0, np.int32)
+    val = (np.concatenate(vals) if vals else None) if C.val is not None else None
+    return SimpleNamespace(nrows=rows.size, ncols=C.ncols, rp=orp, col=col, val=val,
+                           nnz=int(orp[-1]))
+
+
 def to_host(C: DeviceCSR, sr: int):
     """Copy a device result to numpy (rp, col, val) with the semiring's dtypes."""
     from types import SimpleNamespace

@@ -1,0 +1,120 @@
+"""Parity at the full sizes of the benchmark configurations, on sampled rows
+the oracle computes one by one (stratified: the heaviest rows, random rows of
+every size, empty rows), plus properties that hold at any size.
+
+* R-MAT 18 A^2 (262,144 vertices), min-plus FP32 and boolean: exactly the
+  bench product and launch configuration.
+* k-mer reads x k-mers (200,000 x 2^24), C = A A^T over the overlap semiring,
+  A^T by the GPU transpose.
+* 5-point Laplacian on a 2048 x 2048 grid, A^2 plus-times FP64: every entry
+  against the closed form.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from _util import abs_csr, assert_pattern_equal, assert_values
+from paper_2504_06408_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a GPU", allow_module_level=True)
+
+import __graft_entry__  # noqa: E402
+
+__graft_entry__.build()
+from paper_2504_06408_gb300 import spgemm as api  # noqa: E402
+
+
+def sample_rows(ub, k_heavy=20, k_rand=300, seed=0, max_products=3e8):
+    """The heaviest rows, random non-empty rows, a few empty rows; bounded work."""
+    rng = np.random.default_rng(seed)
+    order = np.argsort(-ub, kind="stable")
+    heavy = order[:k_heavy]
+    nz = np.nonzero(ub > 0)[0]
+    rand = rng.choice(nz, min(k_rand, nz.size), replace=False)
+    empty = np.nonzero(ub == 0)[0][:5]
+    rows = np.unique(np.concatenate([heavy, rand, empty]))
+    # keep the work bounded: drop the heaviest first while over budget
+    while ub[rows].sum() > max_products and rows.size > 10:
+        rows = rows[rows != rows[np.argmax(ub[rows])]]
+    return rows
+
+
+def check_rows(sr, A, B, C_dev, rows, row_offset=0):
+    got = api.to_host_rows(C_dev, sr, np.asarray(rows) - row_offset)
+    exp = oracle.spgemm(sr, A, B, rows=rows)
+    assert_pattern_equal(got.rp, got.col, exp.rp, exp.col, f"{len(rows)} sampled rows")
+    if sr == api.PLUS_TIMES_F64:
+        bound = oracle.spgemm(sr, abs_csr(A), abs_csr(B), rows=rows)
+        assert_values(sr, got.val, exp.val, bound=bound.val)
+    elif sr != api.BOOL_OR_AND:
+        assert_values(sr, got.val, exp.val)
+
+
+@pytest.mark.parametrize("sr", [api.MIN_PLUS_F32, api.BOOL_OR_AND])
+def test_rmat18_bench_product(sr):
+    A = I.rmat(18, dtype=np.float32, seed=1)
+    if sr == api.BOOL_OR_AND:
+        A = A.with_values(None)
+    h = api.Handle()
+    dA = api.DeviceCSR.from_host(A, val_dtype=api.IN_NP[sr])
+    C = api.spgemm(sr, dA, dA, handle=h)
+    st = h.stats()
+    assert st["products"] == 9480977744
+    assert C.nnz == 2957756203
+    ub = oracle.row_upper_bounds(A, A)
+    # row sums of the counts equal the scanned row pointers' differences
+    rp = C.rp.cpu().numpy()
+    assert rp[0] == 0 and np.all(np.diff(rp) >= 0) and np.all(np.diff(rp) <= ub)
+    check_rows(sr, A, A, C, sample_rows(ub))
+    if sr == api.MIN_PLUS_F32:   # symmetric weights: C[i,i] = 2 x lightest edge
+        rows = sample_rows(ub, k_rand=2000, seed=5)
+        rows = rows[ub[rows] > 0]
+        got = api.to_host_rows(C, sr, rows)
+        for t, i in enumerate(rows):
+            seg = got.col[got.rp[t]:got.rp[t + 1]]
+            p = np.searchsorted(seg, i)
+            assert seg[p] == i
+            w = A.val[A.rp[i]:A.rp[i + 1]]
+            assert got.val[got.rp[t] + p] == np.float32(2) * w.min()
+
+
+def test_kmer_full_overlap():
+    A = I.kmer(seed=1)                     # 200,000 x 2^24, ~25M nnz
+    h = api.Handle()
+    dA = api.DeviceCSR.from_host(A, val_dtype=np.int32)
+    dAt = h.transpose(dA, 4)
+    C = api.spgemm(api.OVERLAP_I32, dA, dAt, handle=h)
+    At = oracle.transpose(A, np.int32)
+    ub = oracle.row_upper_bounds(A, At)
+    rows = sample_rows(ub, k_heavy=20, k_rand=400)
+    check_rows(api.OVERLAP_I32, A, At, C, rows)
+    # diagonal of every sampled row: {len, (0,0), (1,1)}
+    got = api.to_host_rows(C, api.OVERLAP_I32, rows)
+    for t, i in enumerate(rows):
+        seg = got.col[got.rp[t]:got.rp[t + 1]]
+        p = np.searchsorted(seg, i)
+        r = got.val[got.rp[t] + p]
+        assert (r["count"], r["a0"], r["b0"], r["a1"], r["b1"]) == (A.rp[i + 1] - A.rp[i], 0, 0, 1, 1)
+
+
+def test_laplacian2048_closed_form():
+    g = 2048
+    L = I.laplacian(g)
+    dL = api.DeviceCSR.from_host(L, val_dtype=np.float64)
+    C = api.to_host(api.spgemm(api.PLUS_TIMES_F64, dL, dL), api.PLUS_TIMES_F64)
+    assert C.nnz == g * g + 4 * g * (g - 1) + 4 * g * (g - 2) + 4 * (g - 1) ** 2
+    n = g * g
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(C.rp))
+    x, y = rows % g, rows // g
+    cx, cy = C.col.astype(np.int64) % g, C.col.astype(np.int64) // g
+    dx, dy = cx - x, cy - y
+    nb = (x > 0).astype(int) + (x < g - 1) + (y > 0) + (y < g - 1)
+    exp = np.where((dx == 0) & (dy == 0), 16.0 + nb,
+          np.where(np.abs(dx) + np.abs(dy) == 1, -8.0,
+          np.where((np.abs(dx) == 1) & (np.abs(dy) == 1), 2.0,
+          np.where(((np.abs(dx) == 2) & (dy == 0)) | ((dx == 0) & (np.abs(dy) == 2)), 1.0, np.nan))))
+    assert np.array_equal(C.val, exp)   # small integers: exact in FP64
