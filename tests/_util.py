@@ -43,6 +43,9 @@ def assert_values(sr, got, exp, bound=None, terms=None, what=""):
         return
     got = np.asarray(got)
     exp = np.asarray(exp)
+    assert got.shape == exp.shape, f"{what}: {got.shape} values, expected {exp.shape}"
+    if got.size == 0:
+        return
     if sr == oracle.SR_PT_F64:
         assert bound is not None
         err = np.abs(got - exp)
