@@ -101,7 +101,11 @@ typedef struct {
     int64_t nnz_c;              /* nnz(C)                                                */
     int64_t rows_per_tier[4];   /* symbolic rows: dense, block, warp, empty              */
     int64_t launches;           /* kernels launched by the last symbolic / numeric call   */
-    int64_t reserved[5];
+    int64_t learned_rows;       /* learned path: rows finished without the symbolic pass  */
+    int64_t overflow_rows;      /* learned path: rows whose capacity was too small         */
+    int64_t staging_entries;    /* learned path: sum of the capacities of learned rows     */
+    int64_t learned_nnz;        /* learned path: nnz(C) of the rows it finished            */
+    int64_t reserved[1];
 } spg_stats;
 
 typedef struct spg_handle spg_handle;
@@ -241,9 +245,10 @@ spg_status spgemm_set_timing(spg_handle* handle, int enable);
  * (waits for its last event).  ms must hold SPG_STAGE_COUNT floats, indexed:
  *  1 analysis+binning  2 symbolic dense  3 symbolic block  4 symbolic warp
  *  5 scan              6 numeric binning 7 slab table      8 numeric dense
- *  9 numeric block    10 numeric warp   11 stage merge     (0 unused)
+ *  9 numeric block    10 numeric warp   11 stage merge    12 learned path
+ *  (0 unused)
  */
-#define SPG_STAGE_COUNT 12
+#define SPG_STAGE_COUNT 13
 spg_status spgemm_get_stage_times(spg_handle* handle, float* ms, int n);
 
 /*
@@ -304,6 +309,117 @@ spg_status spgemm_transpose(spg_handle* handle, const spg_csr* A, int value_byte
  */
 spg_status spgemm_transpose_noalloc(const spg_csr* A, int value_bytes, int64_t* t_row_ptr,
                                     int32_t* t_col, void* t_val, void* stream);
+
+/*
+ * ---- Learned output sizing -------------------------------------------------
+ * The paper sizes every output row by a symbolic pass (Section 2.1,
+ * Gustavson).  Here a small network predicts r_i = nnz(C_i) / ub_i, with
+ * ub_i = sum_{k in A_i} nnz(B_k) the row's product count, so that rows with a
+ * small predicted output go straight to a numeric pass into a staging area of
+ * capacity cap_i and skip the symbolic pass.  A row that finds more distinct
+ * columns than cap_i stops and is redone by the exact symbolic + numeric
+ * kernels: C is always exactly the C of spgemm_symbolic + spgemm_numeric
+ * (bit-identical for every semiring but the floating plus-times ones, whose
+ * atomic summation order is free).  Single products only (no batches).
+ *
+ * Network (spgemm_mlp_*): features f_i = log1p of (nnz(A_i), ub_i,
+ * max_k nnz(B_k), mean_k nnz(B_k)); 4 -> 64 -> 64 -> 1, ReLU, r = sigmoid(z).
+ * Parameters: SPGEMM_MLP_PARAMS values in the order W1[64][4] b1[64]
+ * W2[64][64] b2[64] W3[64] b3 (row-major, W[out][in]); BF16 on the device for
+ * inference, FP32 master copy for training.  Features, hidden activations
+ * and weights are rounded to BF16; every sum accumulates in FP32.
+ */
+#define SPGEMM_MLP_PARAMS 4545
+
+typedef struct {
+    const void* model;     /* device BF16 [SPGEMM_MLP_PARAMS], or NULL: cap_i = min(ub_i, ncols)
+                              (the "ub-sized" path: no prediction)                               */
+    float margin;          /* cap_i = ceil(ub_i * r_i * margin), clamped to [1, min(ub_i, ncols)];
+                              <= 0: 1.0                                                           */
+    int64_t exact_max_ub;  /* rows with ub_i <= this use cap_i = min(ub_i, ncols) (0: 64)        */
+    int64_t learned_max;   /* rows with cap_i above this take the exact path (0: 2048; clamped to
+                              what one CTA's shared-memory table holds for the semiring)         */
+    int64_t reserved[4];
+} spg_learned_opts;
+
+/*
+ * Workspace of the learned path: the plain path's workspace plus about 30
+ * bytes per row of A.  The same workspace goes to the plan, symbolic and numeric
+ * calls, unchanged in between.
+ */
+spg_status spgemm_learned_workspace_size(spg_handle* handle, spg_semiring sr, const spg_csr* A,
+                                         const spg_csr* B, size_t* bytes);
+
+/*
+ * Step 1: row features, network inference, capacities and staging offsets.
+ *   opts          : HOST, may be NULL (all defaults, no model)
+ *   staging_bytes : HOST, written: bytes of the staging buffer that steps 2
+ *                   and 3 need (columns + values of sum cap_i entries).
+ * Synchronises `stream`.
+ */
+spg_status spgemm_learned_plan(spg_handle* handle, spg_semiring sr, const spg_csr* A,
+                               const spg_csr* B, const spg_learned_opts* opts, void* workspace,
+                               size_t workspace_bytes, size_t* staging_bytes, void* stream);
+
+/*
+ * Step 2: learned rows accumulate into staging; overflowing and large rows
+ * run the exact symbolic pass; all counts are scanned into C's row pointers.
+ *   c_row_ptr : device int64 [A.nrows + 1], written;  c_nnz : HOST, written.
+ *   staging   : device buffer of at least staging_bytes (from step 1).
+ * Synchronises `stream`.  spgemm_get_stats then reports learned_rows,
+ * overflow_rows and staging_entries.
+ */
+spg_status spgemm_learned_symbolic(spg_handle* handle, spg_semiring sr, const spg_csr* A,
+                                   const spg_csr* B, int64_t* c_row_ptr, int64_t* c_nnz,
+                                   void* workspace, size_t workspace_bytes, void* staging,
+                                   size_t staging_bytes, void* stream);
+
+/*
+ * Step 3: learned rows are copied from staging into C; the other rows run the
+ * plain numeric kernels.  Output arguments as spgemm_numeric.  A and B must
+ * be those of steps 1-2, unchanged (learned rows' values were computed in
+ * step 2).  Asynchronous.
+ */
+spg_status spgemm_learned_numeric(spg_handle* handle, spg_semiring sr, const spg_csr* A,
+                                  const spg_csr* B, const int64_t* c_row_ptr, int32_t* c_col,
+                                  void* c_val, void* workspace, size_t workspace_bytes,
+                                  const void* staging, size_t staging_bytes, void* stream);
+
+/*
+ * Row features of C = A B for the network: feat device float [A.nrows][4];
+ * ub device int64 [A.nrows] (product count per row) or NULL.  Asynchronous.
+ * workspace: any workspace valid for spgemm_symbolic of A and B (only its
+ * head, the product descriptor, is written).
+ */
+spg_status spgemm_row_features(spg_handle* handle, const spg_csr* A, const spg_csr* B,
+                               float* feat, int64_t* ub, void* workspace, size_t workspace_bytes,
+                               void* stream);
+
+/* Inference: z device float [n] = network output (logit of r) for feat [n][4]. */
+spg_status spgemm_mlp_forward(spg_handle* handle, const float* feat, int64_t n,
+                              const void* params_bf16, float* z, void* stream);
+
+/*
+ * Training step pieces.  Loss (mean over the n rows) is the pinball loss of
+ * quantile tau on log r:  u = log_target - log sigmoid(z),
+ * L = tau * u if u > 0 else (tau - 1) * u.
+ *   spgemm_mlp_grad : grad device float [SPGEMM_MLP_PARAMS] = dL/dparams (at the
+ *                     BF16 weights), loss device float [1]; workspace of
+ *                     spgemm_mlp_train_workspace_size(n) bytes.
+ *   spgemm_mlp_adam : one Adam step (beta1 0.9, beta2 0.999, eps 1e-8; step
+ *                     counts from 1) on FP32 master weights, m, v (device
+ *                     float [SPGEMM_MLP_PARAMS] each), refreshing the BF16 copy.
+ *   spgemm_mlp_to_bf16 : BF16 copy of FP32 master weights.
+ * Asynchronous.
+ */
+size_t spgemm_mlp_train_workspace_size(int64_t n);
+spg_status spgemm_mlp_grad(spg_handle* handle, const float* feat, const float* log_target,
+                           int64_t n, float tau, const void* params_bf16, float* grad,
+                           float* loss, void* workspace, size_t workspace_bytes, void* stream);
+spg_status spgemm_mlp_adam(spg_handle* handle, float* master, float* m, float* v,
+                           const float* grad, void* params_bf16, float lr, int step, void* stream);
+spg_status spgemm_mlp_to_bf16(spg_handle* handle, const float* master, void* params_bf16,
+                              void* stream);
 
 #ifdef __cplusplus
 }

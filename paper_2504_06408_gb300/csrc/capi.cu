@@ -36,6 +36,9 @@ struct spg_handle {
     spg_csr hA{}, hB{};            // device descriptors of the last host-API inputs
     int host_sr = -1;
     int64_t host_nnz = -1;
+    // learned path: values fixed by the last spgemm_learned_plan
+    int lrn_sr = -1;
+    int64_t lrn_entries = -1, lrn_warp_max = 0, lrn_block_max = 0, lrn_rows = -1;
 };
 
 namespace spg {
@@ -832,6 +835,267 @@ spg_status spgemm_validate_csr(spg_handle* h, const spg_csr* M, void* workspace,
     WsPtrs w{};
     w.status = ds;
     return read_status(h, w, st);
+}
+
+}  // extern "C"
+
+// ---- learned output sizing --------------------------------------------------------
+
+struct LearnedLayout {
+    size_t feat, z, soff, route, skip, total;
+};
+
+static LearnedLayout learned_layout(const WsLayout& L) {
+    LearnedLayout M;
+    const size_t R = (size_t)L.R;
+    size_t o = L.total;
+    M.feat = o;  o = align256(o + 16 * R);
+    M.z = o;     o = align256(o + 4 * R);
+    M.soff = o;  o = align256(o + 8 * (R + 1));
+    M.route = o; o = align256(o + R);
+    M.skip = o;  o = align256(o + R);
+    M.total = o;
+    return M;
+}
+
+static size_t staging_bytes_for(int sr, int64_t S) {
+    if (S <= 0) return 0;
+    return align256((size_t)S * 4) + (size_t)S * (size_t)out_bytes(sr);
+}
+
+static LearnedWs learned_ptrs(void* ws, const LearnedLayout& M, void* staging, int64_t S) {
+    char* b = (char*)ws;
+    LearnedWs lw;
+    lw.feat = (float*)(b + M.feat);
+    lw.z = (float*)(b + M.z);
+    lw.soff = (int64_t*)(b + M.soff);
+    lw.route = (uint8_t*)(b + M.route);
+    lw.skip = (uint8_t*)(b + M.skip);
+    lw.scol = (int32_t*)staging;
+    lw.sval = staging ? (void*)((char*)staging + align256((size_t)S * 4)) : nullptr;
+    return lw;
+}
+
+extern "C" {
+
+spg_status spgemm_learned_workspace_size(spg_handle* h, spg_semiring sr, const spg_csr* A,
+                                         const spg_csr* B, size_t* bytes) {
+    spg_status s = check_pair(h, sr, A, B, false);
+    if (s != SPG_OK) return s;
+    if (!bytes) return fail(h, SPG_ERR_INVALID_ARG, "bytes is NULL");
+    *bytes = learned_layout(layout_for(A, B, effective_tuning(h, sr))).total;
+    return SPG_OK;
+}
+
+spg_status spgemm_learned_plan(spg_handle* h, spg_semiring sr, const spg_csr* A,
+                               const spg_csr* B, const spg_learned_opts* opts, void* workspace,
+                               size_t workspace_bytes, size_t* staging_bytes, void* stream) {
+    spg_status s = check_pair(h, sr, A, B, false);
+    if (s != SPG_OK) return s;
+    if (!staging_bytes) return fail(h, SPG_ERR_INVALID_ARG, "staging_bytes is NULL");
+    const Tuning t = effective_tuning(h, sr);
+    const WsLayout L = layout_for(A, B, t);
+    const LearnedLayout M = learned_layout(L);
+    if (!workspace || workspace_bytes < M.total)
+        return fail(h, SPG_ERR_WORKSPACE, "workspace needs %zu bytes", M.total);
+    const float margin = opts && opts->margin > 0.f ? opts->margin : 1.f;
+    const int64_t exact_max = opts && opts->exact_max_ub > 0 ? opts->exact_max_ub : 64;
+    const int64_t want = opts && opts->learned_max > 0 ? opts->learned_max : 2048;
+    const int64_t block_max = learned_capacity_limit(sr, want, false);
+    int64_t warp_max = t.num_warp_max_nnz < block_max ? t.num_warp_max_nnz : block_max;
+    warp_max = learned_capacity_limit(sr, warp_max, true);
+    const void* model = opts ? opts->model : nullptr;
+    cudaStream_t st = (cudaStream_t)stream;
+    const WsPtrs w = ws_ptrs(workspace, L);
+    const LearnedWs lw = learned_ptrs(workspace, M, nullptr, 0);
+    h->launches = 0;
+    h->timer.n = 0;
+    h->lrn_sr = -1;
+    cudaError_t e = cudaMemsetAsync(workspace, 0, L.probs, st);   // status + counters
+    if (e != cudaSuccess) return cuda_fail(h, e, "memset");
+    ProbTable* tab = new ProbTable;
+    int64_t* no_rp = nullptr;
+    fill_probs(tab, 1, A, B, &no_rp, nullptr, nullptr);
+    e = launch_write_probs(*tab, 1, w, h->dev, st);
+    delete tab;
+    if (e == cudaSuccess) e = launch_row_features(w.probs, 1, L.R, lw.feat, w.ub, h->dev, st);
+    if (e == cudaSuccess && model) e = launch_mlp_forward(lw.feat, L.R, model, lw.z, h->dev, st);
+    if (e == cudaSuccess)
+        e = launch_learned_caps(w, lw, 1, L.R, model ? lw.z : nullptr, margin, exact_max,
+                                block_max, h->dev, st);
+    int64_t* hs = (int64_t*)h->pinned;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hs, lw.soff + L.R, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "learned plan");
+    const int64_t S = hs[0];
+    h->lrn_sr = sr;
+    h->lrn_entries = S;
+    h->lrn_warp_max = warp_max;
+    h->lrn_block_max = block_max;
+    h->lrn_rows = L.R;
+    h->stats.staging_entries = S;
+    *staging_bytes = staging_bytes_for(sr, S);
+    return SPG_OK;
+}
+
+static spg_status learned_check(spg_handle* h, int sr, const spg_csr* A, const void* staging,
+                                size_t staging_bytes) {
+    if (h->lrn_sr != sr || h->lrn_rows != A->nrows)
+        return fail(h, SPG_ERR_INVALID_ARG, "call spgemm_learned_plan first (same semiring and A)");
+    const size_t need = staging_bytes_for(sr, h->lrn_entries);
+    if (need > 0 && (!staging || staging_bytes < need))
+        return fail(h, SPG_ERR_WORKSPACE, "staging needs %zu bytes", need);
+    return SPG_OK;
+}
+
+spg_status spgemm_learned_symbolic(spg_handle* h, spg_semiring sr, const spg_csr* A,
+                                   const spg_csr* B, int64_t* c_row_ptr, int64_t* c_nnz,
+                                   void* workspace, size_t workspace_bytes, void* staging,
+                                   size_t staging_bytes, void* stream) {
+    spg_status s = check_pair(h, sr, A, B, true);
+    if (s != SPG_OK) return s;
+    if (!c_row_ptr || !c_nnz) return fail(h, SPG_ERR_INVALID_ARG, "c_row_ptr / c_nnz is NULL");
+    s = learned_check(h, sr, A, staging, staging_bytes);
+    if (s != SPG_OK) return s;
+    const Tuning t = effective_tuning(h, sr);
+    const WsLayout L = layout_for(A, B, t);
+    const LearnedLayout M = learned_layout(L);
+    if (!workspace || workspace_bytes < M.total)
+        return fail(h, SPG_ERR_WORKSPACE, "workspace needs %zu bytes", M.total);
+    cudaStream_t st = (cudaStream_t)stream;
+    WsPtrs w = ws_ptrs(workspace, L);
+    const LearnedWs lw = learned_ptrs(workspace, M, staging, h->lrn_entries);
+    h->launches = 0;
+    h->timer.n = 0;
+    cudaError_t e = cudaMemsetAsync(workspace, 0, L.probs, st);
+    if (e == cudaSuccess && w.row_slot)
+        e = cudaMemsetAsync(w.row_slot, 0xff, sizeof(int32_t) * (size_t)L.R, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "memset");
+    ProbTable* tab = new ProbTable;
+    fill_probs(tab, 1, A, B, &c_row_ptr, nullptr, nullptr);
+    e = launch_write_probs(*tab, 1, w, h->dev, st);
+    delete tab;
+    if (e == cudaSuccess)
+        e = launch_learned_direct(sr, w, lw, 1, L.R, h->lrn_warp_max, h->lrn_block_max, h->dev, st);
+    w.skip = lw.skip;
+    if (e == cudaSuccess) e = launch_analyze(w, 1, L.R, t, h->dev, st);
+    if (e == cudaSuccess) e = launch_symbolic(w, 1, L.R, t, B->ncols, h->dev, st);
+    if (e == cudaSuccess) e = launch_scan_rowptr(w, 1, L.R, h->dev, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "learned symbolic launch");
+    Counters* hc = (Counters*)h->pinned;
+    e = cudaMemcpyAsync(hc, w.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "learned symbolic");
+    *c_nnz = hc->nnz[0];
+    h->stats.products = (int64_t)hc->products;
+    h->stats.nnz_c = hc->nnz[0];
+    for (int tier = 0; tier < kTiers; ++tier) {
+        int64_t n = 0;
+        for (int b = 0; b < kSubBins; ++b) n += hc->sym_bin_count[tier * kSubBins + b];
+        h->stats.rows_per_tier[tier] = n;
+    }
+    h->stats.overflow_rows = hc->claim[11];
+    h->stats.learned_rows = (int64_t)hc->claim[8] + hc->claim[9] - hc->claim[11];
+    h->stats.staging_entries = h->lrn_entries;
+    h->stats.learned_nnz = (int64_t)hc->learned_nnz;
+    return read_status(h, w, st);
+}
+
+spg_status spgemm_learned_numeric(spg_handle* h, spg_semiring sr, const spg_csr* A,
+                                  const spg_csr* B, const int64_t* c_row_ptr, int32_t* c_col,
+                                  void* c_val, void* workspace, size_t workspace_bytes,
+                                  const void* staging, size_t staging_bytes, void* stream) {
+    spg_status s = check_pair(h, sr, A, B, true);
+    if (s != SPG_OK) return s;
+    if (!c_row_ptr) return fail(h, SPG_ERR_INVALID_ARG, "c_row_ptr is NULL");
+    s = learned_check(h, sr, A, staging, staging_bytes);
+    if (s != SPG_OK) return s;
+    const Tuning t = effective_tuning(h, sr);
+    const WsLayout L = layout_for(A, B, t);
+    const LearnedLayout M = learned_layout(L);
+    if (!workspace || workspace_bytes < M.total)
+        return fail(h, SPG_ERR_WORKSPACE, "workspace needs %zu bytes", M.total);
+    cudaStream_t st = (cudaStream_t)stream;
+    WsPtrs w = ws_ptrs(workspace, L);
+    const LearnedWs lw = learned_ptrs(workspace, M, const_cast<void*>(staging), h->lrn_entries);
+    h->launches = 0;
+    h->timer.n = 0;
+    ProbTable* tab = new ProbTable;
+    int64_t* rp = const_cast<int64_t*>(c_row_ptr);
+    fill_probs(tab, 1, A, B, &rp, &c_col, &c_val);
+    cudaError_t e = launch_write_probs(*tab, 1, w, h->dev, st);
+    delete tab;
+    if (e == cudaSuccess) e = launch_learned_compact(sr, w, lw, 1, L.R, h->dev, st);
+    w.skip = lw.skip;
+    if (e == cudaSuccess) e = launch_numeric(sr, w, to_dcsr(B), 1, L.R, t, B->ncols, h->dev, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "learned numeric launch");
+    return SPG_OK;
+}
+
+spg_status spgemm_row_features(spg_handle* h, const spg_csr* A, const spg_csr* B, float* feat,
+                               int64_t* ub, void* workspace, size_t workspace_bytes,
+                               void* stream) {
+    spg_status s = check_pair(h, SPG_SR_BOOL_OR_AND, A, B, false);
+    if (s != SPG_OK) return s;
+    if (!feat && A->nrows > 0) return fail(h, SPG_ERR_INVALID_ARG, "feat is NULL");
+    const WsLayout L = layout_for(A, B, effective_tuning(h, SPG_SR_BOOL_OR_AND));
+    if (!workspace || workspace_bytes < L.ub)
+        return fail(h, SPG_ERR_WORKSPACE, "workspace needs %zu bytes", L.ub);
+    cudaStream_t st = (cudaStream_t)stream;
+    const WsPtrs w = ws_ptrs(workspace, L);
+    ProbTable* tab = new ProbTable;
+    int64_t* no_rp = nullptr;
+    fill_probs(tab, 1, A, B, &no_rp, nullptr, nullptr);
+    cudaError_t e = launch_write_probs(*tab, 1, w, h->dev, st);
+    delete tab;
+    if (e == cudaSuccess) e = launch_row_features(w.probs, 1, A->nrows, feat, ub, h->dev, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "row features");
+    return SPG_OK;
+}
+
+spg_status spgemm_mlp_forward(spg_handle* h, const float* feat, int64_t n,
+                              const void* params_bf16, float* z, void* stream) {
+    if (!h) return SPG_ERR_INVALID_ARG;
+    if (n < 0 || (n > 0 && (!feat || !params_bf16 || !z)))
+        return fail(h, SPG_ERR_INVALID_ARG, "feat / params / z NULL or n < 0");
+    cudaError_t e = launch_mlp_forward(feat, n, params_bf16, z, h->dev, (cudaStream_t)stream);
+    return e == cudaSuccess ? SPG_OK : cuda_fail(h, e, "mlp forward");
+}
+
+size_t spgemm_mlp_train_workspace_size(int64_t n) { return mlp_train_ws_bytes(n < 0 ? 0 : n); }
+
+spg_status spgemm_mlp_grad(spg_handle* h, const float* feat, const float* log_target, int64_t n,
+                           float tau, const void* params_bf16, float* grad, float* loss,
+                           void* workspace, size_t workspace_bytes, void* stream) {
+    if (!h) return SPG_ERR_INVALID_ARG;
+    if (n < 1 || !feat || !log_target || !params_bf16 || !grad || !loss)
+        return fail(h, SPG_ERR_INVALID_ARG, "NULL argument or n < 1");
+    if (!(tau > 0.f && tau < 1.f)) return fail(h, SPG_ERR_INVALID_ARG, "tau must be in (0, 1)");
+    const size_t need = mlp_train_ws_bytes(n);
+    if (!workspace || workspace_bytes < need)
+        return fail(h, SPG_ERR_WORKSPACE, "workspace needs %zu bytes", need);
+    cudaError_t e = launch_mlp_grad(feat, log_target, n, tau, params_bf16, grad, loss, workspace,
+                                    h->dev, (cudaStream_t)stream);
+    return e == cudaSuccess ? SPG_OK : cuda_fail(h, e, "mlp grad");
+}
+
+spg_status spgemm_mlp_adam(spg_handle* h, float* master, float* m, float* v, const float* grad,
+                           void* params_bf16, float lr, int step, void* stream) {
+    if (!h) return SPG_ERR_INVALID_ARG;
+    if (!master || !m || !v || !grad || !params_bf16 || step < 1)
+        return fail(h, SPG_ERR_INVALID_ARG, "NULL argument or step < 1");
+    cudaError_t e = launch_mlp_adam(master, m, v, grad, params_bf16, lr, step, h->dev,
+                                    (cudaStream_t)stream);
+    return e == cudaSuccess ? SPG_OK : cuda_fail(h, e, "mlp adam");
+}
+
+spg_status spgemm_mlp_to_bf16(spg_handle* h, const float* master, void* params_bf16,
+                              void* stream) {
+    if (!h) return SPG_ERR_INVALID_ARG;
+    if (!master || !params_bf16) return fail(h, SPG_ERR_INVALID_ARG, "NULL argument");
+    cudaError_t e = launch_mlp_to_bf16(master, params_bf16, (cudaStream_t)stream);
+    return e == cudaSuccess ? SPG_OK : cuda_fail(h, e, "mlp to bf16");
 }
 
 }  // extern "C"

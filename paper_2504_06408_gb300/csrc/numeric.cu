@@ -42,7 +42,8 @@ SPG_DEV int64_t row_nnz(const Prob* probs, int nprob, int64_t g, const Prob** pp
 
 __global__ void __launch_bounds__(256) k_num_hist(const Prob* __restrict__ probs, int nprob,
                                                   int64_t R, Tuning t,
-                                                  const int64_t* __restrict__ ub, Counters* ctr) {
+                                                  const int64_t* __restrict__ ub, Counters* ctr,
+                                                  const uint8_t* __restrict__ skip) {
     __shared__ int s_hist[kNumBins];
     for (int b = threadIdx.x; b < kNumBins; b += blockDim.x) s_hist[b] = 0;
     __syncthreads();
@@ -50,7 +51,8 @@ __global__ void __launch_bounds__(256) k_num_hist(const Prob* __restrict__ probs
          g += (int64_t)gridDim.x * blockDim.x) {
         const Prob* P;
         const int64_t n = row_nnz(probs, nprob, g, &P);
-        atomicAdd(&s_hist[num_bin_key(num_tier(n, t), ub[g])], 1);
+        const int tier = (skip && skip[g]) ? kTierEmpty : num_tier(n, t);
+        atomicAdd(&s_hist[num_bin_key(tier, ub[g])], 1);
     }
     __syncthreads();
     for (int b = threadIdx.x; b < kNumBins; b += blockDim.x)
@@ -72,7 +74,8 @@ __global__ void k_num_bin_offsets(Counters* ctr) {
 __global__ void __launch_bounds__(1024) k_num_scatter(const Prob* __restrict__ probs, int nprob,
                                                       int64_t R, Tuning t,
                                                       const int64_t* __restrict__ ub,
-                                                      Counters* ctr, int32_t* rows) {
+                                                      Counters* ctr, int32_t* rows,
+                                                      const uint8_t* __restrict__ skip) {
     __shared__ int s_cnt[kNumBins];
     __shared__ int s_base[kNumBins];
     for (int b = threadIdx.x; b < kNumBins; b += blockDim.x) s_cnt[b] = 0;
@@ -82,7 +85,7 @@ __global__ void __launch_bounds__(1024) k_num_scatter(const Prob* __restrict__ p
     if (g < R) {
         const Prob* P;
         const int64_t n = row_nnz(probs, nprob, g, &P);
-        key = num_bin_key(num_tier(n, t), ub[g]);
+        key = num_bin_key((skip && skip[g]) ? kTierEmpty : num_tier(n, t), ub[g]);
         rank = atomicAdd(&s_cnt[key], 1);
     }
     __syncthreads();
@@ -1043,10 +1046,10 @@ cudaError_t launch_numeric(int sr, const WsPtrs& w, const DCsr& B0, int nprob, i
     cudaMemsetAsync(&w.ctr->claim[2], 0, 2 * sizeof(int32_t), st);
     int64_t blocks = (R + 255) / 256;
     if (blocks > (int64_t)dev.sms * 8) blocks = (int64_t)dev.sms * 8;
-    k_num_hist<<<(unsigned)blocks, 256, 0, st>>>(w.probs, nprob, R, t, w.ub, w.ctr);
+    k_num_hist<<<(unsigned)blocks, 256, 0, st>>>(w.probs, nprob, R, t, w.ub, w.ctr, w.skip);
     k_num_bin_offsets<<<1, 32, 0, st>>>(w.ctr);
     k_num_scatter<<<(unsigned)((R + 1023) / 1024), 1024, 0, st>>>(w.probs, nprob, R, t, w.ub,
-                                                                   w.ctr, w.rows_num);
+                                                                   w.ctr, w.rows_num, w.skip);
     count_launch(dev, 3);
     mark_stage(dev, kStNumBin, st);
     cudaError_t e = cudaGetLastError();

@@ -46,6 +46,7 @@ struct Counters {
     int32_t claim[16];                  // per-kernel dynamic row counters
     int32_t bm_next;                    // next free bitmap cache slot
     unsigned long long products;        // sum of ub over all rows
+    unsigned long long learned_nnz;     // learned path: entries of the rows it finished
     int64_t nnz[kMaxProb];              // per-product nnz(C)
 };
 
@@ -74,6 +75,7 @@ struct WsPtrs {
     int32_t* cursor;
     int32_t* slab_ptr;       // slab starts of B's rows (numeric dense tier)
     size_t slab_ptr_bytes;
+    const uint8_t* skip = nullptr;   // rows to leave out of binning (learned path), or null
     uint32_t* bm_cache;      // row bitmaps kept by the symbolic dense tier, or null
     int64_t bm_cache_words;  // words per cached bitmap
     int64_t bm_cache_slots;  // cached bitmaps that fit
@@ -85,7 +87,7 @@ WsPtrs ws_ptrs(void* ws, const WsLayout& L);
 // stream after each stage; stage time = its event minus the previous one.
 enum StageTag : int {
     kStBegin = 0, kStAnalyze, kStSymDense, kStSymBlock, kStSymWarp, kStScan,
-    kStNumBin, kStSlabPtr, kStNumDense, kStNumBlock, kStNumWarp, kStMerge, kStCount
+    kStNumBin, kStSlabPtr, kStNumDense, kStNumBlock, kStNumWarp, kStMerge, kStLearned, kStCount
 };
 struct StageTimer {
     static constexpr int kMax = 32;
@@ -195,5 +197,42 @@ cudaError_t launch_split_columns(const DCsr& M, int nparts, const int32_t* cuts_
                                  int64_t* prp, int64_t* part_base_dev, int32_t* pcol, void* pval,
                                  int vbytes, int64_t* part, const DevInfo& dev, cudaStream_t st);
 
+// ---- learned sizing (mlp.cu, learned.cu) ----
+
+constexpr size_t kLearnedSmemBudget = 200 * 1024;
+
+struct LearnedWs {
+    float* feat;       // [R][4] row features
+    float* z;          // [R] network output (logit of nnz / ub)
+    int64_t* soff;     // [R + 1] staging offsets (scan of the capacities)
+    uint8_t* route;    // [R] 0 learned, 1 exact
+    uint8_t* skip;     // [R] skip mask handed to the exact path
+    int32_t* scol;     // staging columns
+    void* sval;        // staging values
+};
+
+int mlp_param_count();
+size_t mlp_train_ws_bytes(int64_t B);
+cudaError_t launch_row_features(const Prob* probs, int nprob, int64_t R, float* feat,
+                                int64_t* ub, const DevInfo& dev, cudaStream_t st);
+cudaError_t launch_mlp_forward(const float* feat, int64_t R, const void* params, float* z,
+                               const DevInfo& dev, cudaStream_t st);
+cudaError_t launch_mlp_grad(const float* feat, const float* logt, int64_t B, float tau,
+                            const void* params, float* grad, float* loss, void* ws,
+                            const DevInfo& dev, cudaStream_t st);
+cudaError_t launch_mlp_adam(float* master, float* m, float* v, const float* grad, void* params,
+                            float lr, int step, const DevInfo& dev, cudaStream_t st);
+cudaError_t launch_mlp_to_bf16(const float* master, void* params, cudaStream_t st);
+
+// largest capacity <= want whose hash table fits the warp (or CTA) tier
+int64_t learned_capacity_limit(int sr, int64_t want, bool warp);
+cudaError_t launch_learned_caps(const WsPtrs& w, const LearnedWs& lw, int nprob, int64_t R,
+                                const float* z, float margin, int64_t exact_max,
+                                int64_t learned_max, const DevInfo& dev, cudaStream_t st);
+cudaError_t launch_learned_direct(int sr, const WsPtrs& w, const LearnedWs& lw, int nprob,
+                                  int64_t R, int64_t warp_max, int64_t block_max,
+                                  const DevInfo& dev, cudaStream_t st);
+cudaError_t launch_learned_compact(int sr, const WsPtrs& w, const LearnedWs& lw, int nprob,
+                                   int64_t R, const DevInfo& dev, cudaStream_t st);
 
 }  // namespace spg

@@ -39,7 +39,8 @@ __global__ void k_write_probs(ProbTable tab, int nprob, Prob* dst) {
 // ub_i, the empty rows' counts, the symbolic bin histogram and P = sum ub.
 __global__ void __launch_bounds__(256) k_analyze(const Prob* __restrict__ probs, int nprob,
                                                  int64_t R, Tuning t, int64_t* __restrict__ ub,
-                                                 int64_t* __restrict__ cnt, Counters* ctr) {
+                                                 int64_t* __restrict__ cnt, Counters* ctr,
+                                                 const uint8_t* __restrict__ skip) {
     __shared__ int s_hist[kNumBins];
     for (int b = threadIdx.x; b < kNumBins; b += blockDim.x) s_hist[b] = 0;
     __syncthreads();
@@ -58,8 +59,9 @@ __global__ void __launch_bounds__(256) k_analyze(const Prob* __restrict__ probs,
         s = warp_sum(s);
         if (lane == 0) {
             ub[g] = s;
-            if (s == 0) cnt[g] = 0;
-            atomicAdd(&s_hist[bin_key(sym_tier(s, t), s)], 1);
+            const bool skipped = skip && skip[g];
+            if (s == 0 && !skipped) cnt[g] = 0;
+            atomicAdd(&s_hist[bin_key(skipped ? kTierEmpty : sym_tier(s, t), s)], 1);
             prod += (unsigned long long)s;
         }
     }
@@ -105,10 +107,11 @@ SPG_DEV void scatter_by_key(int64_t R, int32_t* cursor, int32_t* rows, KeyFn key
 
 __global__ void __launch_bounds__(1024) k_scatter_sym(int64_t R, Tuning t,
                                                       const int64_t* __restrict__ ub,
-                                                      Counters* ctr, int32_t* rows) {
+                                                      Counters* ctr, int32_t* rows,
+                                                      const uint8_t* __restrict__ skip) {
     scatter_by_key(R, ctr->sym_bin_cursor, rows, [&](int64_t g) {
         const int64_t u = ub[g];
-        return bin_key(sym_tier(u, t), u);
+        return bin_key((skip && skip[g]) ? kTierEmpty : sym_tier(u, t), u);
     });
 }
 
@@ -403,7 +406,8 @@ cudaError_t launch_analyze(const WsPtrs& w, int nprob, int64_t R, const Tuning& 
     if (R > 0) {
         int64_t blocks = (R + 7) / 8;
         if (blocks > (int64_t)dev.sms * 16) blocks = (int64_t)dev.sms * 16;
-        k_analyze<<<(unsigned)blocks, 256, 0, st>>>(w.probs, nprob, R, t, w.ub, w.cnt, w.ctr);
+        k_analyze<<<(unsigned)blocks, 256, 0, st>>>(w.probs, nprob, R, t, w.ub, w.cnt, w.ctr,
+                                                    w.skip);
         count_launch(dev);
     }
     k_bin_offsets<<<1, 32, 0, st>>>(w.ctr->sym_bin_count, w.ctr->sym_bin_off,
@@ -411,7 +415,7 @@ cudaError_t launch_analyze(const WsPtrs& w, int nprob, int64_t R, const Tuning& 
     count_launch(dev);
     if (R > 0) {
         k_scatter_sym<<<(unsigned)((R + 1023) / 1024), 1024, 0, st>>>(R, t, w.ub, w.ctr,
-                                                                       w.rows_sym);
+                                                                       w.rows_sym, w.skip);
         count_launch(dev);
     }
     mark_stage(dev, kStAnalyze, st);

@@ -55,12 +55,23 @@ class spg_tuning(ctypes.Structure):
 class spg_stats(ctypes.Structure):
     _fields_ = [("products", ctypes.c_int64), ("nnz_c", ctypes.c_int64),
                 ("rows_per_tier", ctypes.c_int64 * 4), ("launches", ctypes.c_int64),
-                ("reserved", ctypes.c_int64 * 5)]
+                ("learned_rows", ctypes.c_int64), ("overflow_rows", ctypes.c_int64),
+                ("staging_entries", ctypes.c_int64), ("learned_nnz", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 1)]
+
+
+class spg_learned_opts(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_void_p), ("margin", ctypes.c_float),
+                ("exact_max_ub", ctypes.c_int64), ("learned_max", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 4)]
+
+
+MLP_PARAMS = 4545   # SPGEMM_MLP_PARAMS
 
 
 # stage indices of spgemm_get_stage_times
 STAGES = ["", "analysis", "sym_dense", "sym_block", "sym_warp", "scan", "num_binning",
-          "slab_table", "num_dense", "num_block", "num_warp", "merge"]
+          "slab_table", "num_dense", "num_block", "num_warp", "merge", "learned"]
 
 
 _lib = None
@@ -111,6 +122,20 @@ def load_library(path: str = LIB_PATH):
         "spgemm_split_workspace_size": [_P, _CSR, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)],
         "spgemm_split_columns": [_P, _CSR, ctypes.c_int, _P, ctypes.c_int, _P, _P, _P, _P, _P,
                                  ctypes.c_size_t, _P],
+        "spgemm_learned_workspace_size": [_P, ctypes.c_int, _CSR, _CSR,
+                                          ctypes.POINTER(ctypes.c_size_t)],
+        "spgemm_learned_plan": [_P, ctypes.c_int, _CSR, _CSR, ctypes.POINTER(spg_learned_opts),
+                                _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t), _P],
+        "spgemm_learned_symbolic": [_P, ctypes.c_int, _CSR, _CSR, _P, ctypes.POINTER(_I64), _P,
+                                    ctypes.c_size_t, _P, ctypes.c_size_t, _P],
+        "spgemm_learned_numeric": [_P, ctypes.c_int, _CSR, _CSR, _P, _P, _P, _P, ctypes.c_size_t,
+                                   _P, ctypes.c_size_t, _P],
+        "spgemm_row_features": [_P, _CSR, _CSR, _P, _P, _P, ctypes.c_size_t, _P],
+        "spgemm_mlp_forward": [_P, _P, _I64, _P, _P, _P],
+        "spgemm_mlp_grad": [_P, _P, _P, _I64, ctypes.c_float, _P, _P, _P, _P, ctypes.c_size_t,
+                            _P],
+        "spgemm_mlp_adam": [_P, _P, _P, _P, _P, _P, ctypes.c_float, ctypes.c_int, _P],
+        "spgemm_mlp_to_bf16": [_P, _P, _P, _P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -118,6 +143,8 @@ def load_library(path: str = LIB_PATH):
         fn.restype = ctypes.c_int
     lib.spgemm_last_error.argtypes = [_P]
     lib.spgemm_last_error.restype = ctypes.c_char_p
+    lib.spgemm_mlp_train_workspace_size.argtypes = [_I64]
+    lib.spgemm_mlp_train_workspace_size.restype = ctypes.c_size_t
     _lib = lib
     return lib
 
@@ -131,7 +158,10 @@ def exported_symbols() -> list[str]:
             "spgemm_transpose_noalloc", "spgemm_workspace_size_batched",
             "spgemm_symbolic_batched", "spgemm_numeric_batched", "spgemm_merge_workspace_size",
             "spgemm_merge_stages", "spgemm_merge_stages_batched", "spgemm_split_workspace_size",
-            "spgemm_split_columns"]
+            "spgemm_split_columns", "spgemm_learned_workspace_size", "spgemm_learned_plan",
+            "spgemm_learned_symbolic", "spgemm_learned_numeric", "spgemm_row_features",
+            "spgemm_mlp_forward", "spgemm_mlp_train_workspace_size", "spgemm_mlp_grad",
+            "spgemm_mlp_adam", "spgemm_mlp_to_bf16"]
 
 
 @dataclass
@@ -207,7 +237,9 @@ class Handle:
         s = spg_stats()
         self._ok(self.lib.spgemm_get_stats(self._h, ctypes.byref(s)))
         return {"products": s.products, "nnz_c": s.nnz_c,
-                "rows_per_tier": list(s.rows_per_tier), "launches": s.launches}
+                "rows_per_tier": list(s.rows_per_tier), "launches": s.launches,
+                "learned_rows": s.learned_rows, "overflow_rows": s.overflow_rows,
+                "staging_entries": s.staging_entries, "learned_nnz": s.learned_nnz}
 
     def set_timing(self, enable: bool = True):
         self._ok(self.lib.spgemm_set_timing(self._h, 1 if enable else 0))
@@ -394,6 +426,100 @@ class Handle:
             base += k
         return out
 
+    # ---- learned output sizing ----------------------------------------------------
+
+    def learned_workspace_size(self, sr, A: DeviceCSR, B: DeviceCSR) -> int:
+        n = ctypes.c_size_t()
+        a, b = A.c(), B.c()
+        self._ok(self.lib.spgemm_learned_workspace_size(self._h, sr, ctypes.byref(a),
+                                                        ctypes.byref(b), ctypes.byref(n)))
+        return n.value
+
+    def learned_plan(self, sr, A: DeviceCSR, B: DeviceCSR, ws, model=None, margin=0.0,
+                     exact_max_ub=0, learned_max=0, stream=None) -> int:
+        """Step 1 of the learned path; returns the staging bytes steps 2-3 need.
+        model: device BF16 parameters (torch tensor of MLP_PARAMS) or None."""
+        o = spg_learned_opts()
+        o.model = None if model is None else model.data_ptr()
+        o.margin = float(margin)
+        o.exact_max_ub = int(exact_max_ub)
+        o.learned_max = int(learned_max)
+        n = ctypes.c_size_t()
+        a, b = A.c(), B.c()
+        self._ok(self.lib.spgemm_learned_plan(self._h, sr, ctypes.byref(a), ctypes.byref(b),
+                                              ctypes.byref(o), ws.data_ptr(), ws.numel(),
+                                              ctypes.byref(n), _stream_ptr(stream)))
+        return n.value
+
+    def learned_symbolic(self, sr, A, B, c_rp, ws, staging, stream=None) -> int:
+        nnz = ctypes.c_int64()
+        a, b = A.c(), B.c()
+        self._ok(self.lib.spgemm_learned_symbolic(
+            self._h, sr, ctypes.byref(a), ctypes.byref(b), c_rp.data_ptr(), ctypes.byref(nnz),
+            ws.data_ptr(), ws.numel(), None if staging is None or staging.numel() == 0
+            else staging.data_ptr(), 0 if staging is None else staging.numel(),
+            _stream_ptr(stream)))
+        return nnz.value
+
+    def learned_numeric(self, sr, A, B, c_rp, c_col, c_val, ws, staging, stream=None):
+        a, b = A.c(), B.c()
+        self._ok(self.lib.spgemm_learned_numeric(
+            self._h, sr, ctypes.byref(a), ctypes.byref(b), c_rp.data_ptr(),
+            c_col.data_ptr() if c_col.numel() else None,
+            None if c_val is None or c_val.numel() == 0 else c_val.data_ptr(),
+            ws.data_ptr(), ws.numel(), None if staging is None or staging.numel() == 0
+            else staging.data_ptr(), 0 if staging is None else staging.numel(),
+            _stream_ptr(stream)))
+
+    def row_features(self, A: DeviceCSR, B: DeviceCSR, ws, stream=None):
+        """(feat [n, 4] float32, ub [n] int64) device tensors."""
+        import torch
+        dev = A.rp.device
+        feat = torch.empty((A.nrows, 4), dtype=torch.float32, device=dev)
+        ub = torch.empty(A.nrows, dtype=torch.int64, device=dev)
+        a, b = A.c(), B.c()
+        self._ok(self.lib.spgemm_row_features(self._h, ctypes.byref(a), ctypes.byref(b),
+                                              feat.data_ptr() if A.nrows else None,
+                                              ub.data_ptr() if A.nrows else None,
+                                              ws.data_ptr(), ws.numel(), _stream_ptr(stream)))
+        return feat, ub
+
+    def mlp_forward(self, feat, params_bf16, stream=None):
+        import torch
+        n = int(feat.shape[0])
+        z = torch.empty(n, dtype=torch.float32, device=feat.device)
+        self._ok(self.lib.spgemm_mlp_forward(self._h, feat.data_ptr() if n else None, n,
+                                             params_bf16.data_ptr(), z.data_ptr() if n else None,
+                                             _stream_ptr(stream)))
+        return z
+
+    def mlp_grad(self, feat, log_target, tau, params_bf16, ws=None, stream=None):
+        """(grad [MLP_PARAMS] float32, loss [1] float32) device tensors."""
+        import torch
+        n = int(feat.shape[0])
+        need = self.lib.spgemm_mlp_train_workspace_size(n)
+        if ws is None or ws.numel() < need:
+            ws = torch.empty(need, dtype=torch.uint8, device=feat.device)
+        grad = torch.empty(MLP_PARAMS, dtype=torch.float32, device=feat.device)
+        loss = torch.empty(1, dtype=torch.float32, device=feat.device)
+        self._ok(self.lib.spgemm_mlp_grad(self._h, feat.data_ptr(), log_target.data_ptr(), n,
+                                          float(tau), params_bf16.data_ptr(), grad.data_ptr(),
+                                          loss.data_ptr(), ws.data_ptr(), ws.numel(),
+                                          _stream_ptr(stream)))
+        return grad, loss
+
+    def mlp_train_workspace_size(self, n: int) -> int:
+        return int(self.lib.spgemm_mlp_train_workspace_size(int(n)))
+
+    def mlp_adam(self, master, m, v, grad, params_bf16, lr, step, stream=None):
+        self._ok(self.lib.spgemm_mlp_adam(self._h, master.data_ptr(), m.data_ptr(), v.data_ptr(),
+                                          grad.data_ptr(), params_bf16.data_ptr(), float(lr),
+                                          int(step), _stream_ptr(stream)))
+
+    def mlp_to_bf16(self, master, params_bf16, stream=None):
+        self._ok(self.lib.spgemm_mlp_to_bf16(self._h, master.data_ptr(), params_bf16.data_ptr(),
+                                             _stream_ptr(stream)))
+
     def validate(self, M: DeviceCSR, ws, stream=None):
         m = M.c()
         self._ok(self.lib.spgemm_validate_csr(self._h, ctypes.byref(m), ws.data_ptr(),
@@ -424,6 +550,26 @@ def spgemm(sr: int, A: DeviceCSR, B: DeviceCSR, handle: Optional[Handle] = None,
     c_col = torch.empty(nnz, dtype=torch.int32, device=dev)
     c_val = out_tensor(sr, nnz, dev)
     h.numeric(sr, A, B, c_rp, c_col, c_val, ws)
+    if check:
+        h.check(ws)
+    return DeviceCSR(A.nrows, B.ncols, c_rp, c_col, c_val)
+
+
+def learned_spgemm(sr: int, A: DeviceCSR, B: DeviceCSR, model=None, margin: float = 0.0,
+                   handle: Optional[Handle] = None, check: bool = True, **opts) -> DeviceCSR:
+    """C = A (x).(+) B through the learned-sizing path (plan, direct + exact
+    symbolic, numeric).  model: device BF16 parameters or None (ub-sized)."""
+    import torch
+    h = handle or Handle()
+    dev = A.rp.device
+    ws = torch.empty(h.learned_workspace_size(sr, A, B), dtype=torch.uint8, device=dev)
+    sb = h.learned_plan(sr, A, B, ws, model=model, margin=margin, **opts)
+    staging = torch.empty(max(sb, 1), dtype=torch.uint8, device=dev)
+    c_rp = torch.empty(A.nrows + 1, dtype=torch.int64, device=dev)
+    nnz = h.learned_symbolic(sr, A, B, c_rp, ws, staging)
+    c_col = torch.empty(nnz, dtype=torch.int32, device=dev)
+    c_val = out_tensor(sr, nnz, dev)
+    h.learned_numeric(sr, A, B, c_rp, c_col, c_val, ws, staging)
     if check:
         h.check(ws)
     return DeviceCSR(A.nrows, B.ncols, c_rp, c_col, c_val)
