@@ -39,6 +39,8 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# the comparison forms allocate and free tens of GB in turn
+os.environ.setdefault("PYTORCH_CUDA_ALLOC_CONF", "expandable_segments:True")
 
 METRIC = "semiring SpGEMM GFLOPS (2*products/s), R-MAT scale 18 A^2 over min-plus FP32"
 UNIT = "GFLOPS"
@@ -197,6 +199,112 @@ def cpu_oracle_sample(A, target_s=12.0, seed=7):
                       f"({P} of {int(ub.sum())} products), {dt:.1f} s wall"}, dt, P
 
 
+def _time_ms(fn, reps, flush):
+    """Median CUDA-event time of fn() (one warm-up call; L2 flushed before each)."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def learned_forms(api, h, sr, dA, dB, flush, reps, plain_ms, params, meta):
+    """plain vs learned (ub-sized capacities) vs learned (trained network) on
+    one product; every form gives the same C (checked on nnz and row pointers
+    here, element by element in the tests)."""
+    import torch
+    out = {"plain_ms": plain_ms}
+    ref_rp = torch.empty(dA.nrows + 1, dtype=torch.int64, device="cuda")
+    ws0 = torch.empty(h.workspace_size(sr, dA, dB), dtype=torch.uint8, device="cuda")
+    nnz = h.symbolic(sr, dA, dB, ref_rp, ws0)
+    del ws0
+    c_col = torch.empty(max(nnz, 1), dtype=torch.int32, device="cuda")
+    c_val = api.out_tensor(sr, max(nnz, 1))
+    lws = torch.empty(h.learned_workspace_size(sr, dA, dB), dtype=torch.uint8, device="cuda")
+    c_rp = torch.empty_like(ref_rp)
+    for name, model in (("learned_ub_sized", None), ("learned_network", params)):
+        kw = {} if model is None else {"model": model, "margin": meta["margin"],
+                                       "exact_max_ub": meta["exact_max_ub"]}
+        sb = h.learned_plan(sr, dA, dB, lws, **kw)
+        staging = torch.empty(max(sb, 1), dtype=torch.uint8, device="cuda")
+
+        def step():
+            h.learned_plan(sr, dA, dB, lws, **kw)
+            h.learned_symbolic(sr, dA, dB, c_rp, lws, staging)
+            h.learned_numeric(sr, dA, dB, c_rp, c_col, c_val, lws, staging)
+
+        ms = _time_ms(step, reps, flush)
+        st = h.stats()
+        h.check(lws)
+        same = bool(torch.equal(c_rp, ref_rp)) and st["nnz_c"] == nnz
+        out[name] = {"ms": ms, "speedup_vs_plain": plain_ms / ms, "same_row_ptr": same,
+                     "learned_rows": st["learned_rows"], "overflow_rows": st["overflow_rows"],
+                     "staging_entries": st["staging_entries"],
+                     "staging_per_entry": st["staging_entries"] / max(st["learned_nnz"], 1)}
+        del staging
+    out["rows"] = dA.nrows
+    return out
+
+
+def plain_ms_of(api, h, sr, dA, dB, flush, reps):
+    import torch
+    ws = torch.empty(h.workspace_size(sr, dA, dB), dtype=torch.uint8, device="cuda")
+    c_rp = torch.empty(dA.nrows + 1, dtype=torch.int64, device="cuda")
+    nnz = h.symbolic(sr, dA, dB, c_rp, ws)
+    c_col = torch.empty(max(nnz, 1), dtype=torch.int32, device="cuda")
+    c_val = api.out_tensor(sr, max(nnz, 1))
+
+    def step():
+        h.symbolic(sr, dA, dB, c_rp, ws)
+        h.numeric(sr, dA, dB, c_rp, c_col, c_val, ws)
+
+    return _time_ms(step, reps, flush), nnz
+
+
+def summa_forms(api, Summa, h, sr, dA, flush, reps):
+    """4 x 4 Sparse-SUMMA block grid: one batched launch per phase (and a CUDA
+    graph of numeric + merge) against one call per block product and merge."""
+    import torch
+    out = {}
+    for batched in (True, False):
+        sm = Summa(h, sr, dA, dA, q=4, batched=batched)
+        sm.plan()
+
+        def full():
+            sm.symbolic()
+            sm.numeric()
+            sm.merge_count()
+            sm.merge_write()
+
+        def numeric_merge():
+            sm.run()
+
+        key = "batched" if batched else "unbatched"
+        out[f"{key}_full_ms"] = _time_ms(full, reps, flush)
+        if batched:
+            sm.capture()
+            out["batched_graph_numeric_merge_ms"] = _time_ms(numeric_merge, reps, flush)
+        else:
+            out["unbatched_numeric_merge_ms"] = _time_ms(numeric_merge, reps, flush)
+        out[f"{key}_nnz_c"] = int(sum(sm.c_nnz))
+        out["partial_entries"] = int(sum(sm.p_nnz))
+        del sm
+        torch.cuda.empty_cache()
+    out["speedup_full"] = out["unbatched_full_ms"] / out["batched_full_ms"]
+    out["speedup_numeric_merge"] = (out["unbatched_numeric_merge_ms"]
+                                    / out["batched_graph_numeric_merge_ms"])
+    return out
+
+
 def run_reference(args, rank):
     """Reference arm: the CPU oracle on a bounded row sample per step."""
     if rank != 0:
@@ -249,6 +357,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the learned / batched vs plain comparisons")
+    ap.add_argument("--form-reps", type=int, default=3)
     args = ap.parse_args()
     world, rank, local = dist_info()
     if args.impl == "reference":
@@ -374,6 +485,37 @@ def main():
                "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e_s}
         del h2
 
+    forms = None
+    if not args.no_forms:
+        from paper_2504_06408_gb300 import learned as L
+        from paper_2504_06408_gb300.summa import Summa
+        params, meta = L.load()
+        reps = args.form_reps
+        forms = {"note": "median of %d CUDA-event timings per form, L2 flushed before each; "
+                         "every form gives the same C; plain_ms of the headline workload = "
+                         "ms_per_step" % reps}
+        del c_col, c_val, step
+        torch.cuda.empty_cache()
+        forms["rmat18_min_plus"] = learned_forms(api, h, sr, dA, dA, flush, reps, ms_per_step,
+                                                 params, meta)
+        torch.cuda.empty_cache()
+        lap = I.laplacian(2048)
+        dL = api.DeviceCSR.from_host(lap, val_dtype=np.float64)
+        pms, _ = plain_ms_of(api, h, api.PLUS_TIMES_F64, dL, dL, flush, reps)
+        forms["laplacian2048_plus_times_f64"] = learned_forms(
+            api, h, api.PLUS_TIMES_F64, dL, dL, flush, reps, pms, params, meta)
+        del dL
+        torch.cuda.empty_cache()
+        A64 = I.rmat(SCALE, dtype=np.float64, seed=1)
+        dA64 = api.DeviceCSR.from_host(A64, val_dtype=np.float64)
+        pms, _ = plain_ms_of(api, h, api.PLUS_TIMES_F64, dA64, dA64, flush, reps)
+        torch.cuda.empty_cache()
+        sf = summa_forms(api, Summa, h, api.PLUS_TIMES_F64, dA64, flush, reps)
+        sf["plain_unblocked_ms"] = pms
+        forms["rmat18_plus_times_f64_summa4x4"] = sf
+        del dA64
+        torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu, _, _ = cpu_oracle_sample(A)
@@ -388,7 +530,7 @@ def main():
                "hbm_roofline_frac_step": (t_alg_all / (ms_per_step * 1e-3) / 1e9) / peak,
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                "clocks": sampler.summary(), "gpu_launches": launches,
-               "step_ms": times}
+               "step_ms": times, "forms": forms}
         print(json.dumps(res), flush=True)
     if dist is not None:
         dist.destroy_process_group()

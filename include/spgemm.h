@@ -336,7 +336,8 @@ typedef struct {
                               (the "ub-sized" path: no prediction)                               */
     float margin;          /* cap_i = ceil(ub_i * r_i * margin), clamped to [1, min(ub_i, ncols)];
                               <= 0: 1.0                                                           */
-    int64_t exact_max_ub;  /* rows with ub_i <= this use cap_i = min(ub_i, ncols) (0: 64)        */
+    int64_t exact_max_ub;  /* rows with ub_i <= this use cap_i = min(ub_i, ncols) (0: 32); the
+                              network runs only on the other rows                              */
     int64_t learned_max;   /* rows with cap_i above this take the exact path (0: 2048; clamped to
                               what one CTA's shared-memory table holds for the semiring)         */
     int64_t reserved[4];
@@ -387,7 +388,8 @@ spg_status spgemm_learned_numeric(spg_handle* handle, spg_semiring sr, const spg
 
 /*
  * Row features of C = A B for the network: feat device float [A.nrows][4];
- * ub device int64 [A.nrows] (product count per row) or NULL.  Asynchronous.
+ * ub device int64 [A.nrows] (product count per row) or NULL.  feat must be
+ * 16-byte aligned.  Asynchronous.
  * workspace: any workspace valid for spgemm_symbolic of A and B (only its
  * head, the product descriptor, is written).
  */

@@ -873,6 +873,7 @@ static LearnedWs learned_ptrs(void* ws, const LearnedLayout& M, void* staging, i
     lw.skip = (uint8_t*)(b + M.skip);
     lw.scol = (int32_t*)staging;
     lw.sval = staging ? (void*)((char*)staging + align256((size_t)S * 4)) : nullptr;
+    lw.entries = S;
     return lw;
 }
 
@@ -899,7 +900,7 @@ spg_status spgemm_learned_plan(spg_handle* h, spg_semiring sr, const spg_csr* A,
     if (!workspace || workspace_bytes < M.total)
         return fail(h, SPG_ERR_WORKSPACE, "workspace needs %zu bytes", M.total);
     const float margin = opts && opts->margin > 0.f ? opts->margin : 1.f;
-    const int64_t exact_max = opts && opts->exact_max_ub > 0 ? opts->exact_max_ub : 64;
+    const int64_t exact_max = opts && opts->exact_max_ub > 0 ? opts->exact_max_ub : 32;
     const int64_t want = opts && opts->learned_max > 0 ? opts->learned_max : 2048;
     const int64_t block_max = learned_capacity_limit(sr, want, false);
     int64_t warp_max = t.num_warp_max_nnz < block_max ? t.num_warp_max_nnz : block_max;
@@ -919,7 +920,8 @@ spg_status spgemm_learned_plan(spg_handle* h, spg_semiring sr, const spg_csr* A,
     e = launch_write_probs(*tab, 1, w, h->dev, st);
     delete tab;
     if (e == cudaSuccess) e = launch_row_features(w.probs, 1, L.R, lw.feat, w.ub, h->dev, st);
-    if (e == cudaSuccess && model) e = launch_mlp_forward(lw.feat, L.R, model, lw.z, h->dev, st);
+    if (e == cudaSuccess && model)   // only the rows whose capacity the prediction sets
+        e = launch_mlp_forward(lw.feat, L.R, model, lw.z, w.ub, exact_max, h->dev, st);
     if (e == cudaSuccess)
         e = launch_learned_caps(w, lw, 1, L.R, model ? lw.z : nullptr, margin, exact_max,
                                 block_max, h->dev, st);
@@ -996,7 +998,7 @@ spg_status spgemm_learned_symbolic(spg_handle* h, spg_semiring sr, const spg_csr
         h->stats.rows_per_tier[tier] = n;
     }
     h->stats.overflow_rows = hc->claim[11];
-    h->stats.learned_rows = (int64_t)hc->claim[8] + hc->claim[9] - hc->claim[11];
+    h->stats.learned_rows = (int64_t)hc->claim[8] + hc->claim[9] + hc->claim[12] - hc->claim[11];
     h->stats.staging_entries = h->lrn_entries;
     h->stats.learned_nnz = (int64_t)hc->learned_nnz;
     return read_status(h, w, st);
@@ -1039,6 +1041,8 @@ spg_status spgemm_row_features(spg_handle* h, const spg_csr* A, const spg_csr* B
     spg_status s = check_pair(h, SPG_SR_BOOL_OR_AND, A, B, false);
     if (s != SPG_OK) return s;
     if (!feat && A->nrows > 0) return fail(h, SPG_ERR_INVALID_ARG, "feat is NULL");
+    if ((uintptr_t)feat % 16 != 0)
+        return fail(h, SPG_ERR_INVALID_ARG, "feat must be 16-byte aligned");
     const WsLayout L = layout_for(A, B, effective_tuning(h, SPG_SR_BOOL_OR_AND));
     if (!workspace || workspace_bytes < L.ub)
         return fail(h, SPG_ERR_WORKSPACE, "workspace needs %zu bytes", L.ub);
@@ -1059,7 +1063,8 @@ spg_status spgemm_mlp_forward(spg_handle* h, const float* feat, int64_t n,
     if (!h) return SPG_ERR_INVALID_ARG;
     if (n < 0 || (n > 0 && (!feat || !params_bf16 || !z)))
         return fail(h, SPG_ERR_INVALID_ARG, "feat / params / z NULL or n < 0");
-    cudaError_t e = launch_mlp_forward(feat, n, params_bf16, z, h->dev, (cudaStream_t)stream);
+    cudaError_t e = launch_mlp_forward(feat, n, params_bf16, z, nullptr, 0, h->dev,
+                                       (cudaStream_t)stream);
     return e == cudaSuccess ? SPG_OK : cuda_fail(h, e, "mlp forward");
 }
 

@@ -25,7 +25,9 @@ namespace spg {
 constexpr uint8_t kRouteLearned = 0, kRouteExact = 1;
 
 // claim[] slots used here (the plain kernels use 0..3)
-constexpr int kClWarpRows = 8, kClBlockRows = 9, kClBlockNext = 10, kClOverflow = 11;
+constexpr int kClWarpRows = 8, kClBlockRows = 9, kClBlockNext = 10, kClOverflow = 11,
+              kClTinyRows = 12;
+constexpr int kTinyRows = 1;   // tiny rows per warp at a time (more costs registers)
 
 __global__ void k_learned_caps(const Prob* __restrict__ probs, int nprob, int64_t R,
                                const float* __restrict__ z, float margin, int64_t exact_max,
@@ -59,27 +61,50 @@ __global__ void k_learned_caps(const Prob* __restrict__ probs, int nprob, int64_
     }
 }
 
-// Lists of learned rows with products: cap <= warp_max grows up from rows[0],
-// the others grow down from rows[R - 1].
-__global__ void __launch_bounds__(1024) k_learned_bin(int64_t R, const int64_t* __restrict__ soff,
+// Start of a learned symbolic call: the routes fixed by the plan (a row is
+// learned iff it has a capacity or no products) and zero counts of empty
+// rows, so that the call can be repeated after one plan.
+__global__ void k_learned_reset(int64_t R, const int64_t* __restrict__ soff,
+                                const int64_t* __restrict__ ub, uint8_t* __restrict__ route,
+                                int64_t* __restrict__ cnt) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < R;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const bool empty = ub[g] == 0;
+        route[g] = (empty || soff[g + 1] > soff[g]) ? kRouteLearned : kRouteExact;
+        if (empty) cnt[g] = 0;
+    }
+}
+
+// Lists of learned rows with products: tiny rows (ub <= 32, at most 32
+// entries) in tiny_rows; of the others, cap <= warp_max grows up from rows[0],
+// the rest grows down from rows[R - 1].
+__global__ void __launch_bounds__(1024) k_learned_bin(const Prob* __restrict__ probs, int nprob,
+                                                      int64_t R, const int64_t* __restrict__ soff,
                                                       const uint8_t* __restrict__ route,
                                                       const int64_t* __restrict__ ub,
                                                       int64_t warp_max, int32_t* rows,
-                                                      Counters* ctr) {
+                                                      int32_t* tiny_rows, Counters* ctr) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int which = -1;
-    if (g < R && route[g] == kRouteLearned && ub[g] > 0)
-        which = (soff[g + 1] - soff[g]) <= warp_max ? 0 : 1;
-    for (int l = 0; l < 2; ++l) {
+    if (g < R && route[g] == kRouteLearned && ub[g] > 0) {
+        const Prob& P = probs[nprob == 1 ? 0 : find_prob(probs, nprob, g)];
+        const int64_t i = g - P.row_base;
+        const int64_t na = ld_i64(P.A.rp + i + 1) - ld_i64(P.A.rp + i);
+        if (ub[g] <= kTinyMax && na <= 32) which = 2;
+        else which = (soff[g + 1] - soff[g]) <= warp_max ? 0 : 1;
+    }
+    for (int l = 0; l < 3; ++l) {
         const unsigned m = __ballot_sync(kFull, which == l);
         if (!m) continue;
         const int leader = __ffs(m) - 1;
         int base = 0;
-        if (lane_id() == leader) base = atomicAdd(&ctr->claim[kClWarpRows + l], __popc(m));
+        const int slot = l == 2 ? kClTinyRows : kClWarpRows + l;
+        if (lane_id() == leader) base = atomicAdd(&ctr->claim[slot], __popc(m));
         base = __shfl_sync(kFull, base, leader);
         if (which == l) {
             const int pos = base + __popc(m & ((1u << lane_id()) - 1));
-            rows[l == 0 ? (int64_t)pos : R - 1 - pos] = (int32_t)g;
+            if (l == 2) tiny_rows[pos] = (int32_t)g;
+            else rows[l == 0 ? (int64_t)pos : R - 1 - pos] = (int32_t)g;
         }
     }
 }
@@ -151,8 +176,10 @@ SPG_DEV int table_size_for(int64_t cap, int Tmax) {
 template <class S>
 __global__ void __launch_bounds__(kWarpTierWarps * 32)
     k_learned_warp(const Prob* __restrict__ probs, int nprob, const int32_t* __restrict__ rows,
-                   Counters* ctr, const int64_t* __restrict__ soff, uint8_t* __restrict__ route,
-                   int64_t* __restrict__ cnt, int32_t* scol, void* sval, int Tw) {
+                   const int32_t* __restrict__ tiny_rows, Counters* ctr,
+                   const int64_t* __restrict__ soff, uint8_t* __restrict__ route,
+                   int64_t* __restrict__ cnt, int32_t* scol, void* sval, int64_t S_entries,
+                   DevStatus* st, int Tw) {
     using Slot = typename S::Slot;
     using In = typename S::In;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -169,6 +196,10 @@ __global__ void __launch_bounds__(kWarpTierWarps * 32)
         const Prob& P = probs[nprob == 1 ? 0 : find_prob(probs, nprob, g)];
         const int64_t i = g - P.row_base;
         const int64_t cap = soff[g + 1] - soff[g];
+        if (soff[g] < 0 || cap < 0 || soff[g + 1] > S_entries) {   // not this plan's workspace
+            if (lane == 0) flag_overflow(st, g);
+            continue;
+        }
         const int T = table_size_for(cap, Tw);
         for (int s = lane; s < T; s += 32) {
             keys[s] = kEmptyKey;
@@ -230,6 +261,37 @@ __global__ void __launch_bounds__(kWarpTierWarps * 32)
         }
         __syncwarp();
     }
+    // tiny rows: products sorted and folded in registers, kTinyRows at a time
+    const int tend = ctr->claim[kClTinyRows];
+    const int nwarps = gridDim.x * kWarpTierWarps;
+    const int wg = blockIdx.x * kWarpTierWarps + wid;
+    for (int r = wg * kTinyRows; r < tend; r += nwarps * kTinyRows) {
+        tiny_batch<S, kTinyRows, S::kVal, true>(
+            probs, nprob, tiny_rows, r, tend,
+            [&](int64_t g, const Prob&, int32_t col, const typename S::Out& val, int rank, int m,
+                bool ok) {
+                const int64_t off = soff[g], cap = soff[g + 1] - off;
+                if (off < 0 || cap < 0 || soff[g + 1] > S_entries) {   // another plan's workspace
+                    if (lane == 0) flag_overflow(st, g);
+                    return;
+                }
+                if (!ok || m > cap) {   // the exact path takes the row
+                    if (lane == 0) {
+                        route[g] = kRouteExact;
+                        atomicAdd(&ctr->claim[kClOverflow], 1);
+                    }
+                    return;
+                }
+                if (rank >= 0) {
+                    scol[off + rank] = col;
+                    if constexpr (S::kVal) reinterpret_cast<typename S::Out*>(sval)[off + rank] = val;
+                }
+                if (lane == 0) {
+                    cnt[g] = m;
+                    atomicAdd(&ctr->learned_nnz, (unsigned long long)m);
+                }
+            });
+    }
 }
 
 // CTA per learned row of the CTA list
@@ -238,7 +300,7 @@ __global__ void __launch_bounds__(kBlockThreads)
     k_learned_block(const Prob* __restrict__ probs, int nprob, const int32_t* __restrict__ rows,
                     int64_t R, Counters* ctr, const int64_t* __restrict__ soff,
                     uint8_t* __restrict__ route, int64_t* __restrict__ cnt, int32_t* scol,
-                    void* sval, int Tb) {
+                    void* sval, int64_t S_entries, DevStatus* st, int Tb) {
     using Slot = typename S::Slot;
     using In = typename S::In;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -264,6 +326,11 @@ __global__ void __launch_bounds__(kBlockThreads)
         const Prob& P = probs[nprob == 1 ? 0 : find_prob(probs, nprob, g)];
         const int64_t i = g - P.row_base;
         const int64_t cap = soff[g + 1] - soff[g];
+        if (soff[g] < 0 || cap < 0 || soff[g + 1] > S_entries) {
+            if (threadIdx.x == 0) flag_overflow(st, g);
+            __syncthreads();
+            continue;
+        }
         const int T = table_size_for(cap, Tb);
         for (int s = threadIdx.x; s < T; s += blockDim.x) {
             keys[s] = kEmptyKey;
@@ -317,25 +384,57 @@ __global__ void k_learned_skip(int64_t R, const uint8_t* __restrict__ route, uin
         skip[g] = route[g] == kRouteLearned ? 1 : 0;
 }
 
-// warp per learned row: staging slice -> C row
+// staging slices -> C rows, 32 rows per warp: rows of at most 8 entries are
+// copied by their lane, longer ones by the whole warp one after another
 template <class S>
 __global__ void k_learned_compact(const Prob* __restrict__ probs, int nprob, int64_t R,
                                   const uint8_t* __restrict__ route,
                                   const int64_t* __restrict__ soff, const int32_t* __restrict__ scol,
-                                  const void* __restrict__ sval) {
+                                  const void* __restrict__ sval, int64_t S_entries,
+                                  DevStatus* st) {
     using Out = typename S::Out;
+    constexpr int kShort = 8;
     const int lane = lane_id();
+    const Out* sv = reinterpret_cast<const Out*>(sval);
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); g < R; g += nw) {
-        if (route[g] != kRouteLearned) continue;
-        const Prob& P = probs[nprob == 1 ? 0 : find_prob(probs, nprob, g)];
-        const int64_t i = g - P.row_base;
-        const int64_t dst = P.c_rp[i], n = P.c_rp[i + 1] - dst, src = soff[g];
-        for (int64_t t = lane; t < n; t += 32) {
-            P.c_col[dst + t] = scol[src + t];
-            if constexpr (S::kVal)
-                reinterpret_cast<Out*>(P.c_val)[dst + t] =
-                    reinterpret_cast<const Out*>(sval)[src + t];
+    for (int64_t g0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id()) * 32; g0 < R;
+         g0 += nw * 32) {
+        const int64_t g = g0 + lane;
+        int pi = 0;
+        int64_t dst = 0, n = 0, src = 0;
+        if (g < R && route[g] == kRouteLearned) {
+            pi = nprob == 1 ? 0 : find_prob(probs, nprob, g);
+            const Prob& P = probs[pi];
+            const int64_t i = g - P.row_base;
+            dst = P.c_rp[i];
+            n = P.c_rp[i + 1] - dst;
+            src = soff[g];
+            if (src < 0 || n < 0 || src + n > soff[g + 1] || soff[g + 1] > S_entries) {
+                flag_overflow(st, g);   // workspace of another plan or product
+                n = 0;
+            }
+        }
+        if (n <= kShort) {
+            const Prob& P = probs[pi];
+#pragma unroll
+            for (int t = 0; t < kShort; ++t) {
+                if (t < n) {
+                    P.c_col[dst + t] = scol[src + t];
+                    if constexpr (S::kVal) reinterpret_cast<Out*>(P.c_val)[dst + t] = sv[src + t];
+                }
+            }
+        }
+        unsigned longm = __ballot_sync(kFull, n > kShort);
+        while (longm) {
+            const int l = __ffs(longm) - 1;
+            longm &= longm - 1;
+            const Prob& P = probs[__shfl_sync(kFull, pi, l)];
+            const int64_t d = __shfl_sync(kFull, dst, l), m = __shfl_sync(kFull, n, l),
+                          q = __shfl_sync(kFull, src, l);
+            for (int64_t t = lane; t < m; t += 32) {
+                P.c_col[d + t] = scol[q + t];
+                if constexpr (S::kVal) reinterpret_cast<Out*>(P.c_val)[d + t] = sv[q + t];
+            }
         }
     }
 }
@@ -394,11 +493,15 @@ struct LearnedDirectLaunch {
     cudaStream_t st;
     cudaError_t err = cudaSuccess;
     template <class S> void operator()() {
-        cudaError_t e = cudaMemsetAsync(&w->ctr->claim[kClWarpRows], 0, 4 * sizeof(int32_t), st);
+        cudaError_t e = cudaMemsetAsync(&w->ctr->claim[kClWarpRows], 0, 5 * sizeof(int32_t), st);
         if (e != cudaSuccess) { err = e; return; }
         if (R <= 0) return;
+        k_learned_reset<<<grid_for(R, 256, dev->sms * 8), 256, 0, st>>>(R, lw->soff, w->ub,
+                                                                        lw->route, w->cnt);
+        count_launch(*dev);
         k_learned_bin<<<(unsigned)((R + 1023) / 1024), 1024, 0, st>>>(
-            R, lw->soff, lw->route, w->ub, warp_max, w->rows_num, w->ctr);
+            w->probs, nprob, R, lw->soff, lw->route, w->ub, warp_max, w->rows_num, w->rows_sym,
+            w->ctr);
         count_launch(*dev);
         {
             int64_t T = next_pow2(2 * warp_max);
@@ -411,8 +514,8 @@ struct LearnedDirectLaunch {
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_learned_warp<S>,
                                                           kWarpTierWarps * 32, smem);
             k_learned_warp<S><<<(per > 0 ? per : 1) * dev->sms, kWarpTierWarps * 32, smem, st>>>(
-                w->probs, nprob, w->rows_num, w->ctr, lw->soff, lw->route, w->cnt, lw->scol,
-                lw->sval, (int)T);
+                w->probs, nprob, w->rows_num, w->rows_sym, w->ctr, lw->soff, lw->route, w->cnt,
+                lw->scol, lw->sval, lw->entries, w->status, (int)T);
             count_launch(*dev);
         }
         {
@@ -427,7 +530,7 @@ struct LearnedDirectLaunch {
                                                           smem);
             k_learned_block<S><<<(per > 0 ? per : 1) * dev->sms, kBlockThreads, smem, st>>>(
                 w->probs, nprob, w->rows_num, R, w->ctr, lw->soff, lw->route, w->cnt, lw->scol,
-                lw->sval, (int)T);
+                lw->sval, lw->entries, w->status, (int)T);
             count_launch(*dev);
         }
         k_learned_skip<<<grid_for(R, 256, dev->sms * 8), 256, 0, st>>>(R, lw->route, lw->skip);
@@ -453,8 +556,8 @@ struct CompactLaunch {
     const DevInfo* dev;
     cudaStream_t st;
     template <class S> void operator()() {
-        k_learned_compact<S><<<grid_for(R, 8, dev->sms * 16), 256, 0, st>>>(
-            w->probs, nprob, R, lw->route, lw->soff, lw->scol, lw->sval);
+        k_learned_compact<S><<<grid_for(R, 256, dev->sms * 16), 256, 0, st>>>(
+            w->probs, nprob, R, lw->route, lw->soff, lw->scol, lw->sval, lw->entries, w->status);
         count_launch(*dev);
     }
 };

@@ -30,30 +30,20 @@ SPG_DEV float bf(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
 // ---- features -----------------------------------------------------------------
 
-// warp per flat row: f = log1p(nnz(A_i), ub_i, max nnz(B_k), mean nnz(B_k))
+// 32 rows per warp (warp_row_counts): f = log1p(nnz(A_i), ub_i, max nnz(B_k),
+// mean nnz(B_k)), one 16-byte store per row
 __global__ void k_row_features(const Prob* __restrict__ probs, int nprob, int64_t R,
                                float* __restrict__ feat, int64_t* __restrict__ ub_out) {
-    const int lane = lane_id();
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); g < R; g += nw) {
-        const Prob& P = probs[nprob == 1 ? 0 : find_prob(probs, nprob, g)];
-        const int64_t i = g - P.row_base;
-        const int64_t a0 = ld_i64(P.A.rp + i), a1 = ld_i64(P.A.rp + i + 1);
-        int64_t s = 0, mx = 0;
-        for (int64_t q = a0 + lane; q < a1; q += 32) {
-            const int32_t k = ld_i32(P.A.col + q);
-            const int64_t l = ld_i64(P.B.rp + k + 1) - ld_i64(P.B.rp + k);
-            s += l;
-            mx = l > mx ? l : mx;
-        }
-        s = warp_sum(s);
-        mx = warp_max(mx);
-        if (lane == 0) {
-            const int64_t na = a1 - a0;
-            feat[g * 4 + 0] = log1pf((float)na);
-            feat[g * 4 + 1] = log1pf((float)s);
-            feat[g * 4 + 2] = log1pf((float)mx);
-            feat[g * 4 + 3] = log1pf(na > 0 ? (float)s / (float)na : 0.f);
+    const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id();
+    for (int64_t it = 0; it * 32 * nw < R; ++it) {
+        const int64_t g = row_of_lane(it, w, nw);
+        int64_t s, mx, na;
+        warp_row_counts(probs, nprob, g, g < R, s, mx, na);
+        if (g < R) {
+            const float4 f = make_float4(log1pf((float)na), log1pf((float)s), log1pf((float)mx),
+                                         log1pf(na > 0 ? (float)s / (float)na : 0.f));
+            reinterpret_cast<float4*>(feat)[g] = f;
             if (ub_out) ub_out[g] = s;
         }
     }
@@ -61,15 +51,19 @@ __global__ void k_row_features(const Prob* __restrict__ probs, int nprob, int64_
 
 // ---- forward (inference) ----------------------------------------------------------
 
-// one thread per row; parameters (BF16) staged in shared memory as float
+// one thread per row; parameters (BF16) staged in shared memory as float.
+// With ub != null, rows with ub <= min_ub are skipped (z left unwritten).
 __global__ void __launch_bounds__(128) k_mlp_forward(const float* __restrict__ feat, int64_t R,
                                                      const __nv_bfloat16* __restrict__ params,
-                                                     float* __restrict__ z_out) {
+                                                     float* __restrict__ z_out,
+                                                     const int64_t* __restrict__ ub,
+                                                     int64_t min_ub) {
     __shared__ float w[kParams];
     for (int t = threadIdx.x; t < kParams; t += blockDim.x) w[t] = __bfloat162float(params[t]);
     __syncthreads();
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R;
          r += (int64_t)gridDim.x * blockDim.x) {
+        if (ub && ub[r] <= min_ub) continue;
         float f[kIn];
 #pragma unroll
         for (int m = 0; m < kIn; ++m) f[m] = bf(feat[r * 4 + m]);
@@ -249,7 +243,7 @@ size_t mlp_train_ws_bytes(int64_t B) {
 cudaError_t launch_row_features(const Prob* probs, int nprob, int64_t R, float* feat,
                                 int64_t* ub, const DevInfo& dev, cudaStream_t st) {
     if (R <= 0) return cudaSuccess;
-    int64_t blocks = (R + 7) / 8;
+    int64_t blocks = (R + 255) / 256;    // 8 warps x 32 rows
     if (blocks > (int64_t)dev.sms * 16) blocks = (int64_t)dev.sms * 16;
     k_row_features<<<(unsigned)blocks, 256, 0, st>>>(probs, nprob, R, feat, ub);
     count_launch(dev);
@@ -257,11 +251,13 @@ cudaError_t launch_row_features(const Prob* probs, int nprob, int64_t R, float* 
 }
 
 cudaError_t launch_mlp_forward(const float* feat, int64_t R, const void* params, float* z,
-                               const DevInfo& dev, cudaStream_t st) {
+                               const int64_t* ub, int64_t min_ub, const DevInfo& dev,
+                               cudaStream_t st) {
     if (R <= 0) return cudaSuccess;
     int64_t blocks = (R + 127) / 128;
     if (blocks > (int64_t)dev.sms * 8) blocks = (int64_t)dev.sms * 8;
-    k_mlp_forward<<<(unsigned)blocks, 128, 0, st>>>(feat, R, (const __nv_bfloat16*)params, z);
+    k_mlp_forward<<<(unsigned)blocks, 128, 0, st>>>(feat, R, (const __nv_bfloat16*)params, z,
+                                                    ub, min_ub);
     count_launch(dev);
     return cudaGetLastError();
 }

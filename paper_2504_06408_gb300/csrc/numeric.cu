@@ -27,7 +27,9 @@ SPG_DEV int num_tier(int64_t nnz, const Tuning& t) {
     return kTierDense;
 }
 
+// as the symbolic bins: tiny rows (ub <= 32) of the warp tier in its last sub-bin
 SPG_DEV int num_bin_key(int tier, int64_t work) {
+    if (tier == kTierWarp && work <= kTinyMax) return tier * kSubBins + kSubBins - 1;
     int lg = work > 0 ? 63 - __clzll(work) : 0;
     if (lg > kSubBins - 1) lg = kSubBins - 1;
     return tier * kSubBins + (kSubBins - 1 - lg);
@@ -159,10 +161,13 @@ SPG_DEV size_t hash_region_bytes(int T) {
 
 // ---- warp tier ------------------------------------------------------------------
 
+constexpr int kTinyRows = 1;   // tiny rows per warp at a time (more costs registers)
+
 template <class S>
 __global__ void __launch_bounds__(kWarpTierWarps * 32)
     k_num_warp(const Prob* __restrict__ probs, int nprob, const int32_t* __restrict__ rows,
-               const Counters* __restrict__ ctr, DevStatus* st, int Tw) {
+               const Counters* __restrict__ ctr, const int64_t* __restrict__ ub, DevStatus* st,
+               int Tw) {
     using Slot = typename S::Slot;
     using In = typename S::In;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -172,10 +177,31 @@ __global__ void __launch_bounds__(kWarpTierWarps * 32)
     int32_t* sbuf = keys + Tw;
     const int lane = lane_id();
     const int beg = ctr->num_bin_off[kTierWarp * kSubBins];
+    const int tiny = ctr->num_bin_off[(kTierWarp + 1) * kSubBins - 1];
     const int end = ctr->num_bin_off[(kTierWarp + 1) * kSubBins];
     const int stride = gridDim.x * kWarpTierWarps;
+    const int wg = blockIdx.x * kWarpTierWarps + warp_id();
     const Slab single{0, 0, true, true, true, nullptr, nullptr, 0, 0};
-    for (int r = beg + blockIdx.x * kWarpTierWarps + warp_id(); r < end; r += stride) {
+    // tiny rows: products sorted and folded in registers, kTinyRows at a time
+    for (int r = tiny + wg * kTinyRows; r < end; r += stride * kTinyRows) {
+        tiny_batch<S, kTinyRows, S::kVal, true>(
+            probs, nprob, rows, r, end,
+            [&](int64_t g, const Prob& P, int32_t col, const typename S::Out& val, int rank, int m,
+                bool ok) {
+                const int64_t i = g - P.row_base;
+                const int64_t off = P.c_rp[i];
+                if (!ok || m != P.c_rp[i + 1] - off) {   // inconsistent with the symbolic phase
+                    if (lane == 0) flag_overflow(st, g);
+                    return;
+                }
+                if (rank >= 0) {
+                    P.c_col[off + rank] = col;
+                    if constexpr (S::kVal)
+                        reinterpret_cast<typename S::Out*>(P.c_val)[off + rank] = val;
+                }
+            });
+    }
+    for (int r = beg + wg; r < tiny; r += stride) {
         const int64_t g = rows[r];
         const Prob& P = probs[nprob == 1 ? 0 : find_prob(probs, nprob, g)];
         const int64_t i = g - P.row_base;
@@ -595,75 +621,6 @@ __global__ void __launch_bounds__(kBlockThreads, 2)
 // so the accumulation atomics are free of bank conflicts, and a row is walked
 // 1 + (number of value passes) times instead of once per column slab.
 
-// one A entry per lane, the same in every warp (rows with <= 32 entries)
-template <class In, bool kVal>
-struct LaneEntry {
-    bool v;
-    int32_t k;
-    In a;
-    int64_t rs, re;
-    SPG_DEV void load(const DCsr& A, const DCsr& B, int64_t p, bool valid) {
-        v = valid;
-        k = 0;
-        a = In();
-        rs = re = 0;
-        if (!v) return;
-        k = ld_i32(A.col + p);
-        a = load_val<In, kVal>(A.val, p);
-        rs = ld_i64(B.rp + k);
-        re = ld_i64(B.rp + k + 1);
-    }
-    // segment of slabs [s0, s1) (nslabs slabs in the row; sp may be null only
-    // when the range is the whole row)
-    SPG_DEV void range(const int32_t* sp, int sp_stride, int nslabs, int s0, int s1,
-                       int64_t& b, int64_t& e) const {
-        b = e = 0;
-        if (!v) return;
-        b = (s0 == 0) ? rs : rs + __ldg(sp + (int64_t)k * sp_stride + s0);
-        e = (s1 >= nslabs) ? re : rs + __ldg(sp + (int64_t)k * sp_stride + s1);
-    }
-};
-
-// Products of the <= 32 lane entries' segments [b, e) split evenly over the
-// warps: each warp holds the whole 32-entry table in registers.
-template <class In, bool kVal, class Op>
-SPG_DEV void warp_table_walk(const DCsr& B, int64_t b, int64_t e, In a, Op& op) {
-    const int lane = lane_id(), wid = warp_id();
-    const int nwarps = blockDim.x >> 5;
-    const int64_t len = e - b;
-    const int64_t my_end = warp_incl_scan(len);
-    const int64_t excl = my_end - len;
-    const int64_t total = __shfl_sync(kFull, my_end, 31);
-    const int64_t lo_w = total * wid / nwarps, hi_w = total * (wid + 1) / nwarps;
-    for (int64_t t0 = lo_w; t0 < hi_w; t0 += 128) {   // warp-uniform
-        int64_t qv[4];
-        In av[4];
-        bool vv[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int64_t t = t0 + 32 * u + lane;
-            vv[u] = t < hi_w;
-            int k = 0;   // entry of product t: number of prefix ends <= t
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                const int64_t bv = __shfl_sync(kFull, my_end, k + step - 1);
-                if (bv <= t) k += step;
-            }
-            qv[u] = __shfl_sync(kFull, b, k) + (t - __shfl_sync(kFull, excl, k));
-            av[u] = shfl_val<In, kVal>(a, k);
-        }
-        int32_t col[4];
-        In bval[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            col[u] = vv[u] ? ld_i32(B.col + qv[u]) : 0;
-            bval[u] = vv[u] ? load_val<In, kVal>(B.val, qv[u]) : In();
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) op.any(col[u], av[u], bval[u], vv[u]);
-    }
-}
-
 // Products of row entries [a0, a1) restricted to slabs [s0, s1), spread over the CTA.
 template <class In, bool kVal, class Op, int NT>
 SPG_DEV void cta_range_products(const DCsr& A, const DCsr& B, int64_t a0, int64_t a1,
@@ -718,19 +675,28 @@ template <class S>
 __host__ __device__ inline size_t rank_val_bytes(int64_t cap) {
     return S::kVal ? (((size_t)cap * sizeof(typename S::Slot) + 15) & ~(size_t)15) : 0;
 }
+// the value array's region, which first serves as the warps' C.col staging:
+// at least 3 KB per warp
+constexpr size_t kRankStageMin = (size_t)(kRankThreads / 32) * 3072;
+template <class S>
+__host__ __device__ inline size_t rank_region_bytes(int64_t cap) {
+    const size_t v = rank_val_bytes<S>(cap);
+    return v > kRankStageMin ? v : kRankStageMin;
+}
 
 template <class S>
 __global__ void __launch_bounds__(kRankThreads, 1)
     k_num_rank(const Prob* __restrict__ probs, int nprob, const int32_t* __restrict__ rows,
                Counters* ctr, DevStatus* st, const int32_t* __restrict__ sp, int sp_stride,
                int slab_cols, int bm_words, int cap, const uint32_t* __restrict__ bm_cache,
-               const int32_t* __restrict__ row_slot, int cache_words) {
+               const int32_t* __restrict__ row_slot, int cache_words, int64_t cache_slots,
+               int stage_words) {
     using Slot = typename S::Slot;
     using In = typename S::In;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Slot* vals = reinterpret_cast<Slot*>(smem_raw);                          // [cap]
     // the bitmap is filled with 16-byte copies: its offset must be 16-aligned
-    uint32_t* bm = reinterpret_cast<uint32_t*>(smem_raw + rank_val_bytes<S>(cap));
+    uint32_t* bm = reinterpret_cast<uint32_t*>(smem_raw + rank_region_bytes<S>(cap));
     int32_t* word_off = reinterpret_cast<int32_t*>(bm + bm_words);           // [words + 1]
     __shared__ BatchSmem<In, kRankThreads> bs;
     __shared__ int s_row;
@@ -758,8 +724,10 @@ __global__ void __launch_bounds__(kRankThreads, 1)
         if (small) le.load(P.A, P.B, a0 + lane, a0 + lane < a1);
         // (1) presence bitmap of the whole row: the symbolic phase's copy if it
         //     kept one, else rebuilt from the products
+        // (a slot outside the cache means the workspace did not come from this
+        // product's symbolic call: the row is rebuilt and checked against c_rp)
         const int slot = row_slot ? row_slot[g] : -1;
-        if (slot >= 0 && words <= cache_words) {
+        if (slot >= 0 && slot < cache_slots && words <= cache_words) {
             const uint4* src = reinterpret_cast<const uint4*>(bm_cache + (int64_t)slot * cache_words);
             uint4* dst = reinterpret_cast<uint4*>(bm);
             for (int w = tid; w < (words + 3) / 4; w += blockDim.x) dst[w] = __ldg(src + w);
@@ -773,10 +741,12 @@ __global__ void __launch_bounds__(kRankThreads, 1)
         }
         // (2) ranks: exclusive prefix of the words' popcounts.  Warp w scans a
         //     contiguous block of words, lane l reading word base + l + 32 j
-        //     (no bank conflicts); block offsets come from a scan of the warps.
+        //     (no bank conflicts), into block-local offsets; the warps' block
+        //     offsets come from a scan of the block totals and are added in
+        //     step 3.
+        const int per_warp = ((words + nwarps - 1) / nwarps + 31) & ~31;
+        const int wb = wid * per_warp;
         {
-            const int per_warp = ((words + nwarps - 1) / nwarps + 31) & ~31;
-            const int wb = wid * per_warp;
             int run = 0;
             for (int j = 0; j < per_warp; j += 32) {
                 const int w = wb + j + lane;
@@ -794,12 +764,6 @@ __global__ void __launch_bounds__(kRankThreads, 1)
                 if (lane == 31) word_off[words] = xi;
             }
             __syncthreads();
-            const int add = s_wsum[wid];
-            for (int j = 0; j < per_warp; j += 32) {
-                const int w = wb + j + lane;
-                if (w < words) word_off[w] += add;
-            }
-            __syncthreads();
         }
         const int T = word_off[words];
         if (T != n) {   // symbolic and numeric disagree: leave the row
@@ -807,23 +771,44 @@ __global__ void __launch_bounds__(kRankThreads, 1)
             __syncthreads();
             continue;
         }
-        // (3) C.col from the bitmap: warp w takes a contiguous block of words,
-        //     32 at a time (lane = word); each lane writes its word's columns
-        //     at word_off[w] + 0, 1, ... (the warp's stores stay inside a
-        //     contiguous stretch of C.col)
+        // (3) C.col from the bitmap, and the block-local offsets made global:
+        //     warp w walks its block 32 words at a time (lane = word).  The
+        //     chunk's columns are expanded into the warp's staging area (the
+        //     value array is free until step 4) at the lanes' offsets, then
+        //     copied to C.col 32 consecutive entries per store.  A chunk too
+        //     dense for the staging area writes each lane's columns directly.
         {
-            const int per_warp = ((words + nwarps - 1) / nwarps + 31) & ~31;
-            const int wb = wid * per_warp;
-            for (int j = 0; j < per_warp; j += 32) {
-                const int w = wb + j + lane;
-                if (w < words) {
-                    uint32_t bits = bm[w];
-                    int32_t* dst = P.c_col + off + word_off[w];
-                    const int cbase = w * 32;
+            int32_t* stage = reinterpret_cast<int32_t*>(smem_raw) + (size_t)wid * stage_words;
+            const int add = s_wsum[wid];
+            const int wtot = (wid + 1 < nwarps ? s_wsum[wid + 1] : T) - add;
+            for (int j = 0; j < per_warp && wb + j < words; j += 32) {
+                const int w0 = wb + j;
+                const int w = w0 + lane;
+                const int lbase = word_off[w0];
+                const int lnext = (j + 32 < per_warp && w0 + 32 < words) ? word_off[w0 + 32] : wtot;
+                const int lw = w < words ? word_off[w] : 0;
+                __syncwarp();
+                if (w < words) word_off[w] = lw + add;
+                const int Tc = lnext - lbase;
+                if (Tc == 0) continue;
+                uint32_t bits = w < words ? bm[w] : 0u;
+                int pos = lw - lbase;
+                const int cbase = w * 32;
+                int32_t* dst = P.c_col + off + add + lbase;
+                if (Tc <= stage_words) {
                     while (bits) {
                         const int b = __ffs(bits) - 1;
                         bits &= bits - 1u;
-                        *dst++ = cbase + b;
+                        stage[pos++] = cbase + b;
+                    }
+                    __syncwarp();
+                    for (int t = lane; t < Tc; t += 32) dst[t] = stage[t];
+                    __syncwarp();
+                } else {
+                    while (bits) {
+                        const int b = __ffs(bits) - 1;
+                        bits &= bits - 1u;
+                        dst[pos++] = cbase + b;
                     }
                 }
             }
@@ -984,9 +969,12 @@ struct NumericLaunch {
                 cap = S::kVal ? (int64_t)((budget - fixed - 16) / sizeof(typename S::Slot)) : 0;
             if (cap > (int64_t)1 << 30) cap = (int64_t)1 << 30;
             const bool rank_ok = fixed < budget && (!S::kVal || cap >= slab) &&
+                                 rank_region_bytes<S>(cap) + fixed <= budget &&
                                  max_ncols < INT32_MAX;
             if (rank_ok) {
-                const size_t rsmem = rank_val_bytes<S>(cap) + fixed;
+                const size_t region = rank_region_bytes<S>(cap);
+                const size_t rsmem = region + fixed;
+                const int stage_words = (int)(region / (kRankThreads / 32) / 4);
                 e = cudaFuncSetAttribute(k_num_rank<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)rsmem);
                 if (e != cudaSuccess) { err = e; return; }
@@ -995,7 +983,8 @@ struct NumericLaunch {
                 k_num_rank<S><<<grid, kRankThreads, rsmem, st>>>(
                     w->probs, nprob, w->rows_num, w->ctr, w->status, sp, nslabs + 1, (int)slab,
                     (int)bm_words, (int)cap, cached ? w->bm_cache : nullptr,
-                    cached ? w->row_slot : nullptr, (int)w->bm_cache_words);
+                    cached ? w->row_slot : nullptr, (int)w->bm_cache_words, w->bm_cache_slots,
+                    stage_words);
                 count_launch(*dev);
             } else {
                 const int grid = occupancy_grid((const void*)k_num_dense<S>, kBlockThreads, smem, *dev);
@@ -1029,7 +1018,8 @@ struct NumericLaunch {
             const int grid =
                 occupancy_grid((const void*)k_num_warp<S>, kWarpTierWarps * 32, smem, *dev);
             k_num_warp<S><<<grid, kWarpTierWarps * 32, smem, st>>>(w->probs, nprob, w->rows_num,
-                                                                   w->ctr, w->status, (int)T);
+                                                                   w->ctr, w->ub, w->status,
+                                                                   (int)T);
             count_launch(*dev);
             mark_stage(*dev, kStNumWarp, st);
         }

@@ -209,14 +209,17 @@ struct LearnedWs {
     uint8_t* skip;     // [R] skip mask handed to the exact path
     int32_t* scol;     // staging columns
     void* sval;        // staging values
+    int64_t entries;   // staging capacity (entries) fixed by the plan
 };
 
 int mlp_param_count();
 size_t mlp_train_ws_bytes(int64_t B);
 cudaError_t launch_row_features(const Prob* probs, int nprob, int64_t R, float* feat,
                                 int64_t* ub, const DevInfo& dev, cudaStream_t st);
+// rows with ub[r] <= min_ub are skipped when ub is given
 cudaError_t launch_mlp_forward(const float* feat, int64_t R, const void* params, float* z,
-                               const DevInfo& dev, cudaStream_t st);
+                               const int64_t* ub, int64_t min_ub, const DevInfo& dev,
+                               cudaStream_t st);
 cudaError_t launch_mlp_grad(const float* feat, const float* logt, int64_t B, float tau,
                             const void* params, float* grad, float* loss, void* ws,
                             const DevInfo& dev, cudaStream_t st);

@@ -12,6 +12,8 @@
 // lanes' exclusive prefix sums.
 #pragma once
 
+#include <cstring>
+
 #include "common.cuh"
 
 namespace spg {
@@ -363,6 +365,91 @@ SPG_DEV void cta_row_products(const DCsr& A, const DCsr& B, int64_t a0, int64_t 
     }
 }
 
+// one A entry per lane, the same in every warp (rows with <= 32 entries)
+template <class In, bool kVal>
+struct LaneEntry {
+    bool v;
+    int32_t k;
+    In a;
+    int64_t rs, re;
+    SPG_DEV void load(const DCsr& A, const DCsr& B, int64_t p, bool valid) {
+        v = valid;
+        k = 0;
+        a = In();
+        rs = re = 0;
+        if (!v) return;
+        k = ld_i32(A.col + p);
+        a = load_val<In, kVal>(A.val, p);
+        rs = ld_i64(B.rp + k);
+        re = ld_i64(B.rp + k + 1);
+    }
+    // segment of slabs [s0, s1) (nslabs slabs in the row; sp may be null only
+    // when the range is the whole row)
+    SPG_DEV void range(const int32_t* sp, int sp_stride, int nslabs, int s0, int s1,
+                       int64_t& b, int64_t& e) const {
+        b = e = 0;
+        if (!v) return;
+        b = (s0 == 0) ? rs : rs + __ldg(sp + (int64_t)k * sp_stride + s0);
+        e = (s1 >= nslabs) ? re : rs + __ldg(sp + (int64_t)k * sp_stride + s1);
+    }
+};
+
+// Products of the <= 32 lane entries' segments [b, e) split evenly over the
+// warps: each warp holds the whole 32-entry table in registers.
+template <class In, bool kVal, class Op>
+SPG_DEV void warp_table_walk(const DCsr& B, int64_t b, int64_t e, In a, Op& op) {
+    const int lane = lane_id(), wid = warp_id();
+    const int nwarps = blockDim.x >> 5;
+    const int64_t len = e - b;
+    const int64_t my_end = warp_incl_scan(len);
+    const int64_t excl = my_end - len;
+    const int64_t total = __shfl_sync(kFull, my_end, 31);
+    const int64_t lo_w = total * wid / nwarps, hi_w = total * (wid + 1) / nwarps;
+    int kc = 0;   // entry holding product t0 (warp-uniform, advances with t0)
+    for (int64_t t0 = lo_w; t0 < hi_w; t0 += 128) {   // warp-uniform
+        int64_t qv[4];
+        In av[4];
+        bool vv[4];
+        while (kc < 31 && __shfl_sync(kFull, my_end, kc) <= t0) ++kc;
+        const int64_t endk = __shfl_sync(kFull, my_end, kc);
+        if (t0 + 128 <= endk && t0 + 128 <= hi_w) {
+            // the window lies in one segment (the common case for hub rows of
+            // B): addresses without a per-lane search
+            const int64_t base = __shfl_sync(kFull, b, kc) - __shfl_sync(kFull, excl, kc);
+            const In ak = shfl_val<In, kVal>(a, kc);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                qv[u] = base + t0 + 32 * u + lane;
+                av[u] = ak;
+                vv[u] = true;
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t t = t0 + 32 * u + lane;
+                vv[u] = t < hi_w;
+                int k = 0;   // entry of product t: number of prefix ends <= t
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int64_t bv = __shfl_sync(kFull, my_end, k + step - 1);
+                    if (bv <= t) k += step;
+                }
+                qv[u] = __shfl_sync(kFull, b, k) + (t - __shfl_sync(kFull, excl, k));
+                av[u] = shfl_val<In, kVal>(a, k);
+            }
+        }
+        int32_t col[4];
+        In bval[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            col[u] = vv[u] ? ld_i32(B.col + qv[u]) : 0;
+            bval[u] = vv[u] ? load_val<In, kVal>(B.val, qv[u]) : In();
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) op.any(col[u], av[u], bval[u], vv[u]);
+    }
+}
+
 // OR of one bit per lane into a shared bitmap, for lanes holding ascending
 // columns (c relative to the slab): lanes of one 32-bit word form a run; a
 // segmented OR-scan gives the run's last lane the word's bits, and only that
@@ -381,6 +468,262 @@ SPG_DEV void bitmap_or_sorted(uint32_t* bm, int32_t c, bool valid) {
     }
     const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
     if (valid && tail) atomicOr(bm + w, bit);
+}
+
+// ---- tiny rows: at most 32 products, one per lane, sorted in registers -------
+//
+// A row whose products fit the warp (ub_i <= 32) needs no table: lane t takes
+// product t (owner search over the lanes' prefix sums, as in
+// warp_short_segments), the warp sorts the (column, value) pairs by column
+// with a bitonic network of shuffles, a segmented suffix reduction gives the
+// first lane of each run of equal columns the (+) of the run, and the run
+// heads are the row's sorted output.
+
+constexpr int kTinyMax = 32;
+
+// shuffles of any trivially copyable value, word by word (kMode 0: from lane
+// src, 1: xor src, 2: down by src)
+template <int kMode, class T>
+SPG_DEV T shfl_words(const T& v, int src) {
+    constexpr int W = (int)((sizeof(T) + 3) / 4);
+    uint32_t w[W] = {};
+    memcpy(w, &v, sizeof(T));
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        if constexpr (kMode == 0) w[i] = __shfl_sync(kFull, w[i], src);
+        else if constexpr (kMode == 1) w[i] = __shfl_xor_sync(kFull, w[i], src);
+        else w[i] = __shfl_down_sync(kFull, w[i], src);
+    }
+    T out;
+    memcpy(&out, w, sizeof(T));
+    return out;
+}
+
+// Sorts the lanes' (col, val) by column (INT32_MAX last) and folds equal
+// columns with (+) into the first lane of their run.  Returns the number of
+// distinct columns; `rank` = position of a head lane among them (-1 else).
+// Branch-free: every compare-exchange is a select.
+template <class S, bool kWithVal>
+SPG_DEV int tiny_sort_reduce(int32_t& col, typename S::Out& val, int& rank) {
+    using Out = typename S::Out;
+    const int lane = lane_id();
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const int32_t oc = __shfl_xor_sync(kFull, col, j);
+            const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
+            const bool take = keep_min ? (oc < col) : (oc > col);
+            col = take ? oc : col;
+            if constexpr (kWithVal) {
+                const Out ov = shfl_words<1>(val, j);
+                val = take ? ov : val;
+            }
+        }
+    }
+    if constexpr (kWithVal) {
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int32_t oc = __shfl_down_sync(kFull, col, d);
+            const Out ov = shfl_words<2>(val, d);
+            const Out sum = S::add(val, ov);
+            val = (lane + d < 32 && oc == col) ? sum : val;
+        }
+    }
+    const int32_t prev = __shfl_up_sync(kFull, col, 1);
+    const bool head = col != INT32_MAX && (lane == 0 || prev != col);
+    const unsigned hm = __ballot_sync(kFull, head);
+    rank = head ? __popc(hm & ((1u << lane) - 1)) : -1;
+    return __popc(hm);
+}
+
+// Number of distinct columns held by the lanes (INT32_MAX = none): the lowest
+// lane of each group of equal columns counts it.
+SPG_DEV int tiny_count_distinct(int32_t col) {
+    const unsigned same = __match_any_sync(kFull, col);
+    const bool head = col != INT32_MAX && (__ffs(same) - 1) == lane_id();
+    return __popc(__ballot_sync(kFull, head));
+}
+
+// G tiny rows at once (rows[r0 .. r0 + G) below rend): every load phase is
+// issued for the G rows before the next phase starts, so one warp keeps G
+// rows' dependent loads (row range -> A entries -> B row ranges -> B entries)
+// in flight together.  For each row, emit(g, P, col, val, rank, m, ok) is
+// called by all lanes (ok = false if the row is not tiny after all).  With
+// kSorted = false only m (the distinct count) is computed: no sort, rank -1.
+template <class S, int G, bool kWithVal, bool kSorted, class Emit>
+SPG_DEV void tiny_batch(const Prob* __restrict__ probs, int nprob, const int32_t* __restrict__ rows,
+                        int r0, int rend, Emit&& emit) {
+    using In = typename S::In;
+    using Out = typename S::Out;
+    const int lane = lane_id();
+    int64_t gl = -1, a0l = 0, a1l = 0;
+    int pil = 0;
+    if (lane < G && r0 + lane < rend) {
+        gl = rows[r0 + lane];
+        pil = nprob == 1 ? 0 : find_prob(probs, nprob, gl);
+        const Prob& P = probs[pil];
+        const int64_t i = gl - P.row_base;
+        a0l = ld_i64(P.A.rp + i);
+        a1l = ld_i64(P.A.rp + i + 1);
+    }
+    int64_t g[G], a0[G], na[G];
+    int pi[G];
+#pragma unroll
+    for (int j = 0; j < G; ++j) {
+        g[j] = __shfl_sync(kFull, gl, j);
+        a0[j] = __shfl_sync(kFull, a0l, j);
+        na[j] = __shfl_sync(kFull, a1l, j) - a0[j];
+        pi[j] = __shfl_sync(kFull, pil, j);
+    }
+    int32_t k[G];
+    In a[G];
+#pragma unroll
+    for (int j = 0; j < G; ++j) {
+        k[j] = 0;
+        a[j] = In();
+        if (g[j] >= 0 && lane < na[j]) {
+            const Prob& P = probs[pi[j]];
+            k[j] = ld_i32(P.A.col + a0[j] + lane);
+            a[j] = load_val<In, S::kVal>(P.A.val, a0[j] + lane);
+        }
+    }
+    int64_t b0[G], len[G];
+#pragma unroll
+    for (int j = 0; j < G; ++j) {
+        b0[j] = 0;
+        len[j] = 0;
+        if (g[j] >= 0 && lane < na[j]) {
+            const Prob& P = probs[pi[j]];
+            b0[j] = ld_i64(P.B.rp + k[j]);
+            len[j] = ld_i64(P.B.rp + k[j] + 1) - b0[j];
+        }
+    }
+    int64_t q[G];
+    In oa[G];
+    int total[G];
+#pragma unroll
+    for (int j = 0; j < G; ++j) {
+        const int64_t incl = warp_incl_scan(len[j]);
+        const int64_t tot = __shfl_sync(kFull, incl, 31);
+        total[j] = (tot > kTinyMax || na[j] > 32) ? -1 : (int)tot;
+        q[j] = 0;
+        oa[j] = In();
+        if (total[j] > 0) {
+            const int excl = (int)(incl - len[j]);
+            int owner = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int c = owner + step;
+                if (__shfl_sync(kFull, excl, c) <= lane) owner = c;
+            }
+            q[j] = __shfl_sync(kFull, b0[j], owner) + (lane - __shfl_sync(kFull, excl, owner));
+            oa[j] = shfl_val<In, S::kVal>(a[j], owner);
+        }
+    }
+    int32_t col[G];
+    Out val[G];
+#pragma unroll
+    for (int j = 0; j < G; ++j) {
+        col[j] = INT32_MAX;
+        In bv = In();
+        if (lane < total[j]) {
+            const Prob& P = probs[pi[j]];
+            col[j] = ld_i32(P.B.col + q[j]);
+            if constexpr (kWithVal) bv = load_val<In, true>(P.B.val, q[j]);
+        }
+        if constexpr (kWithVal) val[j] = S::prod(oa[j], bv);
+    }
+#pragma unroll
+    for (int j = 0; j < G; ++j) {
+        if (g[j] < 0) continue;
+        const Prob& P = probs[pi[j]];
+        if (total[j] < 0) {
+            emit(g[j], P, col[j], val[j], -1, 0, false);
+            continue;
+        }
+        int rank = -1;
+        int m;
+        if constexpr (kSorted) m = tiny_sort_reduce<S, kWithVal>(col[j], val[j], rank);
+        else m = tiny_count_distinct(col[j]);
+        emit(g[j], P, col[j], val[j], rank, m, true);
+    }
+}
+
+// ---- per-row product counts, 32 rows per warp ---------------------------------
+//
+// Each lane brings one row g (active = false: none): rows with at most
+// kRowShort entries are summed by their lane (independent loads, unrolled);
+// longer rows are then walked by the whole warp one after another.  Gives
+// ub = sum nnz(B_k), the largest nnz(B_k) and nnz(A_i) of the lane's row
+// (zeros without one).  Callers give a warp rows far apart (row_of_lane), so
+// that the long rows of a graph's hub region spread over many warps.
+constexpr int kRowShort = 8;
+
+// the row of lane l in round `it` of warp w among nw warps: consecutive rows
+// go to consecutive warps
+SPG_DEV int64_t row_of_lane(int64_t it, int64_t w, int64_t nw) {
+    return (it * 32 + lane_id()) * nw + w;
+}
+
+SPG_DEV void warp_row_counts(const Prob* __restrict__ probs, int nprob, int64_t g, bool active,
+                             int64_t& ub, int64_t& mx, int64_t& na) {
+    const int lane = lane_id();
+    const bool v = active;
+    const int pi = (v && nprob > 1) ? find_prob(probs, nprob, g) : 0;
+    const Prob& P = probs[pi];
+    int64_t a0 = 0, a1 = 0;
+    if (v) {
+        const int64_t i = g - P.row_base;
+        a0 = ld_i64(P.A.rp + i);
+        a1 = ld_i64(P.A.rp + i + 1);
+    }
+    na = a1 - a0;
+    ub = 0;
+    mx = 0;
+    if (na <= kRowShort) {
+#pragma unroll
+        for (int t = 0; t < kRowShort; ++t) {
+            if (t < na) {
+                const int32_t k = ld_i32(P.A.col + a0 + t);
+                const int64_t l = ld_i64(P.B.rp + k + 1) - ld_i64(P.B.rp + k);
+                ub += l;
+                mx = l > mx ? l : mx;
+            }
+        }
+    }
+    unsigned longm = __ballot_sync(kFull, na > kRowShort);
+    while (longm) {
+        const int src = __ffs(longm) - 1;
+        longm &= longm - 1;
+        const Prob& Q = probs[__shfl_sync(kFull, pi, src)];
+        const int64_t b0 = __shfl_sync(kFull, a0, src), b1 = __shfl_sync(kFull, a1, src);
+        int64_t s = 0, m = 0;
+        int64_t q = b0 + lane;
+        for (; q + 96 < b1; q += 128) {   // 4 independent gathers in flight per lane
+            int32_t k[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) k[u] = ld_i32(Q.A.col + q + 32 * u);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t l = ld_i64(Q.B.rp + k[u] + 1) - ld_i64(Q.B.rp + k[u]);
+                s += l;
+                m = l > m ? l : m;
+            }
+        }
+        for (; q < b1; q += 32) {
+            const int32_t k = ld_i32(Q.A.col + q);
+            const int64_t l = ld_i64(Q.B.rp + k + 1) - ld_i64(Q.B.rp + k);
+            s += l;
+            m = l > m ? l : m;
+        }
+        s = warp_sum(s);
+        m = warp_max(m);
+        if (lane == src) {
+            ub = s;
+            mx = m;
+        }
+    }
 }
 
 // ---- shared-memory hash tables (linear probing, power-of-two size) ----------

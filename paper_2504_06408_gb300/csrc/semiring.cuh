@@ -12,7 +12,8 @@
 //                      exact semirings, order-dependent rounding for floats)
 //   touched(Slot)      some product reached this Slot (only when !kBitmap)
 //   out(Slot)          Slot -> output value
-//   add(Out, Out)      plain (+) on outputs, used by the stage merge
+//   prod(a, b)         a (x) b as an output value (register accumulation)
+//   add(Out, Out)      plain (+) on outputs (stage merge, register accumulation)
 #pragma once
 
 #include "common.cuh"
@@ -37,6 +38,7 @@ struct SrPtF64 {
     static SPG_DEV void acc(Slot* s, In a, In b) { atomicAdd(s, __dmul_rn(a, b)); }
     static SPG_DEV bool touched(Slot) { return true; }
     static SPG_DEV Out out(Slot v) { return v; }
+    static SPG_DEV Out prod(In a, In b) { return __dmul_rn(a, b); }
     static SPG_DEV Out add(Out x, Out y) { return __dadd_rn(x, y); }
 };
 
@@ -49,6 +51,7 @@ struct SrPtF32 {
     static SPG_DEV void acc(Slot* s, In a, In b) { atomicAdd(s, __fmul_rn(a, b)); }
     static SPG_DEV bool touched(Slot) { return true; }
     static SPG_DEV Out out(Slot v) { return v; }
+    static SPG_DEV Out prod(In a, In b) { return __fmul_rn(a, b); }
     static SPG_DEV Out add(Out x, Out y) { return __fadd_rn(x, y); }
 };
 
@@ -63,6 +66,9 @@ struct SrPtI64 {
     }
     static SPG_DEV bool touched(Slot) { return true; }
     static SPG_DEV Out out(Slot v) { return (Out)v; }
+    static SPG_DEV Out prod(In a, In b) {
+        return (Out)((unsigned long long)a * (unsigned long long)b);
+    }
     static SPG_DEV Out add(Out x, Out y) {
         return (Out)((unsigned long long)x + (unsigned long long)y);
     }
@@ -100,6 +106,7 @@ struct SrMpF32 {
     }
     static SPG_DEV bool touched(Slot v) { return v != 0xffffffffu; }
     static SPG_DEV Out out(Slot v) { return ordered_to_f32(v); }
+    static SPG_DEV Out prod(In a, In b) { return __fadd_rn(a, b); }
     static SPG_DEV Out add(Out x, Out y) {
         return f32_to_ordered(y) < f32_to_ordered(x) ? y : x;
     }
@@ -114,6 +121,7 @@ struct SrBool {
     static SPG_DEV void acc(Slot*, In, In) {}
     static SPG_DEV bool touched(Slot) { return true; }
     static SPG_DEV Out out(Slot) { return 1; }
+    static SPG_DEV Out prod(In, In) { return 1; }
     static SPG_DEV Out add(Out, Out) { return 1; }
 };
 
@@ -162,6 +170,7 @@ struct SrOverlap {
         return OvRecord{(int32_t)v.count, (int32_t)(v.m1 >> 32), (int32_t)(v.m1 & 0xffffffffu),
                         (int32_t)(v.m2 >> 32), (int32_t)(v.m2 & 0xffffffffu)};
     }
+    static SPG_DEV Out prod(In a, In b) { return OvRecord{1, a, b, INT32_MAX, INT32_MAX}; }
     static SPG_DEV unsigned long long pk(int32_t a, int32_t b) {
         return ((unsigned long long)(uint32_t)a << 32) | (unsigned long long)(uint32_t)b;
     }

@@ -10,6 +10,7 @@
 //           memory, slab after slab; nnz = popcount.
 #include "plan.h"
 #include "rowwork.cuh"
+#include "semiring.cuh"
 
 namespace spg {
 
@@ -20,8 +21,11 @@ SPG_DEV int sym_tier(int64_t ub, const Tuning& t) {
     return kTierDense;
 }
 
-// tier-major key; inside a tier rows with more work come first
+// tier-major key; inside a tier rows with more work come first.  Tiny rows
+// (ub <= 32) of the warp tier share its last sub-bin, where the warp kernel
+// takes them several at a time.
 SPG_DEV int bin_key(int tier, int64_t work) {
+    if (tier == kTierWarp && work <= kTinyMax) return tier * kSubBins + kSubBins - 1;
     int lg = work > 0 ? 63 - __clzll(work) : 0;
     if (lg > kSubBins - 1) lg = kSubBins - 1;
     return tier * kSubBins + (kSubBins - 1 - lg);
@@ -47,24 +51,26 @@ __global__ void __launch_bounds__(256) k_analyze(const Prob* __restrict__ probs,
     const int lane = lane_id();
     unsigned long long prod = 0;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); g < R; g += nw) {
-        const Prob& P = probs[nprob == 1 ? 0 : find_prob(probs, nprob, g)];
-        const int64_t i = g - P.row_base;
-        const int64_t a0 = ld_i64(P.A.rp + i), a1 = ld_i64(P.A.rp + i + 1);
-        int64_t s = 0;
-        for (int64_t q = a0 + lane; q < a1; q += 32) {
-            const int32_t k = ld_i32(P.A.col + q);
-            s += ld_i64(P.B.rp + k + 1) - ld_i64(P.B.rp + k);
-        }
-        s = warp_sum(s);
-        if (lane == 0) {
-            ub[g] = s;
-            const bool skipped = skip && skip[g];
-            if (s == 0 && !skipped) cnt[g] = 0;
+    const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id();
+    // 32 rows per warp, one per lane (long rows walked by the warp); skipped
+    // rows keep the ub they have and are not walked
+    for (int64_t it = 0; it * 32 * nw < R; ++it) {
+        const int64_t g = row_of_lane(it, w, nw);
+        const bool skipped = skip && g < R && skip[g];
+        int64_t s, mx, na;
+        warp_row_counts(probs, nprob, g, g < R && !skipped, s, mx, na);
+        if (g < R) {
+            if (skipped) {
+                s = ub[g];
+            } else {
+                ub[g] = s;
+                if (s == 0) cnt[g] = 0;
+            }
             atomicAdd(&s_hist[bin_key(skipped ? kTierEmpty : sym_tier(s, t), s)], 1);
             prod += (unsigned long long)s;
         }
     }
+    prod = warp_sum(prod);
     if (lane == 0 && prod) atomicAdd(&ctr->products, prod);
     __syncthreads();
     for (int b = threadIdx.x; b < kNumBins; b += blockDim.x)
@@ -133,6 +139,8 @@ struct KeyInsertOp {
     SPG_DEV void sorted(int32_t col, char a, char b, bool valid) { any(col, a, b, valid); }
 };
 
+constexpr int kTinyRows = 4;   // tiny rows in flight per warp
+
 __global__ void __launch_bounds__(kWarpTierWarps * 32)
     k_sym_warp(const Prob* __restrict__ probs, int nprob, const int32_t* __restrict__ rows,
                const Counters* __restrict__ ctr, const int64_t* __restrict__ ub,
@@ -141,14 +149,17 @@ __global__ void __launch_bounds__(kWarpTierWarps * 32)
     int32_t* tab = smem_i32 + (size_t)warp_id() * per_warp_slots;
     const int lane = lane_id();
     const int beg = ctr->sym_bin_off[kTierWarp * kSubBins];
+    const int tiny = ctr->sym_bin_off[(kTierWarp + 1) * kSubBins - 1];
     const int end = ctr->sym_bin_off[(kTierWarp + 1) * kSubBins];
-    const int stride = gridDim.x * kWarpTierWarps;
+    const int nwarps = gridDim.x * kWarpTierWarps;
+    const int wg = blockIdx.x * kWarpTierWarps + warp_id();
     const Slab single{0, 0, true, true, true, nullptr, nullptr, 0, 0};
-    for (int r = beg + blockIdx.x * kWarpTierWarps + warp_id(); r < end; r += stride) {
+    for (int r = beg + wg; r < tiny; r += nwarps) {
         const int64_t g = rows[r];
         const Prob& P = probs[nprob == 1 ? 0 : find_prob(probs, nprob, g)];
         const int64_t i = g - P.row_base;
         const int64_t u = ub[g];
+        const int64_t a0 = ld_i64(P.A.rp + i), a1 = ld_i64(P.A.rp + i + 1);
         const int64_t distinct = u < P.B.ncols ? u : P.B.ncols;
         int64_t T = dev_next_pow2(2 * distinct);
         if (T < 32) T = 32;
@@ -159,12 +170,22 @@ __global__ void __launch_bounds__(kWarpTierWarps * 32)
         for (int s = lane; s < T; s += 32) tab[s] = kEmptyKey;
         __syncwarp();
         KeyInsertOp op{tab, 32 - log2_exact(T), (uint32_t)(T - 1), st, g, 0};
-        const int64_t a0 = ld_i64(P.A.rp + i), a1 = ld_i64(P.A.rp + i + 1);
         for (int64_t p0 = a0; p0 < a1; p0 += 32)
             chunk_products<char, false>(P.A, P.B, p0, a1, 0, single, op);
         const int tot = warp_sum(op.mine);
         if (lane == 0) cnt[g] = tot;
         __syncwarp();
+    }
+    // tiny rows: products sorted in registers, kTinyRows rows per warp at a time
+    for (int r = tiny + wg * kTinyRows; r < end; r += nwarps * kTinyRows) {
+        tiny_batch<SrBool, kTinyRows, false, false>(
+            probs, nprob, rows, r, end,
+            [&](int64_t g, const Prob&, int32_t, char, int, int m, bool ok) {
+                if (lane == 0) {
+                    if (ok) cnt[g] = m;
+                    else flag_overflow(st, g);
+                }
+            });
     }
 }
 
@@ -259,9 +280,21 @@ __global__ void __launch_bounds__(kBlockThreads)
             const int words = (hi - lo + 31) >> 5;
             for (int w = threadIdx.x; w < words; w += blockDim.x) bm[w] = 0u;
             __syncthreads();
-            const Slab slab{lo, hi, s == 0, s == nslabs - 1, nslabs == 1, cursor, nullptr, 0, s};
             BitOrOp op{bm, lo};
-            cta_row_products<char, false>(P.A, P.B, a0, a1, P.nnz_base + (a0 - ld_i64(P.A.rp)), slab, bs, op);
+            if (nslabs == 1 && a1 - a0 <= 32) {
+                // <= 32 entries: every warp holds the entry table and takes an
+                // equal share of the products (no batch compaction)
+                LaneEntry<char, false> le;
+                le.load(P.A, P.B, a0 + lane, a0 + lane < a1);
+                int64_t b, e;
+                le.range(nullptr, 0, 1, 0, 1, b, e);
+                warp_table_walk<char, false>(P.B, b, e, char(), op);
+                __syncthreads();
+            } else {
+                const Slab slab{lo, hi, s == 0, s == nslabs - 1, nslabs == 1, cursor, nullptr, 0, s};
+                cta_row_products<char, false>(P.A, P.B, a0, a1, P.nnz_base + (a0 - ld_i64(P.A.rp)),
+                                              slab, bs, op);
+            }
             if (nslabs == 1 && cache_slots > 0 && words <= cache_words) {
                 // keep the row's bitmap for the numeric phase while cache slots last
                 if (threadIdx.x == 0) {
@@ -404,7 +437,7 @@ cudaError_t launch_write_probs(const ProbTable& tab, int nprob, const WsPtrs& w,
 cudaError_t launch_analyze(const WsPtrs& w, int nprob, int64_t R, const Tuning& t,
                            const DevInfo& dev, cudaStream_t st) {
     if (R > 0) {
-        int64_t blocks = (R + 7) / 8;
+        int64_t blocks = (R + 255) / 256;    // 8 warps x 32 rows
         if (blocks > (int64_t)dev.sms * 16) blocks = (int64_t)dev.sms * 16;
         k_analyze<<<(unsigned)blocks, 256, 0, st>>>(w.probs, nprob, R, t, w.ub, w.cnt, w.ctr,
                                                     w.skip);

@@ -40,7 +40,8 @@ from . import spgemm as api
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_STEM = os.path.join(HERE, "weights", "row_nnz_mlp")
-EXACT_MAX_UB = 16          # rows with ub <= this are sized by ub (no prediction)
+EXACT_MAX_UB = 32          # rows with ub <= this are sized by ub (no prediction): they
+                           # take the library's register path, whose capacity is ub
 TRAIN_SEEDS = (1001, 1002, 1003, 1004, 1005, 1006)
 VALID_SEEDS = (1007,)
 

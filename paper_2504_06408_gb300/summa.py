@@ -45,11 +45,18 @@ class Summa:
     (stages), col_cuts split B's columns (grid columns); defaults are even.
     batched=False runs one library call per block product and per merge (the
     plain form); batched=True one call for all of them.
+
+    A symbolic call leaves state in its workspace that its numeric call reads,
+    so the plain form gives every block product its own workspace, from a
+    handle whose symbolic bitmap cache is split between the blocks
+    (unbatched_cache_bytes in total; `tuning` = the other tier limits of that
+    handle).
     """
 
     def __init__(self, handle: api.Handle, sr: int, A: api.DeviceCSR, B: api.DeviceCSR,
                  q: int = 4, row_cuts=None, inner_cuts=None, col_cuts=None,
-                 batched: bool = True):
+                 batched: bool = True, unbatched_cache_bytes: int = 4 << 30,
+                 tuning: Optional[dict] = None):
         import torch
         self.h, self.sr, self.q, self.batched = handle, sr, q, batched
         self.A, self.B = A, B
@@ -67,6 +74,9 @@ class Summa:
         self.dev = A.rp.device
         self._torch = torch
         self.graph = None
+        if not batched:
+            per = max(unbatched_cache_bytes // len(self.blocks), 1 << 20)
+            self.hb = api.Handle(tuning=dict(tuning or {}, bitmap_cache_bytes=per))
 
     # ---- phase 1: block products -------------------------------------------------
 
@@ -78,10 +88,12 @@ class Summa:
                                   dtype=torch.uint8, device=self.dev)
             self.p_nnz = self.h.symbolic_batched(self.sr, self.As, self.Bs, self.p_rp, self.ws)
         else:
-            size = max(self.h.workspace_size(self.sr, a, b) for a, b in zip(self.As, self.Bs))
-            self.ws = torch.empty(size, dtype=torch.uint8, device=self.dev)
-            self.p_nnz = [self.h.symbolic(self.sr, a, b, rp, self.ws)
-                          for a, b, rp in zip(self.As, self.Bs, self.p_rp)]
+            self.ws_list = [torch.empty(max(self.hb.workspace_size(self.sr, a, b), 1),
+                                        dtype=torch.uint8, device=self.dev)
+                            for a, b in zip(self.As, self.Bs)]
+            self.ws = self.ws_list[0]
+            self.p_nnz = [self.hb.symbolic(self.sr, a, b, rp, w)
+                          for a, b, rp, w in zip(self.As, self.Bs, self.p_rp, self.ws_list)]
         self.products = self.h.stats()["products"] if self.batched else None
         # one buffer for all partials, sliced per block
         tot = int(sum(self.p_nnz))
@@ -102,8 +114,9 @@ class Summa:
             self.h.numeric_batched(self.sr, self.As, self.Bs, self.p_rp, self.p_col,
                                    self.p_val if self._pval is not None else None, self.ws)
         else:
-            for a, b, rp, c, v in zip(self.As, self.Bs, self.p_rp, self.p_col, self.p_val):
-                self.h.numeric(self.sr, a, b, rp, c, v, self.ws)
+            for a, b, rp, c, v, w in zip(self.As, self.Bs, self.p_rp, self.p_col, self.p_val,
+                                         self.ws_list):
+                self.hb.numeric(self.sr, a, b, rp, c, v, w)
 
     # ---- phase 2: merge of the stage partials of every C block ------------------
 
@@ -175,6 +188,17 @@ class Summa:
             self.merge_write()
         self.graph = g
         return g
+
+    def check(self):
+        """Kernel-detected errors of every call (raises SpgemmError)."""
+        if self.batched:
+            self.h.check(self.ws)
+            self.h.check(self.mws)
+        else:
+            for w in self.ws_list:
+                self.hb.check(w)
+            for w in self._mws_per_group:
+                self.h.check(w)
 
     def block(self, I: int, J: int) -> api.DeviceCSR:
         k = I * self.q + J

@@ -273,6 +273,39 @@ def test_learned_calls_need_a_plan():
     assert e.value.status == 8
 
 
+@pytest.mark.parametrize("mode", ["ub_sized", "capacity_one"])
+def test_learned_calls_repeat_after_one_plan(mode):
+    """symbolic + numeric may run again on the same plan (e.g. new values of
+    the same patterns): same C, same statistics."""
+    sr = api.MIN_PLUS_F32
+    pat = I.rmat(12, seed=5, dtype=None)
+    A = values_for(sr, pat, 2)
+    dA = dev(sr, A)
+    h = api.Handle()
+    opts = dict(MODES[mode])
+    if opts.get("model") == "random":
+        opts["model"] = random_params(h, 11)[1]
+    ws = torch.empty(h.learned_workspace_size(sr, dA, dA), dtype=torch.uint8, device="cuda")
+    sb = h.learned_plan(sr, dA, dA, ws, **opts)
+    staging = torch.empty(max(sb, 1), dtype=torch.uint8, device="cuda")
+    exp = oracle.spgemm(sr, A, A)
+    seen = []
+    for _ in range(3):
+        c_rp = torch.empty(A.nrows + 1, dtype=torch.int64, device="cuda")
+        nnz = h.learned_symbolic(sr, dA, dA, c_rp, ws, staging)
+        assert nnz == exp.nnz
+        c_col = torch.empty(nnz, dtype=torch.int32, device="cuda")
+        c_val = api.out_tensor(sr, nnz)
+        h.learned_numeric(sr, dA, dA, c_rp, c_col, c_val, ws, staging)
+        h.check(ws)
+        got = api.to_host(api.DeviceCSR(A.nrows, A.ncols, c_rp, c_col, c_val), sr)
+        assert_pattern_equal(got.rp, got.col, exp.rp, exp.col)
+        assert_values(sr, got.val, exp.val)
+        st = h.stats()
+        seen.append((st["learned_rows"], st["overflow_rows"], st["learned_nnz"]))
+    assert seen[0] == seen[1] == seen[2]
+
+
 # ---- what the trained network gains ----------------------------------------------------
 
 def _weights_or_skip():

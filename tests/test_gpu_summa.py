@@ -163,9 +163,27 @@ def test_summa_4x4_matches_oracle(sr, batched):
                col_cuts=cuts, batched=batched)
     sm.plan()
     sm.run()
-    h.check(sm.ws)
+    sm.check()
     torch.cuda.synchronize()
     _check_blocks(sm, sr, A, B)
+
+
+@pytest.mark.parametrize("batched", [True, False])
+def test_summa_dense_tier_blocks(batched):
+    """Every block row in the dense tiers (symbolic bitmap cache kept): in the
+    plain form each block product needs its own workspace."""
+    from test_gpu_spgemm import TIERS
+    sr = api.MIN_PLUS_F32
+    pat = I.rmat(12, seed=2, dtype=None)
+    A = values_for(sr, pat, 7)
+    h = api.Handle(tuning=TIERS["all_dense"])
+    dA = api.DeviceCSR.from_host(A, val_dtype=np.float32)
+    sm = Summa(h, sr, dA, dA, q=4, batched=batched, tuning=TIERS["all_dense"])
+    sm.plan()
+    sm.run()
+    sm.check()
+    torch.cuda.synchronize()
+    _check_blocks(sm, sr, A, A)
 
 
 def test_summa_graph_replay_matches():
