@@ -43,16 +43,17 @@ sys.path.insert(0, ROOT)
 os.environ.setdefault("PYTORCH_CUDA_ALLOC_CONF", "expandable_segments:True")
 
 METRIC = "semiring SpGEMM GFLOPS (2*products/s), R-MAT scale 18 A^2 over min-plus FP32"
+METRIC_SCALED = "semiring SpGEMM GFLOPS (2*products/s), R-MAT scale %d A^2 over min-plus FP32"
 UNIT = "GFLOPS"
 SCALE = 18
 L2_FLUSH_BYTES = 256 << 20
 
 
-def workload_config(P=None, nnz_c=None, nnz_a=None):
-    cfg = {"workload": "R-MAT scale 18 (262,144 vertices, edge factor 16, a=.57 b=.19 c=.19 "
+def workload_config(P=None, nnz_c=None, nnz_a=None, scale=SCALE):
+    cfg = {"workload": "R-MAT scale %d (%s vertices, edge factor 16, a=.57 b=.19 c=.19 "
                        "d=.05), symmetrised, self-loops and duplicates removed, FP32 weights "
-                       "U[1,100), seed 1; C = A*A over min-plus FP32",
-           "semiring": "min_plus_f32", "n": 1 << SCALE,
+                       "U[1,100), seed 1; C = A*A over min-plus FP32" % (scale, f"{1 << scale:,}"),
+           "semiring": "min_plus_f32", "n": 1 << scale,
            "l2": "256 MiB buffer written before every timed step"}
     if nnz_a is not None:
         cfg["nnz_A"] = int(nnz_a)
@@ -61,6 +62,25 @@ def workload_config(P=None, nnz_c=None, nnz_a=None):
     if nnz_c is not None:
         cfg["nnz_C"] = int(nnz_c)
     return cfg
+
+
+def max_over_ranks(x: float, dist=None, device="cuda") -> float:
+    """The largest value of x over the ranks (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(total_ms: float, steps: int, products_per_rank: int, world: int, dist=None,
+                   device="cuda"):
+    """(ms per step, GFLOPS) of the whole job: every rank runs the same product
+    (replicas, weak scaling), the job takes as long as the slowest rank, and
+    value = all ranks' 2 x products / that time."""
+    ms = max_over_ranks(total_ms, dist, device) / steps
+    return ms, world * 2.0 * products_per_rank / (ms * 1e-3) / 1e9
 
 
 def dist_info():
@@ -360,6 +380,9 @@ def main():
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the learned / batched vs plain comparisons")
     ap.add_argument("--form-reps", type=int, default=3)
+    ap.add_argument("--scale", type=int, default=SCALE,
+                    help="R-MAT scale of the product (18 = the headline workload; smaller "
+                         "scales are for profiling captures)")
     args = ap.parse_args()
     world, rank, local = dist_info()
     if args.impl == "reference":
@@ -382,7 +405,7 @@ def main():
             dist.barrier()
 
     sr = api.MIN_PLUS_F32
-    A = I.rmat(SCALE, dtype=np.float32, seed=1)
+    A = I.rmat(args.scale, dtype=np.float32, seed=1)
     h = api.Handle()
     dA = api.DeviceCSR.from_host(A, val_dtype=np.float32)
     ws = torch.empty(h.workspace_size(sr, dA, dA), dtype=torch.uint8, device="cuda")
@@ -426,13 +449,7 @@ def main():
         barrier()
     h.set_timing(False)
     h.check(ws)
-    total_ms = sum(times)
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
-    value = world * 2.0 * P / (ms_per_step * 1e-3) / 1e9
+    ms_per_step, value = job_throughput(sum(times), args.steps, P, world, dist)
 
     # roofline of the dominant kernel (numeric dense tier) by the Gustavson
     # traffic model restricted to the rows it processes
@@ -445,7 +462,7 @@ def main():
     d_ms = statistics.mean(dense_ms)
     achieved = t_alg / (d_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
-    traffic = traffic_from_profiles(kernel_source_hash())
+    traffic = traffic_from_profiles(kernel_source_hash()) if args.scale == SCALE else None
     roofline = {"bound": "hbm", "kernel": "k_num_rank<SrMpF32> (numeric dense tier)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_kind": peak_kind, "traffic": traffic, "kernel_ms": d_ms,
@@ -474,11 +491,7 @@ def main():
             _, _, _, n2 = h2.host_multiply(sr, hA, hA, out=out)
             et.append(time.perf_counter() - t0)
         assert n2 == nnz
-        e_s = statistics.mean(et)
-        if dist is not None:
-            t = torch.tensor([e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_s = float(t.item())
+        e_s = max_over_ranks(statistics.mean(et), dist)
         h2d = (A.nrows + 1) * 8 + A.nnz * 8
         d2h = (A.nrows + 1) * 8 + nnz * 8
         e2e = {"value": world * 2.0 * P / e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -496,7 +509,7 @@ def main():
                          "ms_per_step" % reps}
         del c_col, c_val, step
         torch.cuda.empty_cache()
-        forms["rmat18_min_plus"] = learned_forms(api, h, sr, dA, dA, flush, reps, ms_per_step,
+        forms[f"rmat{args.scale}_min_plus"] = learned_forms(api, h, sr, dA, dA, flush, reps, ms_per_step,
                                                  params, meta)
         torch.cuda.empty_cache()
         lap = I.laplacian(2048)
@@ -506,13 +519,13 @@ def main():
             api, h, api.PLUS_TIMES_F64, dL, dL, flush, reps, pms, params, meta)
         del dL
         torch.cuda.empty_cache()
-        A64 = I.rmat(SCALE, dtype=np.float64, seed=1)
+        A64 = I.rmat(args.scale, dtype=np.float64, seed=1)
         dA64 = api.DeviceCSR.from_host(A64, val_dtype=np.float64)
         pms, _ = plain_ms_of(api, h, api.PLUS_TIMES_F64, dA64, dA64, flush, reps)
         torch.cuda.empty_cache()
         sf = summa_forms(api, Summa, h, api.PLUS_TIMES_F64, dA64, flush, reps)
         sf["plain_unblocked_ms"] = pms
-        forms["rmat18_plus_times_f64_summa4x4"] = sf
+        forms[f"rmat{args.scale}_plus_times_f64_summa4x4"] = sf
         del dA64
         torch.cuda.empty_cache()
 
@@ -521,11 +534,12 @@ def main():
         cpu, _, _ = cpu_oracle_sample(A)
 
     if rank == 0:
-        res = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        res = {"metric": METRIC if args.scale == SCALE else METRIC_SCALED % args.scale,
+               "value": value, "unit": UNIT, "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                "data": "synthetic",
-               "config": dict(workload_config(P=P, nnz_c=nnz, nnz_a=A.nnz),
+               "config": dict(workload_config(P=P, nnz_c=nnz, nnz_a=A.nnz, scale=args.scale),
                               parallelism=f"replicas x{world}"),
                "hbm_roofline_frac_step": (t_alg_all / (ms_per_step * 1e-3) / 1e9) / peak,
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,

@@ -74,6 +74,20 @@ SPG_DEV T warp_incl_scan(T v) {
     return v;
 }
 
+// Store that streams past L2 (evict-first): output written once and not read
+// back by the kernel, so it does not push the input matrices out of L2.
+template <class T>
+SPG_DEV void st_stream(T* p, const T& v) {
+    if constexpr (sizeof(T) == 4 && alignof(T) >= 4) {
+        __stcs(reinterpret_cast<unsigned int*>(p), *reinterpret_cast<const unsigned int*>(&v));
+    } else if constexpr (sizeof(T) == 8 && alignof(T) >= 8) {
+        __stcs(reinterpret_cast<unsigned long long*>(p),
+               *reinterpret_cast<const unsigned long long*>(&v));
+    } else {
+        *p = v;
+    }
+}
+
 SPG_DEV int64_t ld_i64(const int64_t* p) { return __ldg(p); }
 SPG_DEV int32_t ld_i32(const int32_t* p) { return __ldg(p); }
 

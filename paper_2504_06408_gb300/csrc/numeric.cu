@@ -148,8 +148,8 @@ struct DenseAccOp {
 
 template <class S>
 SPG_DEV void write_entry(const Prob& P, int64_t pos, int32_t col, const typename S::Slot& v) {
-    P.c_col[pos] = col;
-    if constexpr (S::kVal) reinterpret_cast<typename S::Out*>(P.c_val)[pos] = S::out(v);
+    st_stream(P.c_col + pos, col);
+    if constexpr (S::kVal) st_stream(reinterpret_cast<typename S::Out*>(P.c_val) + pos, S::out(v));
 }
 
 template <class S>
@@ -730,7 +730,7 @@ __global__ void __launch_bounds__(kRankThreads, 1)
         if (slot >= 0 && slot < cache_slots && words <= cache_words) {
             const uint4* src = reinterpret_cast<const uint4*>(bm_cache + (int64_t)slot * cache_words);
             uint4* dst = reinterpret_cast<uint4*>(bm);
-            for (int w = tid; w < (words + 3) / 4; w += blockDim.x) dst[w] = __ldg(src + w);
+            for (int w = tid; w < (words + 3) / 4; w += blockDim.x) dst[w] = __ldcs(src + w);
             __syncthreads();
         } else {
             for (int w = tid; w < words; w += blockDim.x) bm[w] = 0u;
@@ -802,13 +802,13 @@ __global__ void __launch_bounds__(kRankThreads, 1)
                         stage[pos++] = cbase + b;
                     }
                     __syncwarp();
-                    for (int t = lane; t < Tc; t += 32) dst[t] = stage[t];
+                    for (int t = lane; t < Tc; t += 32) st_stream(dst + t, stage[t]);
                     __syncwarp();
                 } else {
                     while (bits) {
                         const int b = __ffs(bits) - 1;
                         bits &= bits - 1u;
-                        dst[pos++] = cbase + b;
+                        st_stream(dst + pos++, (int32_t)(cbase + b));
                     }
                 }
             }
@@ -839,7 +839,7 @@ __global__ void __launch_bounds__(kRankThreads, 1)
                         cta_range_products<In, S::kVal>(P.A, P.B, a0, a1, le, small, sp, sp_stride,
                                                         nslabs, 0, nslabs, bs, op);
                     typename S::Out* cv = reinterpret_cast<typename S::Out*>(P.c_val) + off + r0;
-                    for (int t = tid; t < cnt; t += blockDim.x) cv[t] = S::out(vals[t]);
+                    for (int t = tid; t < cnt; t += blockDim.x) st_stream(cv + t, S::out(vals[t]));
                     __syncthreads();
                 }
                 s0 = s1;

@@ -247,7 +247,9 @@ struct BitOrOp {
     SPG_DEV void sorted(int32_t col, char a, char b, bool valid) { any(col, a, b, valid); }
 };
 
-__global__ void __launch_bounds__(kBlockThreads)
+// 3 CTAs of 512 threads per SM (registers capped at 42): the walk is latency-bound,
+// more resident warps measured ~12% faster than 2 CTAs at 64 registers
+__global__ void __launch_bounds__(kBlockThreads, 3)
     k_sym_dense(const Prob* __restrict__ probs, int nprob, const int32_t* __restrict__ rows,
                 Counters* ctr, int64_t* __restrict__ cnt, int32_t* cursor, int slab_cols,
                 uint32_t* bm_cache, int32_t* row_slot, int64_t cache_words, int64_t cache_slots) {
@@ -306,7 +308,7 @@ __global__ void __launch_bounds__(kBlockThreads)
                 if (s_slot >= 0) {
                     uint4* dst = reinterpret_cast<uint4*>(bm_cache + (int64_t)s_slot * cache_words);
                     const uint4* src = reinterpret_cast<const uint4*>(bm);
-                    for (int w = threadIdx.x; w < (words + 3) / 4; w += blockDim.x) dst[w] = src[w];
+                    for (int w = threadIdx.x; w < (words + 3) / 4; w += blockDim.x) __stcs(dst + w, src[w]);
                 }
             }
             int mine = 0;
