@@ -919,7 +919,8 @@ spg_status spgemm_learned_plan(spg_handle* h, spg_semiring sr, const spg_csr* A,
     fill_probs(tab, 1, A, B, &no_rp, nullptr, nullptr);
     e = launch_write_probs(*tab, 1, w, h->dev, st);
     delete tab;
-    if (e == cudaSuccess) e = launch_row_features(w.probs, 1, L.R, lw.feat, w.ub, h->dev, st);
+    if (e == cudaSuccess)
+        e = launch_row_features(w.probs, 1, L.R, lw.feat, w.ub, w.rows_num, w.ctr, h->dev, st);
     if (e == cudaSuccess && model)   // only the rows whose capacity the prediction sets
         e = launch_mlp_forward(lw.feat, L.R, model, lw.z, w.ub, exact_max, h->dev, st);
     if (e == cudaSuccess)
@@ -1044,8 +1045,9 @@ spg_status spgemm_row_features(spg_handle* h, const spg_csr* A, const spg_csr* B
     if ((uintptr_t)feat % 16 != 0)
         return fail(h, SPG_ERR_INVALID_ARG, "feat must be 16-byte aligned");
     const WsLayout L = layout_for(A, B, effective_tuning(h, SPG_SR_BOOL_OR_AND));
-    if (!workspace || workspace_bytes < L.ub)
-        return fail(h, SPG_ERR_WORKSPACE, "workspace needs %zu bytes", L.ub);
+    if (!workspace || workspace_bytes < L.rows_num + sizeof(int32_t) * (size_t)L.R)
+        return fail(h, SPG_ERR_WORKSPACE, "workspace needs %zu bytes",
+                    L.rows_num + sizeof(int32_t) * (size_t)L.R);
     cudaStream_t st = (cudaStream_t)stream;
     const WsPtrs w = ws_ptrs(workspace, L);
     ProbTable* tab = new ProbTable;
@@ -1053,7 +1055,8 @@ spg_status spgemm_row_features(spg_handle* h, const spg_csr* A, const spg_csr* B
     fill_probs(tab, 1, A, B, &no_rp, nullptr, nullptr);
     cudaError_t e = launch_write_probs(*tab, 1, w, h->dev, st);
     delete tab;
-    if (e == cudaSuccess) e = launch_row_features(w.probs, 1, A->nrows, feat, ub, h->dev, st);
+    if (e == cudaSuccess)
+        e = launch_row_features(w.probs, 1, A->nrows, feat, ub, w.rows_num, w.ctr, h->dev, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "row features");
     return SPG_OK;
 }

@@ -117,9 +117,9 @@ SPG_DEV void stage_write(void* sval, int32_t* scol, int64_t pos, int32_t col,
 }
 
 // Hash accumulation bounded by the row's capacity: the insert that would make
-// the distinct count exceed cap sets *abort, after which every product is
-// dropped (the row goes to the exact path).  The table holds 2 cap slots or
-// more, so probing stays short.
+// the distinct count exceed cap sets *abort and the row goes to the exact
+// path.  The table holds 2 cap slots or more, so probing stays short; a full
+// table also aborts.
 template <class S>
 struct CapHashOp {
     int32_t* keys;
@@ -130,7 +130,8 @@ struct CapHashOp {
     volatile int* abort;   // shared
     int cap;
     SPG_DEV void any(int32_t col, typename S::In a, typename S::In b, bool valid) {
-        if (!valid || *abort) return;
+        // (the abort flag is read only before inserting a new key)
+        if (!valid) return;
         uint32_t s = hash_slot(col, shift);
         for (uint32_t n = 0;; ++n) {
             if (n > mask) {
@@ -140,6 +141,7 @@ struct CapHashOp {
             const int32_t cur = *(volatile int32_t*)(keys + s);
             if (cur == col) break;
             if (cur == kEmptyKey) {
+                if (*abort) return;   // abandoned table: no more keys, probes stay short
                 const int32_t old = atomicCAS(keys + s, kEmptyKey, col);
                 if (old == kEmptyKey) {
                     if (atomicAdd(count, 1) >= cap) {

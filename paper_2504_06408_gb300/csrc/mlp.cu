@@ -30,22 +30,52 @@ SPG_DEV float bf(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
 // ---- features -----------------------------------------------------------------
 
-// 32 rows per warp (warp_row_counts): f = log1p(nnz(A_i), ub_i, max nnz(B_k),
-// mean nnz(B_k)), one 16-byte store per row
+// f = log1p(nnz(A_i), ub_i, max nnz(B_k), mean nnz(B_k)), one 16-byte store per
+// row.  Pass 1: 32 consecutive rows per warp, long rows to a list; pass 2: a
+// warp per listed row.
+SPG_DEV void store_features(float* feat, int64_t* ub_out, int64_t g, int64_t na, int64_t s,
+                            int64_t mx) {
+    const float4 f = make_float4(log1pf((float)na), log1pf((float)s), log1pf((float)mx),
+                                 log1pf(na > 0 ? (float)s / (float)na : 0.f));
+    reinterpret_cast<float4*>(feat)[g] = f;
+    if (ub_out) ub_out[g] = s;
+}
+
 __global__ void k_row_features(const Prob* __restrict__ probs, int nprob, int64_t R,
-                               float* __restrict__ feat, int64_t* __restrict__ ub_out) {
+                               float* __restrict__ feat, int64_t* __restrict__ ub_out,
+                               int32_t* long_rows, Counters* ctr) {
+    const int lane = lane_id();
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id();
-    for (int64_t it = 0; it * 32 * nw < R; ++it) {
-        const int64_t g = row_of_lane(it, w, nw);
-        int64_t s, mx, na;
-        warp_row_counts(probs, nprob, g, g < R, s, mx, na);
+    for (int64_t g0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id()) * 32; g0 < R;
+         g0 += nw * 32) {
+        const int64_t g = g0 + lane;
+        bool is_long = false;
         if (g < R) {
-            const float4 f = make_float4(log1pf((float)na), log1pf((float)s), log1pf((float)mx),
-                                         log1pf(na > 0 ? (float)s / (float)na : 0.f));
-            reinterpret_cast<float4*>(feat)[g] = f;
-            if (ub_out) ub_out[g] = s;
+            const RowRange rr = row_range(probs, nprob, g);
+            const int64_t na = rr.a1 - rr.a0;
+            if (na > kRowShort) {
+                is_long = true;
+            } else {
+                int64_t s, mx;
+                lane_row_counts(probs[rr.pi], rr.a0, na, s, mx);
+                store_features(feat, ub_out, g, na, s, mx);
+            }
         }
+        append_rows(is_long, g, long_rows, ctr);
+    }
+}
+
+__global__ void k_row_features_long(const Prob* __restrict__ probs, int nprob,
+                                    float* __restrict__ feat, int64_t* __restrict__ ub_out,
+                                    const int32_t* __restrict__ long_rows, const Counters* ctr) {
+    const int n = ctr->claim[kClLongRows];
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int r = blockIdx.x * (blockDim.x >> 5) + warp_id(); r < n; r += nw) {
+        const int64_t g = long_rows[r];
+        const RowRange rr = row_range(probs, nprob, g);
+        int64_t s, mx;
+        warp_row_long(probs[rr.pi], rr.a0, rr.a1, s, mx);
+        if (lane_id() == 0) store_features(feat, ub_out, g, rr.a1 - rr.a0, s, mx);
     }
 }
 
@@ -241,12 +271,17 @@ size_t mlp_train_ws_bytes(int64_t B) {
 }
 
 cudaError_t launch_row_features(const Prob* probs, int nprob, int64_t R, float* feat,
-                                int64_t* ub, const DevInfo& dev, cudaStream_t st) {
+                                int64_t* ub, int32_t* long_rows, Counters* ctr,
+                                const DevInfo& dev, cudaStream_t st) {
     if (R <= 0) return cudaSuccess;
     int64_t blocks = (R + 255) / 256;    // 8 warps x 32 rows
     if (blocks > (int64_t)dev.sms * 16) blocks = (int64_t)dev.sms * 16;
-    k_row_features<<<(unsigned)blocks, 256, 0, st>>>(probs, nprob, R, feat, ub);
-    count_launch(dev);
+    cudaError_t e = cudaMemsetAsync(&ctr->claim[kClLongRows], 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+    k_row_features<<<(unsigned)blocks, 256, 0, st>>>(probs, nprob, R, feat, ub, long_rows, ctr);
+    k_row_features_long<<<(unsigned)(dev.sms * 8), 256, 0, st>>>(probs, nprob, feat, ub,
+                                                                  long_rows, ctr);
+    count_launch(dev, 2);
     return cudaGetLastError();
 }
 

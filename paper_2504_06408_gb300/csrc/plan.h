@@ -214,8 +214,10 @@ struct LearnedWs {
 
 int mlp_param_count();
 size_t mlp_train_ws_bytes(int64_t B);
+// long_rows: R int32 scratch; ctr: its length counter (claim slot 13)
 cudaError_t launch_row_features(const Prob* probs, int nprob, int64_t R, float* feat,
-                                int64_t* ub, const DevInfo& dev, cudaStream_t st);
+                                int64_t* ub, int32_t* long_rows, Counters* ctr,
+                                const DevInfo& dev, cudaStream_t st);
 // rows with ub[r] <= min_ub are skipped when ub is given
 cudaError_t launch_mlp_forward(const float* feat, int64_t R, const void* params, float* z,
                                const int64_t* ub, int64_t min_ub, const DevInfo& dev,

@@ -178,6 +178,7 @@ SPG_DEV void chunk_products(const DCsr& A, const DCsr& B, int64_t p0, int64_t p_
 // boundaries cover a window).  Every warp holds its share of the products to
 // within one pass, whatever the mix of long hub segments and short ones.
 constexpr int kBatch = 512;
+constexpr int kWalkWin = 4;     // windows of 32 products in flight per warp
 constexpr int kCountShift = 50;   // scan packs (entry count << 50) + product count
 
 template <class In, int NT = kBatch>
@@ -241,13 +242,13 @@ SPG_DEV void cta_walk_segments(const DCsr& B, int64_t beg, int64_t len, In a,
         int64_t eend = bs.off[e + 1];
         In ea = In();
         if constexpr (kVal) ea = bs.a[e];
-        for (int64_t t0 = lo_w; t0 < hi_w; t0 += 128) {   // warp-uniform
-            int64_t qv[4];
-            In av[4];
-            bool vv[4];
-            if (eend >= t0 + 128 || eend >= hi_w) {       // the pass lies in segment e
+        for (int64_t t0 = lo_w; t0 < hi_w; t0 += 32 * kWalkWin) {   // warp-uniform
+            int64_t qv[kWalkWin];
+            In av[kWalkWin];
+            bool vv[kWalkWin];
+            if (eend >= t0 + 32 * kWalkWin || eend >= hi_w) {       // the pass lies in segment e
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < kWalkWin; ++u) {
                     const int64_t t = t0 + 32 * u + lane;
                     vv[u] = t < hi_w;
                     qv[u] = ebase + t;
@@ -255,7 +256,7 @@ SPG_DEV void cta_walk_segments(const DCsr& B, int64_t beg, int64_t len, In a,
                 }
             } else {
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < kWalkWin; ++u) {
                     const int64_t tu = t0 + 32 * u;
                     const int64_t t = tu + lane;
                     vv[u] = t < hi_w;
@@ -279,7 +280,7 @@ SPG_DEV void cta_walk_segments(const DCsr& B, int64_t beg, int64_t len, In a,
                     if constexpr (kVal) av[u] = bs.a[me];
                     else av[u] = In();
                 }
-                const int64_t tn = t0 + 128;              // segment of the next pass
+                const int64_t tn = t0 + 32 * kWalkWin;              // segment of the next pass
                 if (tn < hi_w) {
                     while (bs.off[e + 1] <= tn) ++e;
                 }
@@ -287,15 +288,15 @@ SPG_DEV void cta_walk_segments(const DCsr& B, int64_t beg, int64_t len, In a,
                 eend = bs.off[e + 1];
                 if constexpr (kVal) ea = bs.a[e];
             }
-            int32_t col[4];
-            In bval[4];
+            int32_t col[kWalkWin];
+            In bval[kWalkWin];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < kWalkWin; ++u) {
                 col[u] = vv[u] ? ld_i32(B.col + qv[u]) : 0;
                 bval[u] = vv[u] ? load_val<In, kVal>(B.val, qv[u]) : In();
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) op.any(col[u], av[u], bval[u], vv[u]);
+            for (int u = 0; u < kWalkWin; ++u) op.any(col[u], av[u], bval[u], vv[u]);
         }
     }
     __syncthreads();
@@ -406,26 +407,26 @@ SPG_DEV void warp_table_walk(const DCsr& B, int64_t b, int64_t e, In a, Op& op) 
     const int64_t total = __shfl_sync(kFull, my_end, 31);
     const int64_t lo_w = total * wid / nwarps, hi_w = total * (wid + 1) / nwarps;
     int kc = 0;   // entry holding product t0 (warp-uniform, advances with t0)
-    for (int64_t t0 = lo_w; t0 < hi_w; t0 += 128) {   // warp-uniform
-        int64_t qv[4];
-        In av[4];
-        bool vv[4];
+    for (int64_t t0 = lo_w; t0 < hi_w; t0 += 32 * kWalkWin) {   // warp-uniform
+        int64_t qv[kWalkWin];
+        In av[kWalkWin];
+        bool vv[kWalkWin];
         while (kc < 31 && __shfl_sync(kFull, my_end, kc) <= t0) ++kc;
         const int64_t endk = __shfl_sync(kFull, my_end, kc);
-        if (t0 + 128 <= endk && t0 + 128 <= hi_w) {
+        if (t0 + 32 * kWalkWin <= endk && t0 + 32 * kWalkWin <= hi_w) {
             // the window lies in one segment (the common case for hub rows of
             // B): addresses without a per-lane search
             const int64_t base = __shfl_sync(kFull, b, kc) - __shfl_sync(kFull, excl, kc);
             const In ak = shfl_val<In, kVal>(a, kc);
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < kWalkWin; ++u) {
                 qv[u] = base + t0 + 32 * u + lane;
                 av[u] = ak;
                 vv[u] = true;
             }
         } else {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < kWalkWin; ++u) {
                 const int64_t t = t0 + 32 * u + lane;
                 vv[u] = t < hi_w;
                 int k = 0;   // entry of product t: number of prefix ends <= t
@@ -438,15 +439,15 @@ SPG_DEV void warp_table_walk(const DCsr& B, int64_t b, int64_t e, In a, Op& op) 
                 av[u] = shfl_val<In, kVal>(a, k);
             }
         }
-        int32_t col[4];
-        In bval[4];
+        int32_t col[kWalkWin];
+        In bval[kWalkWin];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kWalkWin; ++u) {
             col[u] = vv[u] ? ld_i32(B.col + qv[u]) : 0;
             bval[u] = vv[u] ? load_val<In, kVal>(B.val, qv[u]) : In();
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) op.any(col[u], av[u], bval[u], vv[u]);
+        for (int u = 0; u < kWalkWin; ++u) op.any(col[u], av[u], bval[u], vv[u]);
     }
 }
 
@@ -650,80 +651,82 @@ SPG_DEV void tiny_batch(const Prob* __restrict__ probs, int nprob, const int32_t
     }
 }
 
-// ---- per-row product counts, 32 rows per warp ---------------------------------
+// ---- per-row product counts: short rows by their lane, long rows by a warp -----
 //
-// Each lane brings one row g (active = false: none): rows with at most
-// kRowShort entries are summed by their lane (independent loads, unrolled);
-// longer rows are then walked by the whole warp one after another.  Gives
-// ub = sum nnz(B_k), the largest nnz(B_k) and nnz(A_i) of the lane's row
-// (zeros without one).  Callers give a warp rows far apart (row_of_lane), so
-// that the long rows of a graph's hub region spread over many warps.
+// Pass 1 gives a warp 32 consecutive rows, one per lane (coalesced row
+// pointers): rows with at most kRowShort entries are summed by their lane with
+// independent, unrolled gathers; longer rows are appended to a list.  Pass 2
+// gives every listed row a whole warp (4 gathers in flight per lane), so the
+// hub rows of a graph spread over all warps.  Both give ub = sum nnz(B_k),
+// the largest nnz(B_k) and nnz(A_i).
 constexpr int kRowShort = 8;
+constexpr int kClLongRows = 13;   // Counters::claim slot of the long-row list length
 
-// the row of lane l in round `it` of warp w among nw warps: consecutive rows
-// go to consecutive warps
-SPG_DEV int64_t row_of_lane(int64_t it, int64_t w, int64_t nw) {
-    return (it * 32 + lane_id()) * nw + w;
+struct RowRange {
+    int pi;
+    int64_t a0, a1;
+};
+
+SPG_DEV RowRange row_range(const Prob* __restrict__ probs, int nprob, int64_t g) {
+    RowRange r;
+    r.pi = nprob > 1 ? find_prob(probs, nprob, g) : 0;
+    const Prob& P = probs[r.pi];
+    const int64_t i = g - P.row_base;
+    r.a0 = ld_i64(P.A.rp + i);
+    r.a1 = ld_i64(P.A.rp + i + 1);
+    return r;
 }
 
-SPG_DEV void warp_row_counts(const Prob* __restrict__ probs, int nprob, int64_t g, bool active,
-                             int64_t& ub, int64_t& mx, int64_t& na) {
-    const int lane = lane_id();
-    const bool v = active;
-    const int pi = (v && nprob > 1) ? find_prob(probs, nprob, g) : 0;
-    const Prob& P = probs[pi];
-    int64_t a0 = 0, a1 = 0;
-    if (v) {
-        const int64_t i = g - P.row_base;
-        a0 = ld_i64(P.A.rp + i);
-        a1 = ld_i64(P.A.rp + i + 1);
-    }
-    na = a1 - a0;
+// sum and max of nnz(B_k) over the <= kRowShort entries of a row (one lane)
+SPG_DEV void lane_row_counts(const Prob& P, int64_t a0, int64_t na, int64_t& ub, int64_t& mx) {
     ub = 0;
     mx = 0;
-    if (na <= kRowShort) {
 #pragma unroll
-        for (int t = 0; t < kRowShort; ++t) {
-            if (t < na) {
-                const int32_t k = ld_i32(P.A.col + a0 + t);
-                const int64_t l = ld_i64(P.B.rp + k + 1) - ld_i64(P.B.rp + k);
-                ub += l;
-                mx = l > mx ? l : mx;
-            }
+    for (int t = 0; t < kRowShort; ++t) {
+        if (t < na) {
+            const int32_t k = ld_i32(P.A.col + a0 + t);
+            const int64_t l = ld_i64(P.B.rp + k + 1) - ld_i64(P.B.rp + k);
+            ub += l;
+            mx = l > mx ? l : mx;
         }
     }
-    unsigned longm = __ballot_sync(kFull, na > kRowShort);
-    while (longm) {
-        const int src = __ffs(longm) - 1;
-        longm &= longm - 1;
-        const Prob& Q = probs[__shfl_sync(kFull, pi, src)];
-        const int64_t b0 = __shfl_sync(kFull, a0, src), b1 = __shfl_sync(kFull, a1, src);
-        int64_t s = 0, m = 0;
-        int64_t q = b0 + lane;
-        for (; q + 96 < b1; q += 128) {   // 4 independent gathers in flight per lane
-            int32_t k[4];
+}
+
+// appends the calling lanes' rows (flag set) to list[ctr->claim[kClLongRows]...]
+SPG_DEV void append_rows(bool flag, int64_t g, int32_t* list, Counters* ctr) {
+    const unsigned m = __ballot_sync(kFull, flag);
+    if (!m) return;
+    const int leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane_id() == leader) base = atomicAdd(&ctr->claim[kClLongRows], __popc(m));
+    base = __shfl_sync(kFull, base, leader);
+    if (flag) list[base + __popc(m & ((1u << lane_id()) - 1))] = (int32_t)g;
+}
+
+// sum and max of nnz(B_k) over the entries [a0, a1) of one row, whole warp
+SPG_DEV void warp_row_long(const Prob& P, int64_t a0, int64_t a1, int64_t& ub, int64_t& mx) {
+    const int lane = lane_id();
+    int64_t s = 0, m = 0;
+    int64_t q = a0 + lane;
+    for (; q + 96 < a1; q += 128) {   // 4 independent gathers in flight per lane
+        int32_t k[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) k[u] = ld_i32(Q.A.col + q + 32 * u);
+        for (int u = 0; u < 4; ++u) k[u] = ld_i32(P.A.col + q + 32 * u);
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int64_t l = ld_i64(Q.B.rp + k[u] + 1) - ld_i64(Q.B.rp + k[u]);
-                s += l;
-                m = l > m ? l : m;
-            }
-        }
-        for (; q < b1; q += 32) {
-            const int32_t k = ld_i32(Q.A.col + q);
-            const int64_t l = ld_i64(Q.B.rp + k + 1) - ld_i64(Q.B.rp + k);
+        for (int u = 0; u < 4; ++u) {
+            const int64_t l = ld_i64(P.B.rp + k[u] + 1) - ld_i64(P.B.rp + k[u]);
             s += l;
             m = l > m ? l : m;
         }
-        s = warp_sum(s);
-        m = warp_max(m);
-        if (lane == src) {
-            ub = s;
-            mx = m;
-        }
     }
+    for (; q < a1; q += 32) {
+        const int32_t k = ld_i32(P.A.col + q);
+        const int64_t l = ld_i64(P.B.rp + k + 1) - ld_i64(P.B.rp + k);
+        s += l;
+        m = l > m ? l : m;
+    }
+    ub = warp_sum(s);
+    mx = warp_max(m);
 }
 
 // ---- shared-memory hash tables (linear probing, power-of-two size) ----------

@@ -40,41 +40,83 @@ __global__ void k_write_probs(ProbTable tab, int nprob, Prob* dst) {
     if (i < nprob) dst[i] = tab.p[i];
 }
 
-// ub_i, the empty rows' counts, the symbolic bin histogram and P = sum ub.
+// ub_i, the empty rows' counts, the symbolic bin histogram and P = sum ub:
+// pass 1, 32 consecutive rows per warp; rows with more than kRowShort entries
+// go to the long list (skipped rows keep the ub they have).
+SPG_DEV void analyze_add(int* s_hist, unsigned long long& prod, int64_t g, int64_t s, bool skipped,
+                         const Tuning& t, int64_t* ub, int64_t* cnt) {
+    if (skipped) {
+        s = ub[g];
+    } else {
+        ub[g] = s;
+        if (s == 0) cnt[g] = 0;
+    }
+    atomicAdd(&s_hist[bin_key(skipped ? kTierEmpty : sym_tier(s, t), s)], 1);
+    prod += (unsigned long long)s;
+}
+
+SPG_DEV void analyze_flush(int* s_hist, unsigned long long prod, Counters* ctr) {
+    prod = warp_sum(prod);
+    if (lane_id() == 0 && prod) atomicAdd(&ctr->products, prod);
+    __syncthreads();
+    for (int b = threadIdx.x; b < kNumBins; b += blockDim.x)
+        if (s_hist[b]) atomicAdd(&ctr->sym_bin_count[b], s_hist[b]);
+}
+
 __global__ void __launch_bounds__(256) k_analyze(const Prob* __restrict__ probs, int nprob,
                                                  int64_t R, Tuning t, int64_t* __restrict__ ub,
                                                  int64_t* __restrict__ cnt, Counters* ctr,
-                                                 const uint8_t* __restrict__ skip) {
+                                                 const uint8_t* __restrict__ skip,
+                                                 int32_t* long_rows) {
     __shared__ int s_hist[kNumBins];
     for (int b = threadIdx.x; b < kNumBins; b += blockDim.x) s_hist[b] = 0;
     __syncthreads();
     const int lane = lane_id();
     unsigned long long prod = 0;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id();
-    // 32 rows per warp, one per lane (long rows walked by the warp); skipped
-    // rows keep the ub they have and are not walked
-    for (int64_t it = 0; it * 32 * nw < R; ++it) {
-        const int64_t g = row_of_lane(it, w, nw);
-        const bool skipped = skip && g < R && skip[g];
-        int64_t s, mx, na;
-        warp_row_counts(probs, nprob, g, g < R && !skipped, s, mx, na);
-        if (g < R) {
-            if (skipped) {
-                s = ub[g];
+    for (int64_t g0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id()) * 32; g0 < R;
+         g0 += nw * 32) {
+        const int64_t g = g0 + lane;
+        const bool in = g < R;
+        const bool skipped = in && skip && skip[g];
+        bool is_long = false;
+        if (in && !skipped) {
+            const RowRange rr = row_range(probs, nprob, g);
+            const int64_t na = rr.a1 - rr.a0;
+            if (na > kRowShort) {
+                is_long = true;
             } else {
-                ub[g] = s;
-                if (s == 0) cnt[g] = 0;
+                int64_t s, mx;
+                lane_row_counts(probs[rr.pi], rr.a0, na, s, mx);
+                analyze_add(s_hist, prod, g, s, false, t, ub, cnt);
             }
-            atomicAdd(&s_hist[bin_key(skipped ? kTierEmpty : sym_tier(s, t), s)], 1);
-            prod += (unsigned long long)s;
+        } else if (skipped) {
+            analyze_add(s_hist, prod, g, 0, true, t, ub, cnt);
         }
+        append_rows(is_long, g, long_rows, ctr);
     }
-    prod = warp_sum(prod);
-    if (lane == 0 && prod) atomicAdd(&ctr->products, prod);
+    analyze_flush(s_hist, prod, ctr);
+}
+
+// pass 2: a warp per long row
+__global__ void __launch_bounds__(256) k_analyze_long(const Prob* __restrict__ probs, int nprob,
+                                                      Tuning t, int64_t* __restrict__ ub,
+                                                      int64_t* __restrict__ cnt, Counters* ctr,
+                                                      const int32_t* __restrict__ long_rows) {
+    __shared__ int s_hist[kNumBins];
+    for (int b = threadIdx.x; b < kNumBins; b += blockDim.x) s_hist[b] = 0;
     __syncthreads();
-    for (int b = threadIdx.x; b < kNumBins; b += blockDim.x)
-        if (s_hist[b]) atomicAdd(&ctr->sym_bin_count[b], s_hist[b]);
+    unsigned long long prod = 0;
+    const int n = ctr->claim[kClLongRows];
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int r = blockIdx.x * (blockDim.x >> 5) + warp_id(); r < n; r += nw) {
+        const int64_t g = long_rows[r];
+        const RowRange rr = row_range(probs, nprob, g);
+        int64_t s, mx;
+        warp_row_long(probs[rr.pi], rr.a0, rr.a1, s, mx);
+        if (lane_id() == 0) analyze_add(s_hist, prod, g, s, false, t, ub, cnt);
+    }
+    analyze_flush(s_hist, prod, ctr);
 }
 
 // exclusive scan of the kNumBins bin counts (tiny: one thread)
@@ -441,9 +483,12 @@ cudaError_t launch_analyze(const WsPtrs& w, int nprob, int64_t R, const Tuning& 
     if (R > 0) {
         int64_t blocks = (R + 255) / 256;    // 8 warps x 32 rows
         if (blocks > (int64_t)dev.sms * 16) blocks = (int64_t)dev.sms * 16;
+        cudaMemsetAsync(&w.ctr->claim[kClLongRows], 0, sizeof(int32_t), st);
         k_analyze<<<(unsigned)blocks, 256, 0, st>>>(w.probs, nprob, R, t, w.ub, w.cnt, w.ctr,
-                                                    w.skip);
-        count_launch(dev);
+                                                    w.skip, w.rows_num);
+        k_analyze_long<<<(unsigned)(dev.sms * 8), 256, 0, st>>>(w.probs, nprob, t, w.ub, w.cnt,
+                                                                 w.ctr, w.rows_num);
+        count_launch(dev, 2);
     }
     k_bin_offsets<<<1, 32, 0, st>>>(w.ctr->sym_bin_count, w.ctr->sym_bin_off,
                                     w.ctr->sym_bin_cursor);
