@@ -92,7 +92,10 @@ typedef struct {
     int64_t sym_slab_cols;      /* symbolic dense tier: columns per bitmap slab         */
     int64_t bitmap_cache_bytes; /* workspace bytes that keep the symbolic phase's row
                                    bitmaps for the numeric dense tier (< 0: none)      */
-    int64_t reserved[3];
+    int64_t host_panel_bytes;   /* host API: outputs larger than this are produced in
+                                   row panels of about this size, each panel's download
+                                   overlapping the next panel's kernels (0: 1 GiB)     */
+    int64_t reserved[2];
 } spg_tuning;
 
 /* Counters of the last analysis on a handle (host copy, filled by spgemm_symbolic). */
@@ -265,7 +268,10 @@ spg_status spgemm_host_symbolic(spg_handle* handle, spg_semiring sr, const spg_c
 
 /*
  * Numeric phase of the inputs of the last spgemm_host_symbolic call on this
- * handle (same semiring); copies C.col and C.val to HOST memory.
+ * handle (same semiring); copies C.col and C.val to HOST memory.  Outputs
+ * larger than spg_tuning.host_panel_bytes are computed in row panels (a
+ * symbolic + numeric call per panel into one of two device buffers) and each
+ * panel is downloaded on a second stream while the next one is computed.
  *   c_col : HOST int32 [nnz(C)];  c_val : HOST [nnz(C)] of the output type.
  * Synchronous; returns kernel-detected errors (as spgemm_check).
  */
@@ -294,7 +300,7 @@ spg_status spgemm_transpose(spg_handle* handle, const spg_csr* A, int value_byte
  * arguments and output) with their scratch in a 32 MiB device array that
  * the library holds on every GPU that loads it, until the process exits.
  *   - No handle; no cudaMalloc / cudaFree or allocating library call.
- *   - Limit: 4 * A.ncols + 8 * A.nnz (plus ~8 bytes per 2048 columns and
+ *   - Limit: 8 * A.ncols + 8 * A.nnz (plus ~8 bytes per 2048 columns and
  *     alignment) must fit in 32 MiB; larger inputs return SPG_ERR_UNSUPPORTED
  *     before any GPU work.
  *   - The first call on a device looks the array's address up (once per

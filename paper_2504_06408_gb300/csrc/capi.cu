@@ -1,10 +1,12 @@
 // C ABI of the SpGEMM library: argument checks, workspace layout, the order
 // of the phases, and the host side of errors.  Every arithmetic step runs in
 // the kernels of symbolic.cu / numeric.cu.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "../../include/spgemm.h"
 #include "plan.h"
@@ -36,6 +38,11 @@ struct spg_handle {
     spg_csr hA{}, hB{};            // device descriptors of the last host-API inputs
     int host_sr = -1;
     int64_t host_nnz = -1;
+    std::vector<int64_t> host_arp, host_crp;   // host copies of A's and C's row pointers
+    cudaStream_t cstream = nullptr;            // download stream of the panel pipeline
+    cudaEvent_t ev_done[2] = {}, ev_copied[2] = {};
+    bool pipe_events = false;
+    DevBuf p_rp[2], p_col[2], p_val[2];        // double-buffered panel outputs
     // learned path: values fixed by the last spgemm_learned_plan
     int lrn_sr = -1;
     int64_t lrn_entries = -1, lrn_warp_max = 0, lrn_block_max = 0, lrn_rows = -1;
@@ -269,8 +276,15 @@ spg_status spgemm_destroy(spg_handle* h) {
     if (h->timer_events)
         for (int i = 0; i < StageTimer::kMax; ++i) cudaEventDestroy(h->timer.ev[i]);
     for (DevBuf* b : {&h->a_rp, &h->a_col, &h->a_val, &h->b_rp, &h->b_col, &h->b_val, &h->ws,
-                      &h->c_rp, &h->c_col, &h->c_val})
+                      &h->c_rp, &h->c_col, &h->c_val, &h->p_rp[0], &h->p_rp[1], &h->p_col[0],
+                      &h->p_col[1], &h->p_val[0], &h->p_val[1]})
         if (b->p) cudaFree(b->p);
+    if (h->pipe_events)
+        for (int i = 0; i < 2; ++i) {
+            cudaEventDestroy(h->ev_done[i]);
+            cudaEventDestroy(h->ev_copied[i]);
+        }
+    if (h->cstream) cudaStreamDestroy(h->cstream);
     if (h->hstream) cudaStreamDestroy(h->hstream);
     delete h;
     return SPG_OK;
@@ -401,9 +415,12 @@ static int64_t max_ncols(int nprob, const spg_csr* B) {
     return m;
 }
 
-static spg_status symbolic_impl(spg_handle* h, int sr, int nprob, const spg_csr* A,
-                                const spg_csr* B, int64_t* const* c_row_ptr, int64_t* c_nnz,
-                                void* workspace, size_t workspace_bytes, cudaStream_t st) {
+// Launches of the symbolic phase, no host synchronisation.  reset_status =
+// false keeps the error flags of earlier calls in the same workspace.
+static spg_status symbolic_launch(spg_handle* h, int sr, int nprob, const spg_csr* A,
+                                  const spg_csr* B, int64_t* const* c_row_ptr, void* workspace,
+                                  size_t workspace_bytes, cudaStream_t st, bool reset_status,
+                                  WsLayout* Lout, WsPtrs* wout) {
     const Tuning t = effective_tuning(h, sr);
     const WsLayout L = layout_batch(nprob, A, B, t);
     if (!workspace || workspace_bytes < L.total)
@@ -411,7 +428,8 @@ static spg_status symbolic_impl(spg_handle* h, int sr, int nprob, const spg_csr*
     const WsPtrs w = ws_ptrs(workspace, L);
     h->launches = 0;
     h->timer.n = 0;
-    cudaError_t e = cudaMemsetAsync(workspace, 0, L.probs, st);   // status + counters
+    cudaError_t e = reset_status ? cudaMemsetAsync(workspace, 0, L.probs, st)   // status + counters
+                                 : cudaMemsetAsync(w.ctr, 0, sizeof(Counters), st);
     if (e == cudaSuccess && w.row_slot)
         e = cudaMemsetAsync(w.row_slot, 0xff, sizeof(int32_t) * (size_t)L.R, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "memset");
@@ -423,10 +441,23 @@ static spg_status symbolic_impl(spg_handle* h, int sr, int nprob, const spg_csr*
     if (e == cudaSuccess) e = launch_symbolic(w, nprob, L.R, t, max_ncols(nprob, B), h->dev, st);
     if (e == cudaSuccess) e = launch_scan_rowptr(w, nprob, L.R, h->dev, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "symbolic launch");
+    if (Lout) *Lout = L;
+    if (wout) *wout = w;
+    return SPG_OK;
+}
+
+static spg_status symbolic_impl(spg_handle* h, int sr, int nprob, const spg_csr* A,
+                                const spg_csr* B, int64_t* const* c_row_ptr, int64_t* c_nnz,
+                                void* workspace, size_t workspace_bytes, cudaStream_t st) {
+    WsLayout L;
+    WsPtrs w;
+    spg_status s = symbolic_launch(h, sr, nprob, A, B, c_row_ptr, workspace, workspace_bytes, st,
+                                   true, &L, &w);
+    if (s != SPG_OK) return s;
     // bring back nnz, products, bin counts and the status in one copy
     Counters* hc = (Counters*)((char*)h->pinned);
     static_assert(sizeof(Counters) <= kPinnedBytes, "staging buffer too small");
-    e = cudaMemcpyAsync(hc, w.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaMemcpyAsync(hc, w.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(h, e, "symbolic");
     int64_t tot = 0;
@@ -793,7 +824,107 @@ spg_status spgemm_host_symbolic(spg_handle* h, spg_semiring sr, const spg_csr* A
     if (e != cudaSuccess) return cuda_fail(h, e, "row_ptr download");
     h->host_sr = sr;
     h->host_nnz = *c_nnz;
+    h->host_arp.assign(A->row_ptr, A->row_ptr + A->nrows + 1);
+    h->host_crp.assign(c_row_ptr, c_row_ptr + A->nrows + 1);
     return SPG_OK;
+}
+
+// Default panel size of the host API's pipelined download (spg_tuning.host_panel_bytes).
+static constexpr size_t kPipePanelBytes = (size_t)1 << 30;
+
+static size_t host_panel_bytes(const spg_handle* h) {
+    return h->user.host_panel_bytes > 0 ? (size_t)h->user.host_panel_bytes : kPipePanelBytes;
+}
+
+// Row panels [cuts[k], cuts[k+1]) of about equal output size.
+static std::vector<int64_t> panel_cuts(const std::vector<int64_t>& crp, int npanels) {
+    const int64_t R = (int64_t)crp.size() - 1, nnz = crp[R];
+    std::vector<int64_t> cuts{0};
+    for (int k = 1; k < npanels; ++k) {
+        const int64_t target = nnz * k / npanels;
+        int64_t r = std::lower_bound(crp.begin(), crp.end(), target) - crp.begin();
+        if (r <= cuts.back()) r = cuts.back() + 1;
+        if (r >= R) break;
+        cuts.push_back(r);
+    }
+    cuts.push_back(R);
+    return cuts;
+}
+
+// spgemm_host_numeric for large outputs: for each row panel of A, symbolic +
+// numeric into one of two device buffers on the compute stream, then the
+// panel's download on the copy stream while the next panel computes.
+static spg_status host_numeric_pipelined(spg_handle* h, int sr, int32_t* c_col, void* c_val) {
+    const int ob = out_bytes(sr);
+    const int64_t nnz = h->host_nnz, R = h->hA.nrows;
+    const size_t out_bytes_total = (size_t)nnz * (size_t)(4 + ob);
+    const size_t panel = host_panel_bytes(h);
+    int64_t npl = (int64_t)((out_bytes_total + panel - 1) / panel);
+    int np = (int)std::max<int64_t>(2, std::min<int64_t>(npl, 64));
+    const std::vector<int64_t> cuts = panel_cuts(h->host_crp, np);
+    np = (int)cuts.size() - 1;
+    int64_t max_rows = 0, max_nnz = 0;
+    for (int k = 0; k < np; ++k) {
+        max_rows = std::max(max_rows, cuts[k + 1] - cuts[k]);
+        max_nnz = std::max(max_nnz, h->host_crp[cuts[k + 1]] - h->host_crp[cuts[k]]);
+    }
+    cudaError_t e = cudaSuccess;
+    if (!h->cstream) e = cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !h->pipe_events) {
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+            e = cudaEventCreateWithFlags(&h->ev_done[i], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_copied[i], cudaEventDisableTiming);
+        }
+        if (e == cudaSuccess) h->pipe_events = true;
+    }
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+        e = ensure(h->p_rp[b], sizeof(int64_t) * (size_t)(max_rows + 1));
+        if (e == cudaSuccess) e = ensure(h->p_col[b], sizeof(int32_t) * (size_t)max_nnz);
+        if (e == cudaSuccess && ob) e = ensure(h->p_val[b], (size_t)ob * (size_t)max_nnz);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "panel buffers");
+    cudaStream_t st = h->hstream, cs = h->cstream;
+    // no host synchronisation inside the loop: the panels' sizes are known from
+    // the symbolic call on the whole of A, and a device-to-host copy on the
+    // compute stream would queue behind the panel downloads; error flags
+    // accumulate in the workspace and are read once at the end
+    WsPtrs w{};
+    for (int k = 0; k < np; ++k) {
+        const int b = k & 1;
+        const int64_t r0 = cuts[k], r1 = cuts[k + 1];
+        if (k >= 2) {
+            e = cudaStreamWaitEvent(st, h->ev_copied[b], 0);
+            if (e != cudaSuccess) return cuda_fail(h, e, "panel wait");
+        }
+        spg_csr Ap = h->hA;
+        Ap.nrows = r1 - r0;
+        Ap.row_ptr = h->hA.row_ptr + r0;
+        Ap.nnz = h->host_arp[r1] - h->host_arp[r0];
+        int64_t* prp = (int64_t*)h->p_rp[b].p;
+        spg_status s = symbolic_launch(h, sr, 1, &Ap, &h->hB, &prp, h->ws.p, h->ws.bytes, st,
+                                       k == 0, nullptr, &w);
+        if (s != SPG_OK) return s;
+        int32_t* pcol = (int32_t*)h->p_col[b].p;
+        void* pval = ob ? h->p_val[b].p : nullptr;
+        const int64_t* cprp = prp;
+        s = numeric_impl(h, sr, 1, &Ap, &h->hB, &cprp, &pcol, &pval, h->ws.p, h->ws.bytes, st);
+        if (s != SPG_OK) return s;
+        e = cudaEventRecord(h->ev_done[b], st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, h->ev_done[b], 0);
+        const int64_t at = h->host_crp[r0], pn = h->host_crp[r1] - at;
+        if (e == cudaSuccess && pn > 0)
+            e = cudaMemcpyAsync(c_col + at, pcol, sizeof(int32_t) * (size_t)pn,
+                                cudaMemcpyDeviceToHost, cs);
+        if (e == cudaSuccess && ob && pn > 0)
+            e = cudaMemcpyAsync((char*)c_val + (size_t)at * ob, pval, (size_t)ob * (size_t)pn,
+                                cudaMemcpyDeviceToHost, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_copied[b], cs);
+        if (e != cudaSuccess) return cuda_fail(h, e, "panel download");
+    }
+    e = cudaStreamSynchronize(cs);
+    if (e != cudaSuccess) return cuda_fail(h, e, "panel download");
+    (void)R;
+    return read_status(h, w, st);   // every panel's kernel-detected errors
 }
 
 spg_status spgemm_host_numeric(spg_handle* h, spg_semiring sr, int32_t* c_col, void* c_val) {
@@ -804,6 +935,9 @@ spg_status spgemm_host_numeric(spg_handle* h, spg_semiring sr, int32_t* c_col, v
     const int ob = out_bytes(sr);
     if (nnz > 0 && (!c_col || (ob && !c_val)))
         return fail(h, SPG_ERR_INVALID_ARG, "c_col / c_val is NULL");
+    if ((size_t)nnz * (size_t)(4 + ob) > host_panel_bytes(h) &&
+        (int64_t)h->host_crp.size() == h->hA.nrows + 1 && h->hA.nrows >= 2)
+        return host_numeric_pipelined(h, sr, c_col, c_val);
     cudaStream_t st = h->hstream;
     cudaError_t e = ensure(h->c_col, sizeof(int32_t) * (size_t)nnz);
     if (e == cudaSuccess && ob) e = ensure(h->c_val, (size_t)ob * (size_t)nnz);

@@ -234,11 +234,12 @@ __global__ void __launch_bounds__(kWarpTierWarps * 32)
 __global__ void __launch_bounds__(kBlockThreads)
     k_sym_block(const Prob* __restrict__ probs, int nprob, const int32_t* __restrict__ rows,
                 Counters* ctr, const int64_t* __restrict__ ub, int64_t* __restrict__ cnt,
-                DevStatus* st, int table_slots) {
+                DevStatus* st, int table_slots, int64_t dense_min, uint32_t* bm_cache,
+                int32_t* row_slot, int64_t cache_words, int64_t cache_slots) {
     extern __shared__ int32_t smem_i32[];
     int32_t* tab = smem_i32;
     __shared__ BatchSmem<char> bs;
-    __shared__ int s_row, s_cnt;
+    __shared__ int s_row, s_cnt, s_slot;
     const int lane = lane_id();
     const int beg = ctr->sym_bin_off[kTierBlock * kSubBins];
     const int end = ctr->sym_bin_off[(kTierBlock + 1) * kSubBins];
@@ -272,6 +273,29 @@ __global__ void __launch_bounds__(kBlockThreads)
         if (lane == 0 && tot) atomicAdd(&s_cnt, tot);
         __syncthreads();
         if (threadIdx.x == 0) cnt[g] = s_cnt;
+        // a row the numeric phase will take in its dense tier: keep the row's
+        // bitmap (from the table's keys) so that the numeric phase does not
+        // rebuild it from the products
+        const int64_t words = (P.B.ncols + 31) >> 5;
+        if (bm_cache && s_cnt > dense_min && words <= cache_words) {
+            if (threadIdx.x == 0) {
+                const int sl = atomicAdd(&ctr->bm_next, 1);
+                s_slot = sl < cache_slots ? sl : -1;
+                row_slot[g] = s_slot;
+            }
+            __syncthreads();
+            if (s_slot >= 0) {
+                uint32_t* dst = bm_cache + (int64_t)s_slot * cache_words;
+                uint4* d4 = reinterpret_cast<uint4*>(dst);
+                for (int64_t w = threadIdx.x; w < (words + 3) / 4; w += blockDim.x)
+                    d4[w] = make_uint4(0u, 0u, 0u, 0u);
+                __syncthreads();
+                for (int s = threadIdx.x; s < T; s += blockDim.x) {
+                    const int32_t k = tab[s];
+                    if (k != kEmptyKey) atomicOr(dst + (k >> 5), 1u << (k & 31));
+                }
+            }
+        }
         __syncthreads();
     }
 }
@@ -544,7 +568,9 @@ cudaError_t launch_symbolic(const WsPtrs& w, int nprob, int64_t R, const Tuning&
         if (e != cudaSuccess) return e;
         const int grid = occupancy((const void*)k_sym_block, kBlockThreads, smem, dev);
         k_sym_block<<<grid, kBlockThreads, smem, st>>>(w.probs, nprob, w.rows_sym, w.ctr, w.ub,
-                                                       w.cnt, w.status, (int)T);
+                                                       w.cnt, w.status, (int)T, t.num_block_max_nnz,
+                                                       w.bm_cache, w.row_slot, w.bm_cache_words,
+                                                       w.bm_cache_slots);
         count_launch(dev);
         mark_stage(dev, kStSymBlock, st);
     }

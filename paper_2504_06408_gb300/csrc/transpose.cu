@@ -36,26 +36,53 @@ __global__ void k_t_scatter(DCsr A, int64_t nnz, const int64_t* t_rp, int32_t* c
     }
 }
 
-// warp per segment of length <= 32
-__global__ void k_t_sort_warp(int64_t ncols, const int64_t* t_rp, int32_t* t_col) {
+// 32 columns per warp (coalesced lengths): segments of 2..32 entries are sorted
+// by the warp in registers, one after another; longer ones are listed for the
+// CTA sort (most of a wide A^T's columns are empty or single).
+__global__ void k_t_sort_warp(int64_t ncols, const int64_t* t_rp, int32_t* t_col,
+                              int32_t* long_list, int32_t* n_long) {
     const int lane = lane_id();
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); j < ncols; j += nw) {
-        const int64_t a = t_rp[j], len = t_rp[j + 1] - a;
-        if (len <= 1 || len > 32) continue;
-        int32_t v = lane < len ? t_col[a + lane] : INT32_MAX;
-        v = warp_bitonic_sort32(v);
-        if (lane < len) t_col[a + lane] = v;
+    for (int64_t j0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id()) * 32; j0 < ncols;
+         j0 += nw * 32) {
+        const int64_t j = j0 + lane;
+        int64_t a = 0, len = 0;
+        if (j < ncols) {
+            a = t_rp[j];
+            len = t_rp[j + 1] - a;
+        }
+        const unsigned lg = __ballot_sync(kFull, len > 32);
+        if (lg) {
+            const int leader = __ffs(lg) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(n_long, __popc(lg));
+            base = __shfl_sync(kFull, base, leader);
+            if (len > 32) long_list[base + __popc(lg & ((1u << lane) - 1))] = (int32_t)j;
+        }
+        unsigned sm = __ballot_sync(kFull, len > 1 && len <= 32);
+        while (sm) {
+            const int src = __ffs(sm) - 1;
+            sm &= sm - 1;
+            const int64_t sa = __shfl_sync(kFull, a, src);
+            const int sl = (int)__shfl_sync(kFull, len, src);
+            int32_t v = lane < sl ? t_col[sa + lane] : INT32_MAX;
+            v = warp_bitonic_sort32(v);
+            if (lane < sl) t_col[sa + lane] = v;
+        }
     }
 }
 
-// CTA per segment of length in (32, kTSmemKeys]; longer ones sort in global scratch
-__global__ void __launch_bounds__(512) k_t_sort_block(int64_t ncols, const int64_t* t_rp,
-                                                      int32_t* t_col, int32_t* scratch) {
+// CTA per listed segment (longer than 32); those longer than kTSmemKeys sort in
+// a global scratch area
+__global__ void __launch_bounds__(512) k_t_sort_block(const int64_t* t_rp, int32_t* t_col,
+                                                      int32_t* scratch,
+                                                      const int32_t* __restrict__ long_list,
+                                                      const int32_t* __restrict__ n_long) {
     extern __shared__ int32_t buf[];   // kTSmemKeys
-    for (int64_t j = blockIdx.x; j < ncols; j += gridDim.x) {
+    const int n = *n_long;
+    for (int r = blockIdx.x; r < n; r += gridDim.x) {
+        const int64_t j = long_list[r];
         const int64_t a = t_rp[j], len = t_rp[j + 1] - a;
-        if (len <= 32) continue;
         int64_t N = 1;
         while (N < len) N <<= 1;
         int32_t* b = N <= kTSmemKeys ? buf : scratch + 2 * a;
@@ -93,7 +120,7 @@ __global__ void k_t_gather(DCsr A, int64_t nnz, int value_bytes, int32_t* t_col,
 size_t transpose_ws_bytes(int64_t ncols, int64_t nnz) {
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     return al(sizeof(int32_t) * (size_t)ncols) + al(sizeof(int64_t) * (size_t)scan_parts_needed(ncols)) +
-           al(sizeof(int32_t) * 2 * (size_t)nnz);
+           al(sizeof(int32_t) * 2 * (size_t)nnz) + al(sizeof(int32_t) * (size_t)(ncols + 1));
 }
 
 cudaError_t launch_transpose(const DCsr& A, int64_t nnz, int value_bytes, int64_t* t_rp,
@@ -105,8 +132,11 @@ cudaError_t launch_transpose(const DCsr& A, int64_t nnz, int value_bytes, int64_
     int32_t* cursor = (int32_t*)b;
     int64_t* part = (int64_t*)(b + al(sizeof(int32_t) * (size_t)n));
     int32_t* scratch = (int32_t*)((char*)part + al(sizeof(int64_t) * (size_t)scan_parts_needed(n)));
+    int32_t* long_list = (int32_t*)((char*)scratch + al(sizeof(int32_t) * 2 * (size_t)nnz));
+    int32_t* n_long = long_list + n;
     cudaError_t e = cudaMemsetAsync(t_rp, 0, sizeof(int64_t) * (size_t)(n + 1), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(cursor, 0, sizeof(int32_t) * (size_t)n, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(n_long, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
     const int grid = dev.sms * 8;
     if (nnz > 0) k_t_count<<<grid, 256, 0, st>>>(A, nnz, t_rp);
@@ -114,11 +144,14 @@ cudaError_t launch_transpose(const DCsr& A, int64_t nnz, int value_bytes, int64_
     if (e != cudaSuccess) return e;
     if (nnz > 0) {
         k_t_scatter<<<grid, 256, 0, st>>>(A, nnz, t_rp, cursor, t_col);
-        k_t_sort_warp<<<grid, 256, 0, st>>>(n, t_rp, t_col);
+        int64_t wblocks = (n + 255) / 256;   // 8 warps x 32 columns
+        if (wblocks > (int64_t)dev.sms * 16) wblocks = (int64_t)dev.sms * 16;
+        k_t_sort_warp<<<(unsigned)wblocks, 256, 0, st>>>(n, t_rp, t_col, long_list, n_long);
         e = cudaFuncSetAttribute(k_t_sort_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kTSmemKeys * 4);
         if (e != cudaSuccess) return e;
-        k_t_sort_block<<<dev.sms * 2, 512, kTSmemKeys * 4, st>>>(n, t_rp, t_col, scratch);
+        k_t_sort_block<<<dev.sms * 2, 512, kTSmemKeys * 4, st>>>(t_rp, t_col, scratch, long_list,
+                                                                  n_long);
         k_t_gather<<<grid, 256, 0, st>>>(A, nnz, value_bytes, t_col, t_val);
     }
     return cudaGetLastError();

@@ -49,7 +49,8 @@ class spg_tuning(ctypes.Structure):
     _fields_ = [("sym_warp_max_ub", ctypes.c_int64), ("sym_block_max_ub", ctypes.c_int64),
                 ("num_warp_max_nnz", ctypes.c_int64), ("num_block_max_nnz", ctypes.c_int64),
                 ("dense_slab_cols", ctypes.c_int64), ("sym_slab_cols", ctypes.c_int64),
-                ("bitmap_cache_bytes", ctypes.c_int64), ("reserved", ctypes.c_int64 * 3)]
+                ("bitmap_cache_bytes", ctypes.c_int64), ("host_panel_bytes", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 2)]
 
 
 class spg_stats(ctypes.Structure):

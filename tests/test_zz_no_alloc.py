@@ -59,7 +59,7 @@ def test_noalloc_transpose_matches_transpose_on_two_calls():
 
 def test_noalloc_transpose_rejects_oversize_before_any_work():
     lib = api.load_library()
-    # 16M columns need 64 MiB of cursors: beyond the 32 MiB scratch
+    # 16M columns need 128 MiB of cursors and lists: beyond the 32 MiB scratch
     rp = torch.zeros(2, dtype=torch.int64, device="cuda")
     big = api.DeviceCSR(1, 1 << 24, rp, torch.zeros(0, dtype=torch.int32, device="cuda"))
     a = big.c()
