@@ -184,7 +184,7 @@ constexpr int kCountShift = 50;   // scan packs (entry count << 50) + product co
 template <class In, int NT = kBatch>
 struct BatchSmem {
     static constexpr int kN = NT;  // entries per batch = threads of the CTA
-    int64_t beg[NT];               // compacted non-empty segments
+    int64_t base[NT];              // compacted non-empty segments: start - flat offset
     int64_t off[NT + 1];           // exclusive scan of their lengths
     In a[NT];
     int64_t wsum[NT / 32];
@@ -218,7 +218,7 @@ SPG_DEV void cta_walk_segments(const DCsr& B, int64_t beg, int64_t len, In a,
     const int64_t ex = bs.wsum[wid] + incl - packed;   // exclusive (count, length)
     if (len > 0) {
         const int c = (int)(ex >> kCountShift);
-        bs.beg[c] = beg;
+        bs.base[c] = beg - (ex & kLenMask);
         bs.off[c] = ex & kLenMask;
         if constexpr (kVal) bs.a[c] = a;
     }
@@ -238,7 +238,7 @@ SPG_DEV void cta_walk_segments(const DCsr& B, int64_t beg, int64_t len, In a,
             }
             e = lo;
         }
-        int64_t ebase = bs.beg[e] - bs.off[e];   // q = ebase + t inside segment e
+        int64_t ebase = bs.base[e];   // q = ebase + t inside segment e
         int64_t eend = bs.off[e + 1];
         In ea = In();
         if constexpr (kVal) ea = bs.a[e];
@@ -266,17 +266,19 @@ SPG_DEV void cta_walk_segments(const DCsr& B, int64_t beg, int64_t len, In a,
                         me = e;
                         if (bs.off[e + 1] < tu + 32 && bs.off[e + 1] < hi_w) {
                             const int ej = e + lane;       // lane j: end of segment e + j
-                            const int64_t bnd = ej < nseg ? bs.off[ej + 1] : INT64_MAX;
+                            // ends relative to the window start fit 32 bits
+                            const int64_t bnd = ej < nseg ? bs.off[ej + 1] - tu : INT32_MAX;
+                            const int32_t rb = bnd < INT32_MAX ? (int32_t)bnd : INT32_MAX;
                             int k = 0;                     // number of ends <= t
 #pragma unroll
                             for (int step = 16; step > 0; step >>= 1) {
-                                const int64_t bv = __shfl_sync(kFull, bnd, k + step - 1);
-                                if (bv <= t) k += step;
+                                const int32_t bv = __shfl_sync(kFull, rb, k + step - 1);
+                                if (bv <= lane) k += step;
                             }
                             me = e + k;
                         }
                     }
-                    qv[u] = bs.beg[me] + (t - bs.off[me]);
+                    qv[u] = bs.base[me] + t;
                     if constexpr (kVal) av[u] = bs.a[me];
                     else av[u] = In();
                 }
@@ -284,7 +286,7 @@ SPG_DEV void cta_walk_segments(const DCsr& B, int64_t beg, int64_t len, In a,
                 if (tn < hi_w) {
                     while (bs.off[e + 1] <= tn) ++e;
                 }
-                ebase = bs.beg[e] - bs.off[e];
+                ebase = bs.base[e];
                 eend = bs.off[e + 1];
                 if constexpr (kVal) ea = bs.a[e];
             }
@@ -404,6 +406,7 @@ SPG_DEV void warp_table_walk(const DCsr& B, int64_t b, int64_t e, In a, Op& op) 
     const int64_t len = e - b;
     const int64_t my_end = warp_incl_scan(len);
     const int64_t excl = my_end - len;
+    const int64_t qbase = b - excl;   // q = qbase + t for the lane's products
     const int64_t total = __shfl_sync(kFull, my_end, 31);
     const int64_t lo_w = total * wid / nwarps, hi_w = total * (wid + 1) / nwarps;
     int kc = 0;   // entry holding product t0 (warp-uniform, advances with t0)
@@ -416,7 +419,7 @@ SPG_DEV void warp_table_walk(const DCsr& B, int64_t b, int64_t e, In a, Op& op) 
         if (t0 + 32 * kWalkWin <= endk && t0 + 32 * kWalkWin <= hi_w) {
             // the window lies in one segment (the common case for hub rows of
             // B): addresses without a per-lane search
-            const int64_t base = __shfl_sync(kFull, b, kc) - __shfl_sync(kFull, excl, kc);
+            const int64_t base = __shfl_sync(kFull, qbase, kc);
             const In ak = shfl_val<In, kVal>(a, kc);
 #pragma unroll
             for (int u = 0; u < kWalkWin; ++u) {
@@ -427,15 +430,19 @@ SPG_DEV void warp_table_walk(const DCsr& B, int64_t b, int64_t e, In a, Op& op) 
         } else {
 #pragma unroll
             for (int u = 0; u < kWalkWin; ++u) {
-                const int64_t t = t0 + 32 * u + lane;
+                const int64_t tu = t0 + 32 * u, t = tu + lane;
                 vv[u] = t < hi_w;
+                // prefix ends relative to the pass start (clamped to 32 bits:
+                // only their order against 0..31 matters)
+                const int64_t rel = my_end - tu;
+                const int32_t re = rel > INT32_MAX ? INT32_MAX : (rel < INT32_MIN ? INT32_MIN : (int32_t)rel);
                 int k = 0;   // entry of product t: number of prefix ends <= t
 #pragma unroll
                 for (int step = 16; step > 0; step >>= 1) {
-                    const int64_t bv = __shfl_sync(kFull, my_end, k + step - 1);
-                    if (bv <= t) k += step;
+                    const int32_t bv = __shfl_sync(kFull, re, k + step - 1);
+                    if (bv <= lane) k += step;
                 }
-                qv[u] = __shfl_sync(kFull, b, k) + (t - __shfl_sync(kFull, excl, k));
+                qv[u] = __shfl_sync(kFull, qbase, k) + t;
                 av[u] = shfl_val<In, kVal>(a, k);
             }
         }
