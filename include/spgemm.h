@@ -95,7 +95,11 @@ typedef struct {
     int64_t host_panel_bytes;   /* host API: outputs larger than this are produced in
                                    row panels of about this size, each panel's download
                                    overlapping the next panel's kernels (0: 1 GiB)     */
-    int64_t reserved[2];
+    int64_t deterministic;      /* != 0: plus-times FP64/FP32 values are summed in the
+                                   order of A's entries (k ascending, a left fold from
+                                   the first product): bit-identical run to run and to a
+                                   sequential Gustavson; costs an extra ordered pass    */
+    int64_t reserved[1];
 } spg_tuning;
 
 /* Counters of the last analysis on a handle (host copy, filled by spgemm_symbolic). */

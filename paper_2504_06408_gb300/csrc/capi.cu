@@ -492,6 +492,8 @@ static spg_status numeric_impl(spg_handle* h, int sr, int nprob, const spg_csr* 
     delete tab;
     if (e == cudaSuccess)
         e = launch_numeric(sr, w, to_dcsr(B), nprob, L.R, t, max_ncols(nprob, B), h->dev, st);
+    if (e == cudaSuccess && h->user.deterministic)
+        e = launch_det_values(sr, w, nprob, L.R, h->dev, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "numeric launch");
     return SPG_OK;
 }
@@ -1166,6 +1168,9 @@ spg_status spgemm_learned_numeric(spg_handle* h, spg_semiring sr, const spg_csr*
     if (e == cudaSuccess) e = launch_learned_compact(sr, w, lw, 1, L.R, h->dev, st);
     w.skip = lw.skip;
     if (e == cudaSuccess) e = launch_numeric(sr, w, to_dcsr(B), 1, L.R, t, B->ncols, h->dev, st);
+    w.skip = nullptr;
+    if (e == cudaSuccess && h->user.deterministic)
+        e = launch_det_values(sr, w, 1, L.R, h->dev, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "learned numeric launch");
     return SPG_OK;
 }

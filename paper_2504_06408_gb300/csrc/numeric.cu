@@ -10,6 +10,8 @@
 //   dense : one CTA per row; a dense accumulator array over a slab of
 //           columns in shared memory, slab after slab.  Output comes out of
 //           a bitmap scan, already sorted: no sort.
+#include <type_traits>
+
 #include "plan.h"
 #include "rowwork.cuh"
 #include "semiring.cuh"
@@ -847,6 +849,81 @@ __global__ void __launch_bounds__(kRankThreads, 1)
         }
         __syncthreads();
     }
+}
+
+// ---- deterministic plus-times values ---------------------------------------------
+//
+// Recomputes the values of C rows already written (sorted columns known): a
+// warp per row takes A_i's entries in order; for entry k the lanes cover
+// B_k's entries (distinct columns), find each column's position in the row by
+// binary search and add the product there.  Every position is updated in k
+// order, starting from -0 (the identity that keeps the first product exactly,
+// signed zeros included), with separately rounded products and sums: the
+// result is the sequential left fold of the definition (Section 2.1),
+// whatever the schedule.
+template <class S>
+SPG_DEV typename S::Out det_zero() {
+    if constexpr (std::is_floating_point<typename S::Out>::value) return -typename S::Out(0);
+    else return typename S::Out(0);
+}
+
+template <class S>
+__global__ void k_det_values(const Prob* __restrict__ probs, int nprob, int64_t R) {
+    using In = typename S::In;
+    using Out = typename S::Out;
+    const int lane = lane_id();
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); g < R; g += nw) {
+        const Prob& P = probs[nprob == 1 ? 0 : find_prob(probs, nprob, g)];
+        const int64_t i = g - P.row_base;
+        const int64_t cs = P.c_rp[i], ce = P.c_rp[i + 1];
+        Out* cv = reinterpret_cast<Out*>(P.c_val);
+        const int32_t* cc = P.c_col;
+        for (int64_t t = cs + lane; t < ce; t += 32) cv[t] = det_zero<S>();
+        __syncwarp();
+        const int64_t a0 = ld_i64(P.A.rp + i), a1 = ld_i64(P.A.rp + i + 1);
+        for (int64_t p = a0; p < a1; ++p) {
+            const int32_t k = ld_i32(P.A.col + p);
+            const In a = load_val<In, true>(P.A.val, p);
+            const int64_t b0 = ld_i64(P.B.rp + k), b1 = ld_i64(P.B.rp + k + 1);
+            for (int64_t q = b0 + lane; q < b1; q += 32) {
+                const int32_t j = ld_i32(P.B.col + q);
+                int64_t lo = cs, hi = ce;   // first position with column >= j
+                while (lo < hi) {
+                    const int64_t m = (lo + hi) >> 1;
+                    if (cc[m] < j) lo = m + 1; else hi = m;
+                }
+                if (lo < ce && cc[lo] == j)
+                    cv[lo] = S::add(cv[lo], S::prod(a, load_val<In, true>(P.B.val, q)));
+            }
+            __syncwarp();   // entry k's updates land before entry k+1's
+        }
+    }
+}
+
+struct DetLaunch {
+    const WsPtrs* w;
+    int nprob;
+    int64_t R;
+    const DevInfo* dev;
+    cudaStream_t st;
+    template <class S> void operator()() {
+        if constexpr (std::is_same<S, SrPtF64>::value || std::is_same<S, SrPtF32>::value) {
+            int64_t blocks = (R + 7) / 8;
+            if (blocks > (int64_t)dev->sms * 32) blocks = (int64_t)dev->sms * 32;
+            if (blocks < 1) blocks = 1;
+            k_det_values<S><<<(unsigned)blocks, 256, 0, st>>>(w->probs, nprob, R);
+            count_launch(*dev);
+        }
+    }
+};
+
+cudaError_t launch_det_values(int sr, const WsPtrs& w, int nprob, int64_t R, const DevInfo& dev,
+                              cudaStream_t st) {
+    if (R <= 0) return cudaSuccess;
+    DetLaunch f{&w, nprob, R, &dev, st};
+    if (!dispatch_semiring(sr, f)) return cudaErrorInvalidValue;
+    return cudaGetLastError();
 }
 
 // ---- slab starts of B's rows ------------------------------------------------------

@@ -135,6 +135,10 @@ cudaError_t launch_numeric(int sr, const WsPtrs& w, const DCsr& B0, int nprob, i
                            const Tuning& t, int64_t max_ncols, const DevInfo& dev,
                            cudaStream_t st);
 cudaError_t launch_validate(const DCsr& M, int64_t nnz, DevStatus* status, cudaStream_t st);
+// plus-times FP64/FP32: values of the written C rows recomputed in A's entry
+// order (deterministic mode); no-op for other semirings
+cudaError_t launch_det_values(int sr, const WsPtrs& w, int nprob, int64_t R, const DevInfo& dev,
+                              cudaStream_t st);
 
 // shared-memory bytes of each tier (for tuning clamps and launches)
 size_t sym_warp_smem_per_warp(const Tuning& t);

@@ -50,7 +50,7 @@ class spg_tuning(ctypes.Structure):
                 ("num_warp_max_nnz", ctypes.c_int64), ("num_block_max_nnz", ctypes.c_int64),
                 ("dense_slab_cols", ctypes.c_int64), ("sym_slab_cols", ctypes.c_int64),
                 ("bitmap_cache_bytes", ctypes.c_int64), ("host_panel_bytes", ctypes.c_int64),
-                ("reserved", ctypes.c_int64 * 2)]
+                ("deterministic", ctypes.c_int64), ("reserved", ctypes.c_int64 * 1)]
 
 
 class spg_stats(ctypes.Structure):
