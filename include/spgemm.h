@@ -433,6 +433,32 @@ spg_status spgemm_mlp_adam(spg_handle* handle, float* master, float* m, float* v
 spg_status spgemm_mlp_to_bf16(spg_handle* handle, const float* master, void* params_bf16,
                               void* stream);
 
+/*
+ * Masked product: C = (A (x).(+) B) restricted to the pattern of a mask M
+ * (M.nrows = A.nrows, M.ncols = B.ncols, columns ascending per row, values
+ * ignored): C[i,j] is present iff (i,j) is in M and at least one product
+ * A[i,k] (x) B[k,j] exists; its value is the (+) of those products (the
+ * Section 2.1 definition on M's positions).  Each mask entry owns an
+ * accumulator in the workspace (masked_workspace_size: about
+ * nnz(M) * (slot + 1) bytes), so the work follows the products and the mask,
+ * not nnz(A B).
+ *   spgemm_masked_symbolic: accumulates every product that falls on M and
+ *     writes C's row pointers (device int64 [A.nrows + 1]); c_nnz HOST,
+ *     synchronises `stream`.
+ *   spgemm_masked_numeric: writes C.col / C.val from the accumulators of the
+ *     symbolic call (same workspace, same A, B, M).  Asynchronous.
+ */
+spg_status spgemm_masked_workspace_size(spg_handle* handle, spg_semiring sr, const spg_csr* A,
+                                        const spg_csr* B, const spg_csr* M, size_t* bytes);
+spg_status spgemm_masked_symbolic(spg_handle* handle, spg_semiring sr, const spg_csr* A,
+                                  const spg_csr* B, const spg_csr* M, int64_t* c_row_ptr,
+                                  int64_t* c_nnz, void* workspace, size_t workspace_bytes,
+                                  void* stream);
+spg_status spgemm_masked_numeric(spg_handle* handle, spg_semiring sr, const spg_csr* A,
+                                 const spg_csr* B, const spg_csr* M, const int64_t* c_row_ptr,
+                                 int32_t* c_col, void* c_val, void* workspace,
+                                 size_t workspace_bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -179,3 +179,18 @@ def summa_blocks(M, row_cuts, col_cuts):
                                         nnz=int(brp[-1])))
         out.append(line)
     return out
+
+
+def masked(sr, A, B, M):
+    """(A (x).(+) B) on the pattern of M, by its definition: the full product,
+    then the entries whose (i, j) is in M."""
+    C = spgemm(sr, A, B)
+    keep = np.zeros(C.nnz, dtype=bool)
+    for i in range(C.nrows):
+        a, b = int(C.rp[i]), int(C.rp[i + 1])
+        m = np.asarray(M.col[int(M.rp[i]):int(M.rp[i + 1])])
+        keep[a:b] = np.isin(C.col[a:b], m)
+    rp = np.zeros(C.nrows + 1, dtype=np.int64)
+    np.cumsum([int(keep[int(C.rp[i]):int(C.rp[i + 1])].sum()) for i in range(C.nrows)], out=rp[1:])
+    return SimpleNamespace(nrows=C.nrows, ncols=C.ncols, rp=rp, col=C.col[keep],
+                           val=None if C.val is None else C.val[keep], nnz=int(rp[-1]))

@@ -1246,3 +1246,93 @@ spg_status spgemm_mlp_to_bf16(spg_handle* h, const float* master, void* params_b
 }
 
 }  // extern "C"
+
+// ---- masked product -------------------------------------------------------------
+
+struct MaskedLayout {
+    size_t status, slots, touched, part, total;
+};
+
+static MaskedLayout masked_layout(int sr, int64_t nnz_m, int64_t R) {
+    MaskedLayout L;
+    size_t o = 0;
+    L.status = o;  o = align256(o + sizeof(DevStatus));
+    L.slots = o;   o = align256(o + masked_slot_bytes(sr) * (size_t)nnz_m);
+    L.touched = o; o = align256(o + (size_t)nnz_m);
+    L.part = o;    o = align256(o + sizeof(int64_t) * (size_t)(scan_parts_needed(R) + 1));
+    L.total = o;
+    return L;
+}
+
+static spg_status masked_check(spg_handle* h, int sr, const spg_csr* A, const spg_csr* B,
+                               const spg_csr* M, bool need_val) {
+    spg_status s = check_pair(h, sr, A, B, need_val);
+    if (s != SPG_OK) return s;
+    s = check_csr_arg(h, M, "M", SPG_SR_BOOL_OR_AND, false);
+    if (s != SPG_OK) return s;
+    if (M->nrows != A->nrows || M->ncols != B->ncols)
+        return fail(h, SPG_ERR_INVALID_ARG, "mask shape %lld x %lld, product %lld x %lld",
+                    (long long)M->nrows, (long long)M->ncols, (long long)A->nrows,
+                    (long long)B->ncols);
+    return SPG_OK;
+}
+
+extern "C" {
+
+spg_status spgemm_masked_workspace_size(spg_handle* h, spg_semiring sr, const spg_csr* A,
+                                        const spg_csr* B, const spg_csr* M, size_t* bytes) {
+    spg_status s = masked_check(h, sr, A, B, M, false);
+    if (s != SPG_OK) return s;
+    if (!bytes) return fail(h, SPG_ERR_INVALID_ARG, "bytes is NULL");
+    *bytes = masked_layout(sr, M->nnz, A->nrows).total;
+    return SPG_OK;
+}
+
+spg_status spgemm_masked_symbolic(spg_handle* h, spg_semiring sr, const spg_csr* A,
+                                  const spg_csr* B, const spg_csr* M, int64_t* c_row_ptr,
+                                  int64_t* c_nnz, void* workspace, size_t workspace_bytes,
+                                  void* stream) {
+    spg_status s = masked_check(h, sr, A, B, M, true);
+    if (s != SPG_OK) return s;
+    if (!c_row_ptr || !c_nnz) return fail(h, SPG_ERR_INVALID_ARG, "c_row_ptr / c_nnz is NULL");
+    const MaskedLayout L = masked_layout(sr, M->nnz, A->nrows);
+    if (!workspace || workspace_bytes < L.total)
+        return fail(h, SPG_ERR_WORKSPACE, "workspace needs %zu bytes", L.total);
+    cudaStream_t st = (cudaStream_t)stream;
+    char* b = (char*)workspace;
+    h->launches = 0;
+    cudaError_t e = cudaMemsetAsync(b + L.status, 0, sizeof(DevStatus), st);
+    if (e == cudaSuccess)
+        e = launch_masked_count(sr, to_dcsr(A), to_dcsr(B), to_dcsr(M), M->nnz, b + L.slots,
+                                (uint8_t*)(b + L.touched), c_row_ptr, (int64_t*)(b + L.part),
+                                h->dev, st);
+    int64_t* hs = (int64_t*)h->pinned;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hs, c_row_ptr + A->nrows, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "masked symbolic");
+    *c_nnz = hs[0];
+    h->stats.nnz_c = hs[0];
+    return SPG_OK;
+}
+
+spg_status spgemm_masked_numeric(spg_handle* h, spg_semiring sr, const spg_csr* A,
+                                 const spg_csr* B, const spg_csr* M, const int64_t* c_row_ptr,
+                                 int32_t* c_col, void* c_val, void* workspace,
+                                 size_t workspace_bytes, void* stream) {
+    spg_status s = masked_check(h, sr, A, B, M, true);
+    if (s != SPG_OK) return s;
+    if (!c_row_ptr) return fail(h, SPG_ERR_INVALID_ARG, "c_row_ptr is NULL");
+    const MaskedLayout L = masked_layout(sr, M->nnz, A->nrows);
+    if (!workspace || workspace_bytes < L.total)
+        return fail(h, SPG_ERR_WORKSPACE, "workspace needs %zu bytes", L.total);
+    char* b = (char*)workspace;
+    h->launches = 0;
+    cudaError_t e = launch_masked_write(sr, to_dcsr(M), b + L.slots, (const uint8_t*)(b + L.touched),
+                                        c_row_ptr, c_col, c_val, (DevStatus*)(b + L.status),
+                                        h->dev, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "masked numeric");
+    return SPG_OK;
+}
+
+}  // extern "C"

@@ -135,6 +135,15 @@ cudaError_t launch_numeric(int sr, const WsPtrs& w, const DCsr& B0, int nprob, i
                            const Tuning& t, int64_t max_ncols, const DevInfo& dev,
                            cudaStream_t st);
 cudaError_t launch_validate(const DCsr& M, int64_t nnz, DevStatus* status, cudaStream_t st);
+// masked product (masked.cu): accumulators per mask entry; cnt = C's row
+// pointers (R + 1), counted then scanned in place
+size_t masked_slot_bytes(int sr);
+cudaError_t launch_masked_count(int sr, const DCsr& A, const DCsr& B, const DCsr& M,
+                                int64_t nnz_m, void* slots, uint8_t* touched, int64_t* cnt,
+                                int64_t* part, const DevInfo& dev, cudaStream_t st);
+cudaError_t launch_masked_write(int sr, const DCsr& M, const void* slots, const uint8_t* touched,
+                                const int64_t* c_rp, int32_t* c_col, void* c_val,
+                                DevStatus* status, const DevInfo& dev, cudaStream_t st);
 // plus-times FP64/FP32: values of the written C rows recomputed in A's entry
 // order (deterministic mode); no-op for other semirings
 cudaError_t launch_det_values(int sr, const WsPtrs& w, int nprob, int64_t R, const DevInfo& dev,

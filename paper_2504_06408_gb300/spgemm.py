@@ -137,6 +137,12 @@ def load_library(path: str = LIB_PATH):
                             _P],
         "spgemm_mlp_adam": [_P, _P, _P, _P, _P, _P, ctypes.c_float, ctypes.c_int, _P],
         "spgemm_mlp_to_bf16": [_P, _P, _P, _P],
+        "spgemm_masked_workspace_size": [_P, ctypes.c_int, _CSR, _CSR, _CSR,
+                                         ctypes.POINTER(ctypes.c_size_t)],
+        "spgemm_masked_symbolic": [_P, ctypes.c_int, _CSR, _CSR, _CSR, _P, ctypes.POINTER(_I64),
+                                   _P, ctypes.c_size_t, _P],
+        "spgemm_masked_numeric": [_P, ctypes.c_int, _CSR, _CSR, _CSR, _P, _P, _P, _P,
+                                  ctypes.c_size_t, _P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -162,7 +168,8 @@ def exported_symbols() -> list[str]:
             "spgemm_split_columns", "spgemm_learned_workspace_size", "spgemm_learned_plan",
             "spgemm_learned_symbolic", "spgemm_learned_numeric", "spgemm_row_features",
             "spgemm_mlp_forward", "spgemm_mlp_train_workspace_size", "spgemm_mlp_grad",
-            "spgemm_mlp_adam", "spgemm_mlp_to_bf16"]
+            "spgemm_mlp_adam", "spgemm_mlp_to_bf16", "spgemm_masked_workspace_size",
+            "spgemm_masked_symbolic", "spgemm_masked_numeric"]
 
 
 @dataclass
@@ -574,6 +581,34 @@ def learned_spgemm(sr: int, A: DeviceCSR, B: DeviceCSR, model=None, margin: floa
     if check:
         h.check(ws)
     return DeviceCSR(A.nrows, B.ncols, c_rp, c_col, c_val)
+
+
+def masked_spgemm(sr: int, A: DeviceCSR, B: DeviceCSR, M: DeviceCSR,
+                  handle: Optional[Handle] = None, check: bool = True) -> DeviceCSR:
+    """C = (A (x).(+) B) on the pattern of M (masked product, on the GPU)."""
+    import torch
+    h = handle or Handle()
+    dev = A.rp.device
+    a, b, m = A.c(), B.c(), M.c()
+    n = ctypes.c_size_t()
+    h._ok(h.lib.spgemm_masked_workspace_size(h._h, sr, ctypes.byref(a), ctypes.byref(b),
+                                             ctypes.byref(m), ctypes.byref(n)))
+    ws = torch.empty(max(n.value, 1), dtype=torch.uint8, device=dev)
+    c_rp = torch.empty(A.nrows + 1, dtype=torch.int64, device=dev)
+    nnz = ctypes.c_int64()
+    h._ok(h.lib.spgemm_masked_symbolic(h._h, sr, ctypes.byref(a), ctypes.byref(b),
+                                       ctypes.byref(m), c_rp.data_ptr(), ctypes.byref(nnz),
+                                       ws.data_ptr(), ws.numel(), _stream_ptr()))
+    c_col = torch.empty(max(nnz.value, 1), dtype=torch.int32, device=dev)
+    c_val = out_tensor(sr, max(nnz.value, 1), dev)
+    h._ok(h.lib.spgemm_masked_numeric(
+        h._h, sr, ctypes.byref(a), ctypes.byref(b), ctypes.byref(m), c_rp.data_ptr(),
+        c_col.data_ptr(), None if c_val is None else c_val.data_ptr(), ws.data_ptr(), ws.numel(),
+        _stream_ptr()))
+    if check:
+        h.check(ws)
+    k = nnz.value
+    return DeviceCSR(A.nrows, B.ncols, c_rp, c_col[:k], None if c_val is None else c_val[:k])
 
 
 def typed_out(sr: int, raw):

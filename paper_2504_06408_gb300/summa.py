@@ -10,9 +10,13 @@ persistent launch per kernel tier over every block's rows, heaviest first),
 and the q^2 merges are one batched merge call.  The numeric phase and the
 merge can be captured once into a CUDA graph and replayed.
 
-Blocks are views: A's columns are split into the q stage ranges and B's into
+Blocks are views: A's columns are split into the stage ranges and B's into
 the q column ranges (spgemm_split_columns, on the GPU); block (I, s) is the
 row range I of column part s (row views need no copy).
+
+The 2.5D variant (Section 2.1's 2.5D grid: each stage split in halves, whose
+partials are merged like stages) is the same driver with 2q stages
+(`stages=2 * q`): q^2 x 2q block products and merges of 2q partials.
 
 This module only orders library calls and allocates their buffers with
 torch; every step runs in the library's kernels.
@@ -42,7 +46,8 @@ class Summa:
     """C = A (x).(+) B emulated on a q x q Sparse-SUMMA grid.
 
     row_cuts split A's rows (grid rows), inner_cuts split the inner dimension
-    (stages), col_cuts split B's columns (grid columns); defaults are even.
+    (stages; without inner_cuts, `stages` even ones, default q), col_cuts split
+    B's columns (grid columns); defaults are even.
     batched=False runs one library call per block product and per merge (the
     plain form); batched=True one call for all of them.
 
@@ -54,20 +59,22 @@ class Summa:
     """
 
     def __init__(self, handle: api.Handle, sr: int, A: api.DeviceCSR, B: api.DeviceCSR,
-                 q: int = 4, row_cuts=None, inner_cuts=None, col_cuts=None,
+                 q: int = 4, row_cuts=None, inner_cuts=None, col_cuts=None, stages=None,
                  batched: bool = True, unbatched_cache_bytes: int = 4 << 30,
                  tuning: Optional[dict] = None):
         import torch
         self.h, self.sr, self.q, self.batched = handle, sr, q, batched
         self.A, self.B = A, B
         self.row_cuts = list(row_cuts or even_cuts(A.nrows, q))
-        self.inner_cuts = list(inner_cuts or even_cuts(A.ncols, q))
+        self.inner_cuts = list(inner_cuts or even_cuts(A.ncols, stages or q))
+        self.stages = len(self.inner_cuts) - 1
         self.col_cuts = list(col_cuts or even_cuts(B.ncols, q))
         vb = api.IN_NP[sr] and np.dtype(api.IN_NP[sr]).itemsize or 0
         self.vb = vb
         self.Ap = handle.split_columns(A, self.inner_cuts, vb)   # stage parts of A
         self.Bp = handle.split_columns(B, self.col_cuts, vb)     # column parts of B
-        self.blocks = [Block(I, J, s) for s in range(q) for I in range(q) for J in range(q)]
+        self.blocks = [Block(I, J, s) for s in range(self.stages) for I in range(q)
+                       for J in range(q)]
         self.As = [self.Ap[b.s].rows(self.row_cuts[b.I], self.row_cuts[b.I + 1]) for b in self.blocks]
         self.Bs = [self.Bp[b.J].rows(self.inner_cuts[b.s], self.inner_cuts[b.s + 1])
                    for b in self.blocks]
@@ -123,7 +130,7 @@ class Summa:
     def _groups(self):
         q = self.q
         idx = {(b.I, b.J, b.s): k for k, b in enumerate(self.blocks)}
-        return [[self.partials[idx[(I, J, s)]] for s in range(q)]
+        return [[self.partials[idx[(I, J, s)]] for s in range(self.stages)]
                 for I in range(q) for J in range(q)]
 
     def merge_count(self):

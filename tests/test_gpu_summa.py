@@ -186,6 +186,25 @@ def test_summa_dense_tier_blocks(batched):
     _check_blocks(sm, sr, A, A)
 
 
+@pytest.mark.parametrize("sr", [api.PLUS_TIMES_F64, api.MIN_PLUS_F32, api.OVERLAP_I32])
+def test_summa_2_5d_half_stages(sr):
+    """2.5D split: every stage in halves, 8 partials per C block merged."""
+    pat = I.rmat(11, seed=9, dtype=None)
+    A = values_for(sr, pat, 1)
+    B = values_for(sr, pat, 2) if sr != api.OVERLAP_I32 else I.positions_csr(pat, 2)
+    h = api.Handle()
+    dA = api.DeviceCSR.from_host(A, val_dtype=api.IN_NP[sr])
+    dB = api.DeviceCSR.from_host(B, val_dtype=api.IN_NP[sr])
+    sm = Summa(h, sr, dA, dB, q=4, stages=8)
+    assert sm.stages == 8 and len(sm.blocks) == 128
+    sm.plan()
+    sm.capture()
+    sm.run()
+    sm.check()
+    torch.cuda.synchronize()
+    _check_blocks(sm, sr, A, B)
+
+
 def test_summa_graph_replay_matches():
     sr = api.MIN_PLUS_F32
     pat = I.rmat(12, seed=8, dtype=None)

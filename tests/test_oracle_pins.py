@@ -534,3 +534,67 @@ def test_generators_deterministic_and_valid():
     rows = np.repeat(np.arange(512), np.diff(R.rp))
     D[rows, R.col] = R.val
     assert np.array_equal(D, D.T) and np.all(np.diag(D) == 0)
+
+
+# ---- masked product (oracle.masked) ------------------------------------------
+
+def _lower(A):
+    rows, cols = [], []
+    for i in range(A.nrows):
+        c = A.col[A.rp[i]:A.rp[i + 1]]
+        c = c[c < i]
+        rows.append(np.full(c.size, i, dtype=np.int64))
+        cols.append(c)
+    r = np.concatenate(rows)
+    c = np.concatenate(cols).astype(np.int32)
+    rp = np.zeros(A.nrows + 1, dtype=np.int64)
+    np.add.at(rp, r + 1, 1)
+    return I.CSR(A.nrows, A.ncols, np.cumsum(rp), c, np.ones(c.size, dtype=np.int64))
+
+
+def test_masked_triangle_count_matches_trace():
+    """sum of (L L) o L over plus-times = number of triangles = trace(A^3) / 6."""
+    A = I.rmat(8, seed=5, dtype=None)
+    L = _lower(A)
+    C = oracle.masked(oracle.SR_PT_I64, L, L, L)
+    D = np.zeros((A.nrows, A.nrows), dtype=np.int64)
+    for i in range(A.nrows):
+        D[i, A.col[A.rp[i]:A.rp[i + 1]]] = 1
+    assert int(C.val.sum()) == int(np.trace(D @ D @ D)) // 6
+    assert int(C.val.sum()) > 0
+
+
+def test_masked_dense_brute_force_and_limits():
+    rng = np.random.default_rng(3)
+    A = I.random_csr(20, 15, 0.3, 1, dtype=np.float64, empty_row_frac=0.1)
+    B = I.random_csr(15, 25, 0.3, 2, dtype=np.float64)
+    M = I.random_csr(20, 25, 0.4, 3, dtype=None)
+    C = oracle.masked(oracle.SR_PT_F64, A, B, M)
+    Ad, Bd = np.zeros((20, 15)), np.zeros((15, 25))
+    Ph = np.zeros((20, 25), dtype=bool)   # has a product
+    for i in range(20):
+        for p in range(A.rp[i], A.rp[i + 1]):
+            k = A.col[p]
+            Ad[i, k] = A.val[p]
+            for q in range(B.rp[k], B.rp[k + 1]):
+                Ph[i, B.col[q]] = True
+    for k in range(15):
+        Bd[k, B.col[B.rp[k]:B.rp[k + 1]]] = B.val[B.rp[k]:B.rp[k + 1]]
+    Md = np.zeros((20, 25), dtype=bool)
+    for i in range(20):
+        Md[i, M.col[M.rp[i]:M.rp[i + 1]]] = True
+    want = Ph & Md
+    got = np.zeros((20, 25), dtype=bool)
+    vals = np.zeros((20, 25))
+    for i in range(20):
+        got[i, C.col[C.rp[i]:C.rp[i + 1]]] = True
+        vals[i, C.col[C.rp[i]:C.rp[i + 1]]] = C.val[C.rp[i]:C.rp[i + 1]]
+    assert np.array_equal(got, want)
+    assert np.allclose(vals[want], (Ad @ Bd)[want], rtol=1e-12, atol=1e-15)
+    # mask = C's own pattern gives C; an empty mask gives nothing
+    full = oracle.spgemm(oracle.SR_PT_F64, A, B)
+    same = oracle.masked(oracle.SR_PT_F64, A, B, full)
+    assert np.array_equal(same.rp, full.rp) and np.array_equal(same.val, full.val)
+    empty = I.random_csr(20, 25, 0.0, 4, dtype=None)
+    assert oracle.masked(oracle.SR_PT_F64, A, B, empty).nnz == 0
+    del rng
