@@ -660,12 +660,14 @@ struct RankAccOp {
     typename S::Slot* vals;
     const uint32_t* bm;
     const int32_t* word_off;
-    int32_t r0;
-    int32_t clo, chi;   // columns of this pass (products outside are skipped)
+    int32_t r1;         // rank of the pass's first output, plus one
+    int32_t clo;        // columns of this pass: [clo, clo + width) (products outside are skipped)
+    uint32_t width;
     SPG_DEV void any(int32_t col, typename S::In a, typename S::In b, bool valid) {
-        if (!valid || col < clo || col >= chi) return;
+        if (!valid || (uint32_t)(col - clo) >= width) return;
         const int w = col >> 5;
-        const int r = word_off[w] + __popc(bm[w] & ((1u << (col & 31)) - 1u)) - r0;
+        // bits of word w at or below col's bit (col's own bit is set): its rank + 1
+        const int r = word_off[w] + __popc(bm[w] << (~col & 31)) - r1;
         S::acc(vals + r, a, b);
     }
 };
@@ -774,11 +776,18 @@ __global__ void __launch_bounds__(kRankThreads, 1)
             continue;
         }
         // (3) C.col from the bitmap, and the block-local offsets made global:
-        //     warp w walks its block 32 words at a time (lane = word).  The
-        //     chunk's columns are expanded into the warp's staging area (the
-        //     value array is free until step 4) at the lanes' offsets, then
-        //     copied to C.col 32 consecutive entries per store.  A chunk too
-        //     dense for the staging area writes each lane's columns directly.
+        //     warp w walks its block 32 words at a time (lane = word).  When
+        //     the chunk's set bits are spread evenly over its words, each lane
+        //     expands its own word into the warp's staging area (the value
+        //     array is free until step 4) at its offset, and the chunk is
+        //     copied to C.col 32 consecutive entries per store (a chunk too
+        //     dense for the staging area writes each lane's columns directly).
+        //     When a few words hold most of the bits (a skewed column
+        //     distribution such as R-MAT's), that loop would run as long as
+        //     the densest word: the chunk is expanded output by output
+        //     instead.  Lane l takes outputs t = l, l + 32, ..., finds the
+        //     word holding t by a binary search over the words' prefix
+        //     counts, the bit by select_bit, and stores C.col[t] (coalesced).
         {
             int32_t* stage = reinterpret_cast<int32_t*>(smem_raw) + (size_t)wid * stage_words;
             const int add = s_wsum[wid];
@@ -794,10 +803,23 @@ __global__ void __launch_bounds__(kRankThreads, 1)
                 const int Tc = lnext - lbase;
                 if (Tc == 0) continue;
                 uint32_t bits = w < words ? bm[w] : 0u;
-                int pos = lw - lbase;
+                int pos = w < words ? lw - lbase : Tc;   // chunk-local exclusive prefix
                 const int cbase = w * 32;
                 int32_t* dst = P.c_col + off + add + lbase;
-                if (Tc <= stage_words) {
+                const int maxc = (int)__reduce_max_sync(kFull, (unsigned)__popc(bits));
+                if (maxc > 4 * ((Tc + 31) >> 5)) {
+                    const int inc = pos + __popc(bits);
+                    for (int t0 = 0; t0 < Tc; t0 += 32) {   // warp-uniform
+                        const int t = t0 + lane;
+                        int k = 0;   // number of words whose outputs all precede t
+#pragma unroll
+                        for (int step = 16; step > 0; step >>= 1)
+                            if (__shfl_sync(kFull, inc, k + step - 1) <= t) k += step;
+                        const uint32_t bk = __shfl_sync(kFull, bits, k);
+                        const int ek = __shfl_sync(kFull, pos, k);
+                        if (t < Tc) st_stream(dst + t, (int32_t)((w0 + k) * 32 + select_bit(bk, t - ek)));
+                    }
+                } else if (Tc <= stage_words) {
                     while (bits) {
                         const int b = __ffs(bits) - 1;
                         bits &= bits - 1u;
@@ -831,7 +853,7 @@ __global__ void __launch_bounds__(kRankThreads, 1)
                     __syncthreads();
                     const int clo = s0 * slab_cols;
                     const int chi = s1 >= nslabs ? ncols : s1 * slab_cols;
-                    RankAccOp<S> op{vals, bm, word_off, r0, clo, chi};
+                    RankAccOp<S> op{vals, bm, word_off, r0 + 1, clo, (uint32_t)(chi - clo)};
                     // with the slab table the walk covers only the pass's slabs;
                     // without it every product is visited and filtered
                     if (sp != nullptr || (s0 == 0 && s1 >= nslabs))

@@ -243,18 +243,28 @@ SPG_DEV void cta_walk_segments(const DCsr& B, int64_t beg, int64_t len, In a,
         In ea = In();
         if constexpr (kVal) ea = bs.a[e];
         for (int64_t t0 = lo_w; t0 < hi_w; t0 += 32 * kWalkWin) {   // warp-uniform
-            int64_t qv[kWalkWin];
+            int32_t col[kWalkWin];
+            In bval[kWalkWin];
             In av[kWalkWin];
             bool vv[kWalkWin];
             if (eend >= t0 + 32 * kWalkWin || eend >= hi_w) {       // the pass lies in segment e
+                // one base pointer per lane; the windows are fixed offsets from it
+                const int64_t q0 = ebase + t0 + lane;
+                const int64_t left = hi_w - t0 - lane;   // products of the pass from this lane on
+                const int rem = left < 32 * kWalkWin ? (int)left : 32 * kWalkWin;
+                const int32_t* cp = B.col + q0;
 #pragma unroll
                 for (int u = 0; u < kWalkWin; ++u) {
-                    const int64_t t = t0 + 32 * u + lane;
-                    vv[u] = t < hi_w;
-                    qv[u] = ebase + t;
+                    vv[u] = 32 * u < rem;
+                    col[u] = vv[u] ? __ldg(cp + 32 * u) : 0;
+                    if constexpr (kVal)
+                        bval[u] = vv[u] ? __ldg(reinterpret_cast<const In*>(B.val) + q0 + 32 * u) : In();
+                    else
+                        bval[u] = In();
                     av[u] = ea;
                 }
             } else {
+                int64_t qv[kWalkWin];
 #pragma unroll
                 for (int u = 0; u < kWalkWin; ++u) {
                     const int64_t tu = t0 + 32 * u;
@@ -289,13 +299,11 @@ SPG_DEV void cta_walk_segments(const DCsr& B, int64_t beg, int64_t len, In a,
                 ebase = bs.base[e];
                 eend = bs.off[e + 1];
                 if constexpr (kVal) ea = bs.a[e];
-            }
-            int32_t col[kWalkWin];
-            In bval[kWalkWin];
 #pragma unroll
-            for (int u = 0; u < kWalkWin; ++u) {
-                col[u] = vv[u] ? ld_i32(B.col + qv[u]) : 0;
-                bval[u] = vv[u] ? load_val<In, kVal>(B.val, qv[u]) : In();
+                for (int u = 0; u < kWalkWin; ++u) {
+                    col[u] = vv[u] ? ld_i32(B.col + qv[u]) : 0;
+                    bval[u] = vv[u] ? load_val<In, kVal>(B.val, qv[u]) : In();
+                }
             }
 #pragma unroll
             for (int u = 0; u < kWalkWin; ++u) op.any(col[u], av[u], bval[u], vv[u]);
