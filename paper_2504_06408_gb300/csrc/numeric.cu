@@ -658,6 +658,7 @@ struct BitSetOp {
 template <class S>
 struct RankAccOp {
     typename S::Slot* vals;
+    int32_t* cols;      // column of each rank (every product of a column stores the same value)
     const uint32_t* bm;
     const int32_t* word_off;
     int32_t r1;         // rank of the pass's first output, plus one
@@ -669,6 +670,7 @@ struct RankAccOp {
         // bits of word w at or below col's bit (col's own bit is set): its rank + 1
         const int r = word_off[w] + __popc(bm[w] << (~col & 31)) - r1;
         S::acc(vals + r, a, b);
+        cols[r] = col;
     }
 };
 
@@ -676,8 +678,18 @@ constexpr int kRankThreads = 1024;
 
 // bytes of the rank kernel's value array, rounded up to 16
 template <class S>
-__host__ __device__ inline size_t rank_val_bytes(int64_t cap) {
+__host__ __device__ inline size_t rank_slot_bytes(int64_t cap) {
     return S::kVal ? (((size_t)cap * sizeof(typename S::Slot) + 15) & ~(size_t)15) : 0;
+}
+// the value array followed by the column of each rank
+template <class S>
+__host__ __device__ inline size_t rank_val_bytes(int64_t cap) {
+    return S::kVal ? rank_slot_bytes<S>(cap) + (((size_t)cap * 4 + 15) & ~(size_t)15) : 0;
+}
+// shared-memory bytes per output of a value pass
+template <class S>
+constexpr size_t rank_entry_bytes() {
+    return S::kVal ? sizeof(typename S::Slot) + 4 : 0;
 }
 // the value array's region, which first serves as the warps' C.col staging:
 // at least 3 KB per warp
@@ -699,6 +711,7 @@ __global__ void __launch_bounds__(kRankThreads, 1)
     using In = typename S::In;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Slot* vals = reinterpret_cast<Slot*>(smem_raw);                          // [cap]
+    int32_t* cols = reinterpret_cast<int32_t*>(smem_raw + rank_slot_bytes<S>(cap));   // [cap]
     // the bitmap is filled with 16-byte copies: its offset must be 16-aligned
     uint32_t* bm = reinterpret_cast<uint32_t*>(smem_raw + rank_region_bytes<S>(cap));
     int32_t* word_off = reinterpret_cast<int32_t*>(bm + bm_words);           // [words + 1]
@@ -775,8 +788,10 @@ __global__ void __launch_bounds__(kRankThreads, 1)
             __syncthreads();
             continue;
         }
-        // (3) C.col from the bitmap, and the block-local offsets made global:
-        //     warp w walks its block 32 words at a time (lane = word).  When
+        // (3) The block-local offsets made global, and (semirings without
+        //     values only) C.col from the bitmap; with values, step 4 writes
+        //     C.col from the columns its products store by rank.
+        //     Warp w walks its block 32 words at a time (lane = word).  When
         //     the chunk's set bits are spread evenly over its words, each lane
         //     expands its own word into the warp's staging area (the value
         //     array is free until step 4) at its offset, and the chunk is
@@ -800,6 +815,7 @@ __global__ void __launch_bounds__(kRankThreads, 1)
                 const int lw = w < words ? word_off[w] : 0;
                 __syncwarp();
                 if (w < words) word_off[w] = lw + add;
+                if constexpr (S::kVal) continue;
                 const int Tc = lnext - lbase;
                 if (Tc == 0) continue;
                 uint32_t bits = w < words ? bm[w] : 0u;
@@ -838,7 +854,8 @@ __global__ void __launch_bounds__(kRankThreads, 1)
             }
         }
         __syncthreads();
-        // (4) values, in passes over groups of column slabs that fit `cap` outputs
+        // (4) values, in passes over groups of column slabs that fit `cap` outputs;
+        //     each pass writes its stretch of C.col and C.val
         if constexpr (S::kVal) {
             int s0 = 0;
             while (s0 < nslabs) {
@@ -853,7 +870,7 @@ __global__ void __launch_bounds__(kRankThreads, 1)
                     __syncthreads();
                     const int clo = s0 * slab_cols;
                     const int chi = s1 >= nslabs ? ncols : s1 * slab_cols;
-                    RankAccOp<S> op{vals, bm, word_off, r0 + 1, clo, (uint32_t)(chi - clo)};
+                    RankAccOp<S> op{vals, cols, bm, word_off, r0 + 1, clo, (uint32_t)(chi - clo)};
                     // with the slab table the walk covers only the pass's slabs;
                     // without it every product is visited and filtered
                     if (sp != nullptr || (s0 == 0 && s1 >= nslabs))
@@ -863,7 +880,11 @@ __global__ void __launch_bounds__(kRankThreads, 1)
                         cta_range_products<In, S::kVal>(P.A, P.B, a0, a1, le, small, sp, sp_stride,
                                                         nslabs, 0, nslabs, bs, op);
                     typename S::Out* cv = reinterpret_cast<typename S::Out*>(P.c_val) + off + r0;
-                    for (int t = tid; t < cnt; t += blockDim.x) st_stream(cv + t, S::out(vals[t]));
+                    int32_t* cc = P.c_col + off + r0;
+                    for (int t = tid; t < cnt; t += blockDim.x) {
+                        st_stream(cv + t, S::out(vals[t]));
+                        st_stream(cc + t, cols[t]);
+                    }
                     __syncthreads();
                 }
                 s0 = s1;
@@ -1062,10 +1083,13 @@ struct NumericLaunch {
             // array of at least one slab fit in shared memory
             const int64_t bm_words = (max_ncols + 1023) / 1024 * 32;
             const size_t fixed = (size_t)bm_words * 8 + 16;
-            const size_t budget = 200 * 1024 - sizeof(BatchSmem<typename S::In, kRankThreads>) + 12 * 1024;
+            // dynamic shared memory: the device's per-block limit less the
+            // kernel's static variables (the batch arrays and a little more)
+            const size_t optin = dev->max_smem_optin > 0 ? (size_t)dev->max_smem_optin : 212 * 1024;
+            const size_t budget = optin - sizeof(BatchSmem<typename S::In, kRankThreads>) - 1024;
             int64_t cap = 0;
             if (fixed + 16 < budget)
-                cap = S::kVal ? (int64_t)((budget - fixed - 16) / sizeof(typename S::Slot)) : 0;
+                cap = S::kVal ? (int64_t)((budget - fixed - 32) / rank_entry_bytes<S>()) : 0;
             if (cap > (int64_t)1 << 30) cap = (int64_t)1 << 30;
             const bool rank_ok = fixed < budget && (!S::kVal || cap >= slab) &&
                                  rank_region_bytes<S>(cap) + fixed <= budget &&
