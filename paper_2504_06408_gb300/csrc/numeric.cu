@@ -623,17 +623,28 @@ __global__ void __launch_bounds__(kBlockThreads, 2)
 // so the accumulation atomics are free of bank conflicts, and a row is walked
 // 1 + (number of value passes) times instead of once per column slab.
 
+// How a row's entries reach the product walk: one per lane, the same in
+// every warp (<= 32 entries); one per thread, loaded once per row (<= the
+// CTA's threads); or loaded batch by batch in every pass.
+enum RowEntries { kEntriesPerLane, kEntriesPerThread, kEntriesBatched };
+
 // Products of row entries [a0, a1) restricted to slabs [s0, s1), spread over the CTA.
 template <class In, bool kVal, class Op, int NT>
 SPG_DEV void cta_range_products(const DCsr& A, const DCsr& B, int64_t a0, int64_t a1,
-                                const LaneEntry<In, kVal>& le, bool small, const int32_t* sp,
+                                const LaneEntry<In, kVal>& le, RowEntries mode, const int32_t* sp,
                                 int sp_stride, int nslabs, int s0, int s1,
                                 BatchSmem<In, NT>& bs, Op& op) {
-    if (small) {
+    if (mode == kEntriesPerLane) {
         int64_t b, e;
         le.range(sp, sp_stride, nslabs, s0, s1, b, e);
         warp_table_walk<In, kVal>(B, b, e, le.a, op);
         __syncthreads();
+        return;
+    }
+    if (mode == kEntriesPerThread) {
+        int64_t b, e;
+        le.range(sp, sp_stride, nslabs, s0, s1, b, e);
+        cta_walk_segments<In, kVal>(B, b, e - b, le.a, bs, op);
         return;
     }
     for (int64_t b0 = a0; b0 < a1; b0 += NT) {
@@ -736,15 +747,22 @@ __global__ void __launch_bounds__(kRankThreads, 1)
         const int ncols = (int)P.B.ncols;
         const int words = (ncols + 31) >> 5;
         const int nslabs = (ncols + slab_cols - 1) / slab_cols;
-        const bool small = a1 - a0 <= 32;
-        LaneEntry<In, S::kVal> le;
-        if (small) le.load(P.A, P.B, a0 + lane, a0 + lane < a1);
-        // (1) presence bitmap of the whole row: the symbolic phase's copy if it
-        //     kept one, else rebuilt from the products
+        const RowEntries mode = a1 - a0 <= 32 ? kEntriesPerLane
+                                : a1 - a0 <= kRankThreads ? kEntriesPerThread : kEntriesBatched;
         // (a slot outside the cache means the workspace did not come from this
         // product's symbolic call: the row is rebuilt and checked against c_rp)
         const int slot = row_slot ? row_slot[g] : -1;
-        if (slot >= 0 && slot < cache_slots && words <= cache_words) {
+        const bool cached = slot >= 0 && slot < cache_slots && words <= cache_words;
+        // the row's entries, held in registers for every walk of the row (none
+        // without values when the bitmap comes from the cache)
+        LaneEntry<In, S::kVal> le;
+        if (S::kVal || !cached) {
+            if (mode == kEntriesPerLane) le.load(P.A, P.B, a0 + lane, a0 + lane < a1);
+            else if (mode == kEntriesPerThread) le.load(P.A, P.B, a0 + tid, a0 + tid < a1);
+        }
+        // (1) presence bitmap of the whole row: the symbolic phase's copy if it
+        //     kept one, else rebuilt from the products
+        if (cached) {
             const uint4* src = reinterpret_cast<const uint4*>(bm_cache + (int64_t)slot * cache_words);
             uint4* dst = reinterpret_cast<uint4*>(bm);
             for (int w = tid; w < (words + 3) / 4; w += blockDim.x) dst[w] = __ldcs(src + w);
@@ -753,7 +771,7 @@ __global__ void __launch_bounds__(kRankThreads, 1)
             for (int w = tid; w < words; w += blockDim.x) bm[w] = 0u;
             __syncthreads();
             BitSetOp op{bm};
-            cta_range_products<In, S::kVal>(P.A, P.B, a0, a1, le, small, sp, sp_stride, nslabs, 0,
+            cta_range_products<In, S::kVal>(P.A, P.B, a0, a1, le, mode, sp, sp_stride, nslabs, 0,
                                             nslabs, bs, op);
         }
         // (2) ranks: exclusive prefix of the words' popcounts.  Warp w scans a
@@ -874,10 +892,10 @@ __global__ void __launch_bounds__(kRankThreads, 1)
                     // with the slab table the walk covers only the pass's slabs;
                     // without it every product is visited and filtered
                     if (sp != nullptr || (s0 == 0 && s1 >= nslabs))
-                        cta_range_products<In, S::kVal>(P.A, P.B, a0, a1, le, small, sp, sp_stride,
+                        cta_range_products<In, S::kVal>(P.A, P.B, a0, a1, le, mode, sp, sp_stride,
                                                         nslabs, s0, s1, bs, op);
                     else
-                        cta_range_products<In, S::kVal>(P.A, P.B, a0, a1, le, small, sp, sp_stride,
+                        cta_range_products<In, S::kVal>(P.A, P.B, a0, a1, le, mode, sp, sp_stride,
                                                         nslabs, 0, nslabs, bs, op);
                     typename S::Out* cv = reinterpret_cast<typename S::Out*>(P.c_val) + off + r0;
                     int32_t* cc = P.c_col + off + r0;
