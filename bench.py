@@ -40,7 +40,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 # the comparison forms allocate and free tens of GB in turn
-os.environ.setdefault("PYTORCH_CUDA_ALLOC_CONF", "expandable_segments:True")
+if "PYTORCH_CUDA_ALLOC_CONF" not in os.environ:
+    os.environ.setdefault("PYTORCH_ALLOC_CONF", "expandable_segments:True")
 
 METRIC = "semiring SpGEMM GFLOPS (2*products/s), R-MAT scale 18 A^2 over min-plus FP32"
 METRIC_SCALED = "semiring SpGEMM GFLOPS (2*products/s), R-MAT scale %d A^2 over min-plus FP32"
