@@ -263,6 +263,29 @@ SPG_DEV void cta_walk_segments(const DCsr& B, int64_t beg, int64_t len, In a,
                         bval[u] = In();
                     av[u] = ea;
                 }
+            } else if (bs.off[e + 2] >= t0 + 32 * kWalkWin || bs.off[e + 2] >= hi_w) {
+                // one segment end inside the pass (eend < hi_w <= total, so
+                // segment e + 1 exists): products before it are segment e's,
+                // the rest segment e + 1's
+                const int64_t nbase = bs.base[e + 1];
+                In na = In();
+                if constexpr (kVal) na = bs.a[e + 1];
+                const int64_t left = hi_w - t0 - lane;
+                const int rem = left < 32 * kWalkWin ? (int)left : 32 * kWalkWin;
+                const int64_t cut = eend - t0 - lane;    // windows u with 32u >= cut are past the end
+#pragma unroll
+                for (int u = 0; u < kWalkWin; ++u) {
+                    vv[u] = 32 * u < rem;
+                    const bool second = 32 * u >= cut;
+                    const int64_t q = (second ? nbase : ebase) + t0 + 32 * u + lane;
+                    col[u] = vv[u] ? ld_i32(B.col + q) : 0;
+                    bval[u] = vv[u] ? load_val<In, kVal>(B.val, q) : In();
+                    av[u] = second ? na : ea;
+                }
+                ++e;
+                ebase = nbase;
+                eend = bs.off[e + 1];
+                ea = na;
             } else {
                 int64_t qv[kWalkWin];
 #pragma unroll
@@ -422,8 +445,14 @@ SPG_DEV void warp_table_walk(const DCsr& B, int64_t b, int64_t e, In a, Op& op) 
         int64_t qv[kWalkWin];
         In av[kWalkWin];
         bool vv[kWalkWin];
-        while (kc < 31 && __shfl_sync(kFull, my_end, kc) <= t0) ++kc;
+        // entries whose products all precede t0 (ends are non-decreasing)
+        kc = __popc(__ballot_sync(kFull, my_end <= t0));
+        if (kc > 31) kc = 31;
         const int64_t endk = __shfl_sync(kFull, my_end, kc);
+        // first entry with products after endk (empty entries are skipped)
+        const unsigned later = __ballot_sync(kFull, my_end > endk);
+        const int kn = later ? __ffs(later) - 1 : 31;
+        const int64_t endn = __shfl_sync(kFull, my_end, kn);
         if (t0 + 32 * kWalkWin <= endk && t0 + 32 * kWalkWin <= hi_w) {
             // the window lies in one segment (the common case for hub rows of
             // B): addresses without a per-lane search
@@ -434,6 +463,20 @@ SPG_DEV void warp_table_walk(const DCsr& B, int64_t b, int64_t e, In a, Op& op) 
                 qv[u] = base + t0 + 32 * u + lane;
                 av[u] = ak;
                 vv[u] = true;
+            }
+        } else if (later && (endn >= t0 + 32 * kWalkWin || endn >= hi_w)) {
+            // one segment end inside the pass: entry kc before it, entry kn after
+            const int64_t base = __shfl_sync(kFull, qbase, kc);
+            const int64_t nbase = __shfl_sync(kFull, qbase, kn);
+            const In ak = shfl_val<In, kVal>(a, kc);
+            const In an = shfl_val<In, kVal>(a, kn);
+#pragma unroll
+            for (int u = 0; u < kWalkWin; ++u) {
+                const int64_t t = t0 + 32 * u + lane;
+                vv[u] = t < hi_w;
+                const bool second = t >= endk;
+                qv[u] = (second ? nbase : base) + t;
+                av[u] = second ? an : ak;
             }
         } else {
 #pragma unroll
