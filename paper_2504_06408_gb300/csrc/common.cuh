@@ -89,6 +89,13 @@ SPG_DEV void st_stream(T* p, const T& v) {
 }
 
 SPG_DEV int64_t ld_i64(const int64_t* p) { return __ldg(p); }
+
+// Bulk prefetch of [p, p + bytes) into L2 (p 16-byte aligned, bytes a
+// multiple of 16); a hint, nothing waits for it.
+SPG_DEV void prefetch_l2(const void* p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;"
+                 :: "l"(__cvta_generic_to_global(p)), "r"(bytes) : "memory");
+}
 SPG_DEV int32_t ld_i32(const int32_t* p) { return __ldg(p); }
 
 // Fibonacci hashing of a column id into a table of 2^(32 - shift) slots

@@ -733,11 +733,23 @@ __global__ void __launch_bounds__(kRankThreads, 1)
     const int tid = threadIdx.x;
     const int tbeg = ctr->num_bin_off[kTierDense * kSubBins];
     const int tend = ctr->num_bin_off[(kTierDense + 1) * kSubBins];
+    // the value array holds `empty` between passes: filled once here, and each
+    // pass's write-out empties the slots it reads
+    if constexpr (S::kVal) fill_slots<S>(vals, cap);
+    // Rows are claimed one ahead: thread 0 claims the next row while this one
+    // starts, and loads its id, then its cache slot, each a phase later, and
+    // prefetches its cached bitmap into L2 before the value passes, so the
+    // next row's bitmap copy does not wait on DRAM (nothing waits on these
+    // loads until a phase boundary has passed).
+    if (tid == 0) s_row = tbeg + atomicAdd(&ctr->claim[3], 1);
+    __syncthreads();
     for (;;) {
-        if (tid == 0) s_row = tbeg + atomicAdd(&ctr->claim[3], 1);
-        __syncthreads();
-        const int r = s_row;
+        const int r = s_row;   // written one row ahead, read after a barrier
         if (r >= tend) break;
+        int nr = tend;
+        int64_t g2 = -1;
+        int slot2 = -1;
+        if (tid == 0) nr = tbeg + atomicAdd(&ctr->claim[3], 1);
         const int64_t g = rows[r];
         const Prob& P = probs[nprob == 1 ? 0 : find_prob(probs, nprob, g)];
         const int64_t i = g - P.row_base;
@@ -774,6 +786,10 @@ __global__ void __launch_bounds__(kRankThreads, 1)
             cta_range_products<In, S::kVal>(P.A, P.B, a0, a1, le, mode, sp, sp_stride, nslabs, 0,
                                             nslabs, bs, op);
         }
+        if (tid == 0) {   // every thread has read r: publish the next row
+            s_row = nr;
+            if (nr < tend && row_slot) g2 = rows[nr];
+        }
         // (2) ranks: exclusive prefix of the words' popcounts.  Warp w scans a
         //     contiguous block of words, lane l reading word base + l + 32 j
         //     (no bank conflicts), into block-local offsets; the warps' block
@@ -800,6 +816,7 @@ __global__ void __launch_bounds__(kRankThreads, 1)
             }
             __syncthreads();
         }
+        if (g2 >= 0) slot2 = row_slot[g2];
         const int T = word_off[words];
         if (T != n) {   // symbolic and numeric disagree: leave the row
             if (tid == 0) flag_overflow(st, g);
@@ -872,6 +889,8 @@ __global__ void __launch_bounds__(kRankThreads, 1)
             }
         }
         __syncthreads();
+        if (slot2 >= 0 && slot2 < cache_slots)
+            prefetch_l2(bm_cache + (int64_t)slot2 * cache_words, (uint32_t)cache_words * 4u);
         // (4) values, in passes over groups of column slabs that fit `cap` outputs;
         //     each pass writes its stretch of C.col and C.val
         if constexpr (S::kVal) {
@@ -884,8 +903,6 @@ __global__ void __launch_bounds__(kRankThreads, 1)
                 const int r1 = word_off[min(s1 * slab_cols, ncols + 31) >> 5];
                 const int cnt = r1 - r0;
                 if (cnt > 0) {
-                    fill_slots<S>(vals, cnt);
-                    __syncthreads();
                     const int clo = s0 * slab_cols;
                     const int chi = s1 >= nslabs ? ncols : s1 * slab_cols;
                     RankAccOp<S> op{vals, cols, bm, word_off, r0 + 1, clo, (uint32_t)(chi - clo)};
@@ -902,6 +919,7 @@ __global__ void __launch_bounds__(kRankThreads, 1)
                     for (int t = tid; t < cnt; t += blockDim.x) {
                         st_stream(cv + t, S::out(vals[t]));
                         st_stream(cc + t, cols[t]);
+                        vals[t] = S::empty();
                     }
                     __syncthreads();
                 }
