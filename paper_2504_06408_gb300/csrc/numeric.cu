@@ -657,29 +657,36 @@ SPG_DEV void cta_range_products(const DCsr& A, const DCsr& B, int64_t a0, int64_
     }
 }
 
+// The rank kernel keeps word w of the row bitmap (x) and the number of set
+// bits before it (y) side by side, so one 8-byte load gives a product's rank.
 struct BitSetOp {
-    uint32_t* bm;
+    uint2* bw;
     template <class In> SPG_DEV void any(int32_t col, In, In, bool valid) {
         if (!valid) return;
         const uint32_t bit = 1u << (col & 31);
-        if (!(bm[col >> 5] & bit)) atomicOr(bm + (col >> 5), bit);
+        uint32_t* word = &bw[col >> 5].x;
+        if (!(*word & bit)) atomicOr(word, bit);
     }
 };
 
-template <class S>
+// kFilter: the walk may reach products outside the pass's columns (no slab
+// table), which are skipped
+template <class S, bool kFilter>
 struct RankAccOp {
     typename S::Slot* vals;
     int32_t* cols;      // column of each rank (every product of a column stores the same value)
-    const uint32_t* bm;
-    const int32_t* word_off;
+    const uint2* bw;
     int32_t r1;         // rank of the pass's first output, plus one
-    int32_t clo;        // columns of this pass: [clo, clo + width) (products outside are skipped)
+    int32_t clo;        // columns of this pass: [clo, clo + width)
     uint32_t width;
     SPG_DEV void any(int32_t col, typename S::In a, typename S::In b, bool valid) {
-        if (!valid || (uint32_t)(col - clo) >= width) return;
-        const int w = col >> 5;
-        // bits of word w at or below col's bit (col's own bit is set): its rank + 1
-        const int r = word_off[w] + __popc(bm[w] << (~col & 31)) - r1;
+        if (!valid) return;
+        if constexpr (kFilter) {
+            if ((uint32_t)(col - clo) >= width) return;
+        }
+        const uint2 e = bw[col >> 5];
+        // bits of the word at or below col's bit (col's own bit is set): its rank + 1
+        const int r = (int)e.y + __popc(e.x << (~col & 31)) - r1;
         S::acc(vals + r, a, b);
         cols[r] = col;
     }
@@ -723,9 +730,8 @@ __global__ void __launch_bounds__(kRankThreads, 1)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Slot* vals = reinterpret_cast<Slot*>(smem_raw);                          // [cap]
     int32_t* cols = reinterpret_cast<int32_t*>(smem_raw + rank_slot_bytes<S>(cap));   // [cap]
-    // the bitmap is filled with 16-byte copies: its offset must be 16-aligned
-    uint32_t* bm = reinterpret_cast<uint32_t*>(smem_raw + rank_region_bytes<S>(cap));
-    int32_t* word_off = reinterpret_cast<int32_t*>(bm + bm_words);           // [words + 1]
+    // filled with 16-byte stores: its offset must be 16-aligned
+    uint2* bw = reinterpret_cast<uint2*>(smem_raw + rank_region_bytes<S>(cap));   // [words + 1]
     __shared__ BatchSmem<In, kRankThreads> bs;
     __shared__ int s_row;
     __shared__ int s_wsum[kRankThreads / 32];
@@ -776,13 +782,17 @@ __global__ void __launch_bounds__(kRankThreads, 1)
         //     kept one, else rebuilt from the products
         if (cached) {
             const uint4* src = reinterpret_cast<const uint4*>(bm_cache + (int64_t)slot * cache_words);
-            uint4* dst = reinterpret_cast<uint4*>(bm);
-            for (int w = tid; w < (words + 3) / 4; w += blockDim.x) dst[w] = __ldcs(src + w);
+            uint4* dst = reinterpret_cast<uint4*>(bw);   // two (word, offset) pairs per store
+            for (int w = tid; w < (words + 3) / 4; w += blockDim.x) {
+                const uint4 v = __ldcs(src + w);
+                dst[2 * w] = make_uint4(v.x, 0u, v.y, 0u);
+                dst[2 * w + 1] = make_uint4(v.z, 0u, v.w, 0u);
+            }
             __syncthreads();
         } else {
-            for (int w = tid; w < words; w += blockDim.x) bm[w] = 0u;
+            for (int w = tid; w < words; w += blockDim.x) bw[w] = make_uint2(0u, 0u);
             __syncthreads();
-            BitSetOp op{bm};
+            BitSetOp op{bw};
             cta_range_products<In, S::kVal>(P.A, P.B, a0, a1, le, mode, sp, sp_stride, nslabs, 0,
                                             nslabs, bs, op);
         }
@@ -801,9 +811,9 @@ __global__ void __launch_bounds__(kRankThreads, 1)
             int run = 0;
             for (int j = 0; j < per_warp; j += 32) {
                 const int w = wb + j + lane;
-                const int c = w < words ? __popc(bm[w]) : 0;
+                const int c = w < words ? __popc(bw[w].x) : 0;
                 const int inc = warp_incl_scan(c);
-                if (w < words) word_off[w] = run + inc - c;
+                if (w < words) bw[w].y = (uint32_t)(run + inc - c);
                 run += __shfl_sync(kFull, inc, 31);
             }
             if (lane == 0) s_wsum[wid] = run;
@@ -812,12 +822,12 @@ __global__ void __launch_bounds__(kRankThreads, 1)
                 const int x = lane < nwarps ? s_wsum[lane] : 0;
                 const int xi = warp_incl_scan(x);
                 if (lane < nwarps) s_wsum[lane] = xi - x;
-                if (lane == 31) word_off[words] = xi;
+                if (lane == 31) bw[words].y = (uint32_t)xi;
             }
             __syncthreads();
         }
         if (g2 >= 0) slot2 = row_slot[g2];
-        const int T = word_off[words];
+        const int T = (int)bw[words].y;
         if (T != n) {   // symbolic and numeric disagree: leave the row
             if (tid == 0) flag_overflow(st, g);
             __syncthreads();
@@ -845,15 +855,15 @@ __global__ void __launch_bounds__(kRankThreads, 1)
             for (int j = 0; j < per_warp && wb + j < words; j += 32) {
                 const int w0 = wb + j;
                 const int w = w0 + lane;
-                const int lbase = word_off[w0];
-                const int lnext = (j + 32 < per_warp && w0 + 32 < words) ? word_off[w0 + 32] : wtot;
-                const int lw = w < words ? word_off[w] : 0;
+                const int lbase = (int)bw[w0].y;
+                const int lnext = (j + 32 < per_warp && w0 + 32 < words) ? (int)bw[w0 + 32].y : wtot;
+                const int lw = w < words ? (int)bw[w].y : 0;
                 __syncwarp();
-                if (w < words) word_off[w] = lw + add;
+                if (w < words) bw[w].y = (uint32_t)(lw + add);
                 if constexpr (S::kVal) continue;
                 const int Tc = lnext - lbase;
                 if (Tc == 0) continue;
-                uint32_t bits = w < words ? bm[w] : 0u;
+                uint32_t bits = w < words ? bw[w].x : 0u;
                 int pos = w < words ? lw - lbase : Tc;   // chunk-local exclusive prefix
                 const int cbase = w * 32;
                 int32_t* dst = P.c_col + off + add + lbase;
@@ -896,24 +906,26 @@ __global__ void __launch_bounds__(kRankThreads, 1)
         if constexpr (S::kVal) {
             int s0 = 0;
             while (s0 < nslabs) {
-                const int r0 = word_off[(s0 * slab_cols) >> 5];
+                const int r0 = (int)bw[(s0 * slab_cols) >> 5].y;
                 int s1 = s0 + 1;
-                while (s1 < nslabs && word_off[min((s1 + 1) * slab_cols, ncols + 31) >> 5] - r0 <= cap)
+                while (s1 < nslabs && (int)bw[min((s1 + 1) * slab_cols, ncols + 31) >> 5].y - r0 <= cap)
                     ++s1;
-                const int r1 = word_off[min(s1 * slab_cols, ncols + 31) >> 5];
+                const int r1 = (int)bw[min(s1 * slab_cols, ncols + 31) >> 5].y;
                 const int cnt = r1 - r0;
                 if (cnt > 0) {
                     const int clo = s0 * slab_cols;
                     const int chi = s1 >= nslabs ? ncols : s1 * slab_cols;
-                    RankAccOp<S> op{vals, cols, bm, word_off, r0 + 1, clo, (uint32_t)(chi - clo)};
                     // with the slab table the walk covers only the pass's slabs;
                     // without it every product is visited and filtered
-                    if (sp != nullptr || (s0 == 0 && s1 >= nslabs))
+                    if (sp != nullptr || (s0 == 0 && s1 >= nslabs)) {
+                        RankAccOp<S, false> op{vals, cols, bw, r0 + 1, clo, (uint32_t)(chi - clo)};
                         cta_range_products<In, S::kVal>(P.A, P.B, a0, a1, le, mode, sp, sp_stride,
                                                         nslabs, s0, s1, bs, op);
-                    else
+                    } else {
+                        RankAccOp<S, true> op{vals, cols, bw, r0 + 1, clo, (uint32_t)(chi - clo)};
                         cta_range_products<In, S::kVal>(P.A, P.B, a0, a1, le, mode, sp, sp_stride,
                                                         nslabs, 0, nslabs, bs, op);
+                    }
                     typename S::Out* cv = reinterpret_cast<typename S::Out*>(P.c_val) + off + r0;
                     int32_t* cc = P.c_col + off + r0;
                     for (int t = tid; t < cnt; t += blockDim.x) {
