@@ -193,7 +193,7 @@ struct BatchSmem {
 
 // All threads of the CTA call this with their own segment [beg, beg + len)
 // and A value (len 0 for none).  Ends with __syncthreads.
-template <class In, bool kVal, class Op, int NT>
+template <class In, bool kVal, class Op, int NT, int kWin = kWalkWin>
 SPG_DEV void cta_walk_segments(const DCsr& B, int64_t beg, int64_t len, In a,
                                BatchSmem<In, NT>& bs, Op& op) {
     constexpr int kBatch = NT;
@@ -242,19 +242,19 @@ SPG_DEV void cta_walk_segments(const DCsr& B, int64_t beg, int64_t len, In a,
         int64_t eend = bs.off[e + 1];
         In ea = In();
         if constexpr (kVal) ea = bs.a[e];
-        for (int64_t t0 = lo_w; t0 < hi_w; t0 += 32 * kWalkWin) {   // warp-uniform
-            int32_t col[kWalkWin];
-            In bval[kWalkWin];
-            In av[kWalkWin];
-            bool vv[kWalkWin];
-            if (eend >= t0 + 32 * kWalkWin || eend >= hi_w) {       // the pass lies in segment e
+        for (int64_t t0 = lo_w; t0 < hi_w; t0 += 32 * kWin) {   // warp-uniform
+            int32_t col[kWin];
+            In bval[kWin];
+            In av[kWin];
+            bool vv[kWin];
+            if (eend >= t0 + 32 * kWin || eend >= hi_w) {       // the pass lies in segment e
                 // one base pointer per lane; the windows are fixed offsets from it
                 const int64_t q0 = ebase + t0 + lane;
                 const int64_t left = hi_w - t0 - lane;   // products of the pass from this lane on
-                const int rem = left < 32 * kWalkWin ? (int)left : 32 * kWalkWin;
+                const int rem = left < 32 * kWin ? (int)left : 32 * kWin;
                 const int32_t* cp = B.col + q0;
 #pragma unroll
-                for (int u = 0; u < kWalkWin; ++u) {
+                for (int u = 0; u < kWin; ++u) {
                     vv[u] = 32 * u < rem;
                     col[u] = vv[u] ? __ldg(cp + 32 * u) : 0;
                     if constexpr (kVal)
@@ -263,7 +263,7 @@ SPG_DEV void cta_walk_segments(const DCsr& B, int64_t beg, int64_t len, In a,
                         bval[u] = In();
                     av[u] = ea;
                 }
-            } else if (bs.off[e + 2] >= t0 + 32 * kWalkWin || bs.off[e + 2] >= hi_w) {
+            } else if (bs.off[e + 2] >= t0 + 32 * kWin || bs.off[e + 2] >= hi_w) {
                 // one segment end inside the pass (eend < hi_w <= total, so
                 // segment e + 1 exists): products before it are segment e's,
                 // the rest segment e + 1's
@@ -271,10 +271,10 @@ SPG_DEV void cta_walk_segments(const DCsr& B, int64_t beg, int64_t len, In a,
                 In na = In();
                 if constexpr (kVal) na = bs.a[e + 1];
                 const int64_t left = hi_w - t0 - lane;
-                const int rem = left < 32 * kWalkWin ? (int)left : 32 * kWalkWin;
+                const int rem = left < 32 * kWin ? (int)left : 32 * kWin;
                 const int64_t cut = eend - t0 - lane;    // windows u with 32u >= cut are past the end
 #pragma unroll
-                for (int u = 0; u < kWalkWin; ++u) {
+                for (int u = 0; u < kWin; ++u) {
                     vv[u] = 32 * u < rem;
                     const bool second = 32 * u >= cut;
                     const int64_t q = (second ? nbase : ebase) + t0 + 32 * u + lane;
@@ -287,9 +287,9 @@ SPG_DEV void cta_walk_segments(const DCsr& B, int64_t beg, int64_t len, In a,
                 eend = bs.off[e + 1];
                 ea = na;
             } else {
-                int64_t qv[kWalkWin];
+                int64_t qv[kWin];
 #pragma unroll
-                for (int u = 0; u < kWalkWin; ++u) {
+                for (int u = 0; u < kWin; ++u) {
                     const int64_t tu = t0 + 32 * u;
                     const int64_t t = tu + lane;
                     vv[u] = t < hi_w;
@@ -315,7 +315,7 @@ SPG_DEV void cta_walk_segments(const DCsr& B, int64_t beg, int64_t len, In a,
                     if constexpr (kVal) av[u] = bs.a[me];
                     else av[u] = In();
                 }
-                const int64_t tn = t0 + 32 * kWalkWin;              // segment of the next pass
+                const int64_t tn = t0 + 32 * kWin;              // segment of the next pass
                 if (tn < hi_w) {
                     while (bs.off[e + 1] <= tn) ++e;
                 }
@@ -323,13 +323,13 @@ SPG_DEV void cta_walk_segments(const DCsr& B, int64_t beg, int64_t len, In a,
                 eend = bs.off[e + 1];
                 if constexpr (kVal) ea = bs.a[e];
 #pragma unroll
-                for (int u = 0; u < kWalkWin; ++u) {
+                for (int u = 0; u < kWin; ++u) {
                     col[u] = vv[u] ? ld_i32(B.col + qv[u]) : 0;
                     bval[u] = vv[u] ? load_val<In, kVal>(B.val, qv[u]) : In();
                 }
             }
 #pragma unroll
-            for (int u = 0; u < kWalkWin; ++u) op.any(col[u], av[u], bval[u], vv[u]);
+            for (int u = 0; u < kWin; ++u) op.any(col[u], av[u], bval[u], vv[u]);
         }
     }
     __syncthreads();
@@ -387,7 +387,7 @@ struct RowEntry {
 };
 
 // Products of row entries [a0, a1) restricted to the slab, spread over the CTA.
-template <class In, bool kVal, class Op, int NT>
+template <class In, bool kVal, class Op, int NT, int kWin = kWalkWin>
 SPG_DEV void cta_row_products(const DCsr& A, const DCsr& B, int64_t a0, int64_t a1,
                               int64_t flat_base, const Slab& slab, BatchSmem<In, NT>& bs, Op& op) {
     for (int64_t b0 = a0; b0 < a1; b0 += NT) {
@@ -395,7 +395,7 @@ SPG_DEV void cta_row_products(const DCsr& A, const DCsr& B, int64_t a0, int64_t 
         int64_t beg = 0, end = 0;
         In a = In();
         if (p < a1) entry_segment<In, kVal>(A, B, p, flat_base + (p - a0), slab, beg, end, a);
-        cta_walk_segments<In, kVal>(B, beg, end - beg, a, bs, op);
+        cta_walk_segments<In, kVal, Op, NT, kWin>(B, beg, end - beg, a, bs, op);
     }
 }
 
@@ -430,7 +430,7 @@ struct LaneEntry {
 
 // Products of the <= 32 lane entries' segments [b, e) split evenly over the
 // warps: each warp holds the whole 32-entry table in registers.
-template <class In, bool kVal, class Op>
+template <class In, bool kVal, class Op, int kWin = kWalkWin>
 SPG_DEV void warp_table_walk(const DCsr& B, int64_t b, int64_t e, In a, Op& op) {
     const int lane = lane_id(), wid = warp_id();
     const int nwarps = blockDim.x >> 5;
@@ -441,10 +441,10 @@ SPG_DEV void warp_table_walk(const DCsr& B, int64_t b, int64_t e, In a, Op& op) 
     const int64_t total = __shfl_sync(kFull, my_end, 31);
     const int64_t lo_w = total * wid / nwarps, hi_w = total * (wid + 1) / nwarps;
     int kc = 0;   // entry holding product t0 (warp-uniform, advances with t0)
-    for (int64_t t0 = lo_w; t0 < hi_w; t0 += 32 * kWalkWin) {   // warp-uniform
-        int64_t qv[kWalkWin];
-        In av[kWalkWin];
-        bool vv[kWalkWin];
+    for (int64_t t0 = lo_w; t0 < hi_w; t0 += 32 * kWin) {   // warp-uniform
+        int64_t qv[kWin];
+        In av[kWin];
+        bool vv[kWin];
         // entries whose products all precede t0 (ends are non-decreasing)
         kc = __popc(__ballot_sync(kFull, my_end <= t0));
         if (kc > 31) kc = 31;
@@ -453,25 +453,25 @@ SPG_DEV void warp_table_walk(const DCsr& B, int64_t b, int64_t e, In a, Op& op) 
         const unsigned later = __ballot_sync(kFull, my_end > endk);
         const int kn = later ? __ffs(later) - 1 : 31;
         const int64_t endn = __shfl_sync(kFull, my_end, kn);
-        if (t0 + 32 * kWalkWin <= endk && t0 + 32 * kWalkWin <= hi_w) {
+        if (t0 + 32 * kWin <= endk && t0 + 32 * kWin <= hi_w) {
             // the window lies in one segment (the common case for hub rows of
             // B): addresses without a per-lane search
             const int64_t base = __shfl_sync(kFull, qbase, kc);
             const In ak = shfl_val<In, kVal>(a, kc);
 #pragma unroll
-            for (int u = 0; u < kWalkWin; ++u) {
+            for (int u = 0; u < kWin; ++u) {
                 qv[u] = base + t0 + 32 * u + lane;
                 av[u] = ak;
                 vv[u] = true;
             }
-        } else if (later && (endn >= t0 + 32 * kWalkWin || endn >= hi_w)) {
+        } else if (later && (endn >= t0 + 32 * kWin || endn >= hi_w)) {
             // one segment end inside the pass: entry kc before it, entry kn after
             const int64_t base = __shfl_sync(kFull, qbase, kc);
             const int64_t nbase = __shfl_sync(kFull, qbase, kn);
             const In ak = shfl_val<In, kVal>(a, kc);
             const In an = shfl_val<In, kVal>(a, kn);
 #pragma unroll
-            for (int u = 0; u < kWalkWin; ++u) {
+            for (int u = 0; u < kWin; ++u) {
                 const int64_t t = t0 + 32 * u + lane;
                 vv[u] = t < hi_w;
                 const bool second = t >= endk;
@@ -480,7 +480,7 @@ SPG_DEV void warp_table_walk(const DCsr& B, int64_t b, int64_t e, In a, Op& op) 
             }
         } else {
 #pragma unroll
-            for (int u = 0; u < kWalkWin; ++u) {
+            for (int u = 0; u < kWin; ++u) {
                 const int64_t tu = t0 + 32 * u, t = tu + lane;
                 vv[u] = t < hi_w;
                 // prefix ends relative to the pass start (clamped to 32 bits:
@@ -497,15 +497,15 @@ SPG_DEV void warp_table_walk(const DCsr& B, int64_t b, int64_t e, In a, Op& op) 
                 av[u] = shfl_val<In, kVal>(a, k);
             }
         }
-        int32_t col[kWalkWin];
-        In bval[kWalkWin];
+        int32_t col[kWin];
+        In bval[kWin];
 #pragma unroll
-        for (int u = 0; u < kWalkWin; ++u) {
+        for (int u = 0; u < kWin; ++u) {
             col[u] = vv[u] ? ld_i32(B.col + qv[u]) : 0;
             bval[u] = vv[u] ? load_val<In, kVal>(B.val, qv[u]) : In();
         }
 #pragma unroll
-        for (int u = 0; u < kWalkWin; ++u) op.any(col[u], av[u], bval[u], vv[u]);
+        for (int u = 0; u < kWin; ++u) op.any(col[u], av[u], bval[u], vv[u]);
     }
 }
 
