@@ -39,6 +39,10 @@ TIERS = {
                       num_block_max_nnz=1),
     "dense_small_slabs": dict(sym_warp_max_ub=1, sym_block_max_ub=1, num_warp_max_nnz=1,
                               num_block_max_nnz=1, dense_slab_cols=1024, sym_slab_cols=1024),
+    # dense tiers without the symbolic phase's bitmap cache: the rank kernel
+    # rebuilds every row's bitmap from its products
+    "dense_rebuild": dict(sym_warp_max_ub=1, sym_block_max_ub=1, num_warp_max_nnz=1,
+                          num_block_max_nnz=1, bitmap_cache_bytes=1),
 }
 
 
@@ -210,3 +214,33 @@ def test_repeated_calls_same_handle_and_workspace():
     r1 = api.to_host(api.spgemm(api.MIN_PLUS_F32, dA, dA, handle=h, ws=ws), api.MIN_PLUS_F32)
     r2 = api.to_host(api.spgemm(api.MIN_PLUS_F32, dA, dA, handle=h, ws=ws), api.MIN_PLUS_F32)
     assert np.array_equal(r1.col, r2.col) and np.array_equal(r1.val, r2.val)
+
+
+def entry_mode_rows(seed):
+    """Rows of 32, 33, 1024, 1025 and 3000 entries (and an empty one) over B rows
+    of 24 random columns out of 120,000: the dense tier's row-entry modes (one
+    entry per lane, per thread, batched) and, for the long rows, more outputs
+    than one value pass holds."""
+    rng = np.random.default_rng(seed)
+    degs = [32, 33, 1024, 1025, 3000, 0]
+    K, N, per_b = 4000, 120_000, 24
+    a_rows = np.repeat(np.arange(len(degs)), degs)
+    a_cols = np.concatenate([np.sort(rng.choice(K, d, replace=False)) for d in degs if d])
+    A = I._from_sorted_coo(len(degs), K, a_rows, a_cols, None)
+    b_rows = np.repeat(np.arange(K), per_b)
+    b_cols = np.concatenate([np.sort(rng.choice(N, per_b, replace=False)) for _ in range(K)])
+    B = I._from_sorted_coo(K, N, b_rows, b_cols, None)
+    return A, B
+
+
+@pytest.mark.parametrize("tier", ["default", "all_dense", "dense_rebuild"])
+@pytest.mark.parametrize("sr", [api.MIN_PLUS_F32, api.PLUS_TIMES_F64, api.BOOL_OR_AND,
+                                api.OVERLAP_I32])
+def test_dense_row_entry_modes_and_value_passes(sr, tier):
+    A, B = entry_mode_rows(11)
+    A = values_for(sr, A, 12)
+    B = values_for(sr, B, 13)
+    got, h = check(sr, A, B, TIERS[tier], tier)
+    # the 3000-entry row has more outputs than one value pass of the rank
+    # kernel holds (about 18K at 8 bytes per output)
+    assert got.rp[5] - got.rp[4] > 40_000
