@@ -15,7 +15,7 @@ from __future__ import annotations
 import json
 import os
 import statistics
-from typing import Dict, Optional
+from typing import Callable, Dict, Optional
 
 from . import spgemm as api
 
@@ -70,12 +70,21 @@ def tune(sr: int, dA: api.DeviceCSR, dB: api.DeviceCSR, reps: int = 3, sweeps: i
         _time_call(hh, sr, dA, dB, ws, c_rp, c_col, c_val, 1)   # warm-up
         return _time_call(hh, sr, dA, dB, ws, c_rp, c_col, c_val, reps)
 
+    return descend(measure, SPACE, best, sweeps, log)
+
+
+def descend(measure: Callable[[Dict[str, int]], float], space: Dict[str, list],
+            start: Dict[str, int], sweeps: int = 2, log=None) -> Dict[str, int]:
+    """Coordinate descent: every field of ``space`` in turn is tried at each
+    candidate value with the others fixed; a value is kept when it beats the
+    best time by more than 1%.  Sweeps repeat until one improves nothing."""
+    best = dict(start)
     best_t = measure(best)
     if log:
         log(f"start {best} {best_t:.3f} ms")
     for _ in range(sweeps):
         improved = False
-        for field, cands in SPACE.items():
+        for field, cands in space.items():
             for v in cands:
                 if best.get(field) == v:
                     continue
@@ -92,20 +101,24 @@ def tune(sr: int, dA: api.DeviceCSR, dB: api.DeviceCSR, reps: int = 3, sweeps: i
     return best
 
 
-def cache_key(sr: int, tag: str) -> str:
-    import torch
-    return f"{torch.cuda.get_device_name()}|{api.SEMIRING_NAMES[sr]}|{tag}"
+def cache_key(sr: int, tag: str, device: Optional[str] = None) -> str:
+    if device is None:
+        import torch
+        device = torch.cuda.get_device_name()
+    return f"{device}|{api.SEMIRING_NAMES[sr]}|{tag}"
 
 
-def load(sr: int, tag: str, path: str = DEFAULT_CACHE) -> Optional[Dict[str, int]]:
+def load(sr: int, tag: str, path: str = DEFAULT_CACHE,
+         device: Optional[str] = None) -> Optional[Dict[str, int]]:
     try:
         with open(path) as f:
-            return json.load(f).get(cache_key(sr, tag))
+            return json.load(f).get(cache_key(sr, tag, device))
     except (OSError, ValueError):
         return None
 
 
-def save(sr: int, tag: str, tuning: Dict[str, int], path: str = DEFAULT_CACHE) -> None:
+def save(sr: int, tag: str, tuning: Dict[str, int], path: str = DEFAULT_CACHE,
+         device: Optional[str] = None) -> None:
     os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
     data = {}
     try:
@@ -113,7 +126,7 @@ def save(sr: int, tag: str, tuning: Dict[str, int], path: str = DEFAULT_CACHE) -
             data = json.load(f)
     except (OSError, ValueError):
         pass
-    data[cache_key(sr, tag)] = tuning
+    data[cache_key(sr, tag, device)] = tuning
     tmp = path + ".tmp"
     with open(tmp, "w") as f:
         json.dump(data, f, indent=1, sort_keys=True)
