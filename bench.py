@@ -471,6 +471,8 @@ def main():
 
     # whole-step fraction of the HBM roofline by the same model
     t_alg_all = (16 * A.nrows + A.nnz * (8 + 8) + P * 8 + nnz * 8)
+    # compulsory bytes: A and B read once, C written once (B = A, counted twice)
+    t_min = 2 * (8 * (A.nrows + 1) + A.nnz * 8) + 8 * (A.nrows + 1) + nnz * 8
 
     # e2e through the host-memory C ABI call: H2D of A, D2H of C every step
     e2e = None
@@ -543,6 +545,7 @@ def main():
                "config": dict(workload_config(P=P, nnz_c=nnz, nnz_a=A.nnz, scale=args.scale),
                               parallelism=f"replicas x{world}"),
                "hbm_roofline_frac_step": (t_alg_all / (ms_per_step * 1e-3) / 1e9) / peak,
+               "hbm_compulsory_frac_step": (t_min / (ms_per_step * 1e-3) / 1e9) / peak,
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                "clocks": sampler.summary(), "gpu_launches": launches,
                "step_ms": times, "forms": forms}
