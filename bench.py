@@ -75,6 +75,18 @@ def max_over_ranks(x: float, dist=None, device="cuda") -> float:
     return float(t.item())
 
 
+def host_mem_available():
+    """MemAvailable of this node in bytes (None where /proc/meminfo is missing)."""
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except (OSError, ValueError, IndexError):
+        pass
+    return None
+
+
 def job_throughput(total_ms: float, steps: int, products_per_rank: int, world: int, dist=None,
                    device="cuda"):
     """(ms per step, GFLOPS) of the whole job: every rank runs the same product
@@ -476,7 +488,19 @@ def main():
 
     # e2e through the host-memory C ABI call: H2D of A, D2H of C every step
     e2e = None
-    if args.e2e_steps > 0:
+    run_e2e = args.e2e_steps > 0
+    if run_e2e:
+        # with several ranks, every rank of the node pins A and all of C on the
+        # host at once; with too little host memory for that the e2e leg is
+        # left out on every rank
+        need = world * (A.nnz * 16 + nnz * 8 + (A.nrows + 1) * 16)
+        avail = host_mem_available()
+        short = 1.0 if (world > 1 and avail is not None and need > 0.9 * avail) else 0.0
+        run_e2e = max_over_ranks(short, dist) == 0.0
+        if not run_e2e and rank == 0:
+            print(f"e2e left out: {world} ranks need {need / 1e9:.0f} GB of pinned host memory, "
+                  f"{(avail or 0) / 1e9:.0f} GB available", file=sys.stderr, flush=True)
+    if run_e2e:
         pin = lambda n, dt: torch.empty(n, dtype=dt, pin_memory=True).numpy()
         hA = I.CSR(A.nrows, A.ncols, pin(A.nrows + 1, torch.int64), pin(A.nnz, torch.int32),
                    pin(A.nnz, torch.float32))
