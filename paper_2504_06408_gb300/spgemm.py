@@ -236,8 +236,13 @@ class Handle:
             raise SpgemmError(st, msg)
 
     def set_tuning(self, **kw):
+        """Set spg_tuning fields by name (0 = library default); an unknown
+        name raises instead of being ignored."""
         t = spg_tuning()
+        known = {name for name, _ in spg_tuning._fields_}
         for k, v in kw.items():
+            if k not in known or k == "reserved":
+                raise ValueError(f"unknown tuning field {k!r} (known: {sorted(known - {'reserved'})})")
             setattr(t, k, int(v))
         self._ok(self.lib.spgemm_set_tuning(self._h, ctypes.byref(t)))
 

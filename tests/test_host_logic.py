@@ -1,6 +1,6 @@
 """Host-side logic that needs no GPU: the autotuner's coordinate descent and
-cache, the SUMMA grid cuts, the association of iterated products, and the
-sizing network's weight-file format."""
+cache, the SUMMA grid cuts, the association of iterated products, the
+sizing network's weight-file format, and the binding's tuning fields."""
 import hashlib
 import json
 
@@ -159,3 +159,23 @@ def test_weight_file_header_and_hash_check(tmp_path):
     open(stem + ".bin", "wb").write(bytes(bad))
     with pytest.raises(ValueError):
         learned.load(stem, device="cpu")
+
+
+# ---- binding ------------------------------------------------------------------------
+
+def test_set_tuning_rejects_unknown_fields():
+    import ctypes
+
+    class FakeLib:
+        def spgemm_set_tuning(self, h, t):
+            self.t = t._obj
+            return 0
+
+    h = api.Handle.__new__(api.Handle)
+    h.lib, h._h = FakeLib(), ctypes.c_void_p()
+    h.set_tuning(num_block_max_nnz=4096, deterministic=1)
+    assert h.lib.t.num_block_max_nnz == 4096 and h.lib.t.deterministic == 1
+    with pytest.raises(ValueError):
+        h.set_tuning(num_block_max=4096)      # a misspelt field is not ignored
+    with pytest.raises(ValueError):
+        h.set_tuning(reserved=1)
