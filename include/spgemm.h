@@ -118,14 +118,18 @@ typedef struct {
 typedef struct spg_handle spg_handle;
 
 /* Create / destroy a handle (holds tuning, the current device's properties and
- * the last error text).  A handle is used by one host thread at a time. */
+ * the last error text).  A handle is used by one host thread at a time.
+ * Library services with no counterpart in the paper.  Errors: SPG_ERR_INVALID_ARG
+ * (NULL pointer), SPG_ERR_CUDA (no usable device for spgemm_create). */
 spg_status spgemm_create(spg_handle** handle);
 spg_status spgemm_destroy(spg_handle* handle);
 
 /* Text of the last error on this handle ("" if none).  Owned by the handle. */
 const char* spgemm_last_error(const spg_handle* handle);
 
-/* Tier limits (see spg_tuning).  They change speed only, never C. */
+/* Tier limits (see spg_tuning).  They change speed only, never C (the
+ * paper's GALATIC configuration knobs, Section 3.3, play this role there).
+ * Counters (spg_stats) of the last call.  Errors: SPG_ERR_INVALID_ARG. */
 spg_status spgemm_set_tuning(spg_handle* handle, const spg_tuning* tuning);
 spg_status spgemm_get_tuning(const spg_handle* handle, spg_tuning* tuning);
 spg_status spgemm_get_stats(const spg_handle* handle, spg_stats* stats);
@@ -133,7 +137,9 @@ spg_status spgemm_get_stats(const spg_handle* handle, spg_stats* stats);
 /*
  * Bytes of device workspace needed by spgemm_symbolic + spgemm_numeric for
  * these shapes (only nrows, ncols and nnz of A and B are read).  The same
- * workspace must be passed to both calls, unchanged in between.
+ * workspace must be passed to both calls, unchanged in between; the caller
+ * owns it.  Errors: SPG_ERR_INVALID_ARG (shapes, B.nrows != A.ncols),
+ * SPG_ERR_UNSUPPORTED (beyond the index range).
  */
 spg_status spgemm_workspace_size(spg_handle* handle, spg_semiring sr, const spg_csr* A,
                                  const spg_csr* B, size_t* bytes);
@@ -150,7 +156,8 @@ spg_status spgemm_symbolic(spg_handle* handle, spg_semiring sr, const spg_csr* A
                            void* workspace, size_t workspace_bytes, void* stream);
 
 /*
- * Numeric phase: accumulates every product with the semiring and writes each
+ * Numeric phase (Section 2.1 definition, with the (x) and (+) of the semiring,
+ * Section 2.2): accumulates every product with the semiring and writes each
  * row sorted by column.  Requires the c_row_ptr and workspace of the
  * spgemm_symbolic call for the same A and B (values of A and B may differ
  * from that call; patterns may not).
