@@ -96,6 +96,26 @@ def job_throughput(total_ms: float, steps: int, products_per_rank: int, world: i
     return ms, world * 2.0 * products_per_rank / (ms * 1e-3) / 1e9
 
 
+def host_placement():
+    """CPU affinity of this process and the NUMA node of the current GPU (the
+    host memory the e2e copies land in is placed by first touch)."""
+    info = {}
+    try:
+        info["cpus"] = len(os.sched_getaffinity(0))
+    except Exception:
+        pass
+    try:
+        import torch
+        p = torch.cuda.get_device_properties(torch.cuda.current_device())
+        bus = "%04x:%02x:%02x.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+        info["gpu_pci"] = bus
+        with open(f"/sys/bus/pci/devices/{bus}/numa_node") as f:
+            info["gpu_numa_node"] = int(f.read().strip())
+    except Exception:
+        pass
+    return info
+
+
 def dist_info():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -250,15 +270,39 @@ def _time_ms(fn, reps, flush):
     return statistics.median(ts)
 
 
+def same_result(ref_col, ref_val, col, val):
+    """(same pattern, same values) of two device results with the same row
+    pointers: columns bit-exact; values bit-exact (every semiring but the
+    floating plus-times ones, whose atomic summation order is free) or, for
+    those, max |got - ref| / |ref| (the inputs here are non-negative, so
+    |ref| = sum |a b| and the parity bound is 1e-12)."""
+    import torch
+    same_col = bool(torch.equal(ref_col, col))
+    if ref_val is None:
+        return same_col, True, 0.0
+    if ref_val.dtype in (torch.float64, torch.float32):
+        exact = bool(torch.equal(ref_val.view(torch.uint8), val.view(torch.uint8)))
+        if exact:
+            return same_col, True, 0.0
+        den = ref_val.abs().clamp_min(torch.finfo(ref_val.dtype).tiny)
+        rel = float(((val - ref_val).abs() / den).max().item())
+        return same_col, rel <= 1e-12, rel
+    return same_col, bool(torch.equal(ref_val, val)), 0.0
+
+
 def learned_forms(api, h, sr, dA, dB, flush, reps, plain_ms, params, meta):
     """plain vs learned (ub-sized capacities) vs learned (trained network) on
-    one product; every form gives the same C (checked on nnz and row pointers
-    here, element by element in the tests)."""
+    one product; every form's C is compared with the plain C on the device,
+    column by column and value by value (same_result)."""
     import torch
     out = {"plain_ms": plain_ms}
     ref_rp = torch.empty(dA.nrows + 1, dtype=torch.int64, device="cuda")
     ws0 = torch.empty(h.workspace_size(sr, dA, dB), dtype=torch.uint8, device="cuda")
     nnz = h.symbolic(sr, dA, dB, ref_rp, ws0)
+    ref_col = torch.empty(max(nnz, 1), dtype=torch.int32, device="cuda")
+    ref_val = api.out_tensor(sr, max(nnz, 1))
+    h.numeric(sr, dA, dB, ref_rp, ref_col, ref_val, ws0)
+    h.check(ws0)
     del ws0
     c_col = torch.empty(max(nnz, 1), dtype=torch.int32, device="cuda")
     c_val = api.out_tensor(sr, max(nnz, 1))
@@ -279,16 +323,20 @@ def learned_forms(api, h, sr, dA, dB, flush, reps, plain_ms, params, meta):
         st = h.stats()
         h.check(lws)
         same = bool(torch.equal(c_rp, ref_rp)) and st["nnz_c"] == nnz
+        same_col, same_val, rel = same_result(ref_col, ref_val, c_col, c_val)
         out[name] = {"ms": ms, "speedup_vs_plain": plain_ms / ms, "same_row_ptr": same,
+                     "same_columns": same_col, "same_values": same_val, "max_rel_diff": rel,
                      "learned_rows": st["learned_rows"], "overflow_rows": st["overflow_rows"],
                      "staging_entries": st["staging_entries"],
                      "staging_per_entry": st["staging_entries"] / max(st["learned_nnz"], 1)}
         del staging
     out["rows"] = dA.nrows
+    del ref_col, ref_val, c_col, c_val
     return out
 
 
-def plain_ms_of(api, h, sr, dA, dB, flush, reps):
+def plain_ms_of(api, h, sr, dA, dB, flush, reps, keep=False):
+    """Median ms of symbolic + numeric, nnz(C) and (keep) C = (rp, col, val)."""
     import torch
     ws = torch.empty(h.workspace_size(sr, dA, dB), dtype=torch.uint8, device="cuda")
     c_rp = torch.empty(dA.nrows + 1, dtype=torch.int64, device="cuda")
@@ -300,12 +348,49 @@ def plain_ms_of(api, h, sr, dA, dB, flush, reps):
         h.symbolic(sr, dA, dB, c_rp, ws)
         h.numeric(sr, dA, dB, c_rp, c_col, c_val, ws)
 
-    return _time_ms(step, reps, flush), nnz
+    ms = _time_ms(step, reps, flush)
+    h.check(ws)
+    if keep:
+        return ms, nnz, (c_rp, c_col[:nnz], None if c_val is None else c_val[:nnz])
+    return ms, nnz
 
 
-def summa_forms(api, Summa, h, sr, dA, flush, reps):
+def block_matches(ref, r0, r1, c0, c1, blk, chunk=1 << 27):
+    """(same pattern, max rel value diff) of C block [r0, r1) x [c0, c1) (local
+    column ids) against the same block cut out of the unblocked C, on the
+    device, a chunk of rows at a time."""
+    import torch
+    rp, col, val = ref
+    brp, bcol, bval = blk.rp, blk.col, blk.val
+    rph = rp[r0:r1 + 1].cpu()
+    ok, worst, x0 = True, 0.0, r0
+    while x0 < r1:
+        x1 = int(torch.searchsorted(rph, rph[x0 - r0] + chunk, right=True).item()) - 1 + r0
+        x1 = min(max(x1, x0 + 1), r1)
+        a, b = int(rph[x0 - r0]), int(rph[x1 - r0])
+        cc = col[a:b]
+        m = (cc >= c0) & (cc < c1)
+        rows = torch.repeat_interleave(torch.arange(x1 - x0, device=cc.device, dtype=torch.int32),
+                                       (rp[x0 + 1:x1 + 1] - rp[x0:x1]))
+        cnt = torch.bincount(rows[m], minlength=x1 - x0)
+        ba, bb = int(brp[x0 - r0].item()), int(brp[x1 - r0].item())
+        ok &= bool(torch.equal(brp[x0 - r0 + 1:x1 - r0 + 1] - brp[x0 - r0:x1 - r0], cnt))
+        ok &= bb - ba == int(m.sum().item()) and bool(torch.equal(bcol[ba:bb], cc[m] - c0))
+        if ok and val is not None:
+            ev = val[a:b][m]
+            gv = bval[ba:bb]
+            den = ev.abs().clamp_min(torch.finfo(ev.dtype).tiny)
+            if ev.numel():
+                worst = max(worst, float(((gv - ev).abs() / den).max().item()))
+        x0 = x1
+    return ok, worst
+
+
+def summa_forms(api, Summa, h, sr, dA, flush, reps, ref=None):
     """4 x 4 Sparse-SUMMA block grid: one batched launch per phase (and a CUDA
-    graph of numeric + merge) against one call per block product and merge."""
+    graph of numeric + merge) against one call per block product and merge.
+    With ref (the unblocked C), every C block of every form is compared with
+    the same block of the unblocked product."""
     import torch
     out = {}
     for batched in (True, False):
@@ -330,6 +415,18 @@ def summa_forms(api, Summa, h, sr, dA, flush, reps):
             out["unbatched_numeric_merge_ms"] = _time_ms(numeric_merge, reps, flush)
         out[f"{key}_nnz_c"] = int(sum(sm.c_nnz))
         out["partial_entries"] = int(sum(sm.p_nnz))
+        if ref is not None:
+            sm.check()
+            same, worst = True, 0.0
+            for I_ in range(sm.q):
+                for J_ in range(sm.q):
+                    ok, w = block_matches(ref, sm.row_cuts[I_], sm.row_cuts[I_ + 1],
+                                          sm.col_cuts[J_], sm.col_cuts[J_ + 1], sm.block(I_, J_))
+                    same &= ok
+                    worst = max(worst, w)
+            out[f"{key}_same_pattern_as_unblocked"] = same
+            out[f"{key}_max_rel_diff_vs_unblocked"] = worst
+            out[f"{key}_within_1e-12"] = same and worst <= 1e-12
         del sm
         torch.cuda.empty_cache()
     out["speedup_full"] = out["unbatched_full_ms"] / out["batched_full_ms"]
@@ -338,12 +435,139 @@ def summa_forms(api, Summa, h, sr, dA, flush, reps):
     return out
 
 
-def run_reference(args, rank):
-    """Reference arm: the CPU oracle on a bounded row sample per step."""
-    if rank != 0:
-        return 0
+def t_alg_bytes(n, nnz_a, P, nnz_c, s_in, s_out):
+    """Gustavson traffic model: row pointers of A and C, A's entries and the
+    B row-pointer gathers, every product's B entry, C's entries."""
+    return 8 * (n + 1) + nnz_a * (4 + s_in) + 8 * nnz_a + P * (4 + s_in) + 8 * (n + 1) + \
+        nnz_c * (4 + s_out)
+
+
+def bool_form(api, h, A, flush, reps, peak):
+    """C = A A over the boolean semiring (pattern only) on the headline graph."""
+    import torch
+    dAb = api.DeviceCSR.from_host(A.with_values(None))
+    ms, nnz = plain_ms_of(api, h, api.BOOL_OR_AND, dAb, dAb, flush, reps)
+    P = h.stats()["products"]
+    t = t_alg_bytes(A.nrows, A.nnz, P, nnz, 0, 0)
+    del dAb
+    torch.cuda.empty_cache()
+    return {"ms": ms, "gflops": 2.0 * P / (ms * 1e-3) / 1e9, "products": P, "nnz_c": nnz,
+            "algorithmic_bytes": t, "hbm_roofline_frac_step": t / (ms * 1e-3) / 1e9 / peak}
+
+
+def er_forms(api, h, flush, reps=21):
+    """Erdos-Renyi 4096 x 4096, 8 entries per row, A A over plus-times FP64 and
+    boolean: latency-bound, reported in microseconds (median of 21)."""
+    from paper_2504_06408_gb300 import inputs as I
+    E = I.er(4096, 8, seed=1)
+    out = {}
+    for name, sr, dt in (("plus_times_f64", api.PLUS_TIMES_F64, np.float64),
+                         ("bool", api.BOOL_OR_AND, None)):
+        dE = api.DeviceCSR.from_host(E if dt else E.with_values(None), val_dtype=dt)
+        ms, nnz = plain_ms_of(api, h, sr, dE, dE, flush, reps)
+        P = h.stats()["products"]
+        out[name] = {"us": 1e3 * ms, "gflops": 2.0 * P / (ms * 1e-3) / 1e9, "products": P,
+                     "nnz_c": nnz}
+    return out
+
+
+def kmer_form(api, h, flush, reps, peak):
+    """k-mer overlap product C = A A^T (200,000 reads x 2^24 k-mers, overlap
+    semiring, int32 positions); A^T by the library's transpose (untimed)."""
+    import torch
+    from paper_2504_06408_gb300 import inputs as I
+    A = I.kmer(seed=1)
+    dA = api.DeviceCSR.from_host(A, val_dtype=np.int32)
+    dAt = h.transpose(dA, 4)
+    ms, nnz = plain_ms_of(api, h, api.OVERLAP_I32, dA, dAt, flush, reps)
+    P = h.stats()["products"]
+    t = t_alg_bytes(A.nrows, A.nnz, P, nnz, 4, 20)
+    del dA, dAt
+    torch.cuda.empty_cache()
+    return {"ms": ms, "gflops": 2.0 * P / (ms * 1e-3) / 1e9, "products": P, "nnz_c": nnz,
+            "algorithmic_bytes": t, "hbm_roofline_frac": t / (ms * 1e-3) / 1e9 / peak}
+
+
+# Stand-ins shaped like the paper's Table 2 matrices, multiplied over the
+# plus-times "float" semiring as in its experiments
+FLOAT_STANDINS = {
+    "rmat_16_ef4": "R-MAT scale 16, edge factor 4 (65,536 rows, 494,224 entries; Table 2 rmat: "
+                   "65,536 rows, 490,228)",
+    "stencil7_108": "3D 7-point stencil on 108^3 (1,259,712 rows, 8,748,000 entries; atmosmodd: "
+                    "1,270,432 rows, 8,814,880)",
+    "trigrid_2048": "triangular lattice 2048^2, 6 neighbours (4,194,304 rows, 25,149,442 "
+                    "entries; delaunay_n22: 4,194,304 rows, 25,165,738)",
+    "stencil27_114": "3D 27-point stencil on 114^3 (1,481,544 rows; Long_dt_Coup0: 1,470,152 "
+                     "rows, 70,219,816 entries, denser rows)",
+}
+
+
+def float_standin(name):
+    from paper_2504_06408_gb300 import inputs as I
+    if name == "rmat_16_ef4":
+        return I.rmat(16, edge_factor=4, seed=1, dtype=np.float32)
+    if name == "stencil7_108":
+        return I.stencil3d(108, 7)
+    if name == "trigrid_2048":
+        return I.trigrid(2048)
+    return I.stencil3d(114, 27)
+
+
+def cold_warm_one(name):
+    """First multiplication in a fresh process (lazy kernel loading, workspace
+    and output allocation included: the paper's first-iteration time) against
+    the median of 5 warm ones on preallocated buffers; plus-times FP32."""
+    import torch
     import __graft_entry__
     __graft_entry__.build()
+    from paper_2504_06408_gb300 import spgemm as api
+    A = float_standin(name)
+    dA = api.DeviceCSR.from_host(A, val_dtype=np.float32)
+    torch.cuda.synchronize()
+    sr = api.PLUS_TIMES_F32
+    t0 = time.perf_counter()
+    h = api.Handle()
+    C = api.spgemm(sr, dA, dA, handle=h)
+    torch.cuda.synchronize()
+    cold = 1e3 * (time.perf_counter() - t0)
+    P = h.stats()["products"]
+    ws = torch.empty(h.workspace_size(sr, dA, dA), dtype=torch.uint8, device="cuda")
+    ts = []
+    for _ in range(5):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h.symbolic(sr, dA, dA, C.rp, ws)
+        h.numeric(sr, dA, dA, C.rp, C.col, C.val, ws)
+        torch.cuda.synchronize()
+        ts.append(1e3 * (time.perf_counter() - t0))
+    return {"cold_ms": cold, "warm_ms": statistics.median(ts), "nrows": A.nrows, "nnz": A.nnz,
+            "products": P, "nnz_c": C.nnz}
+
+
+def cold_warm_forms():
+    """cold_warm_one for every stand-in, each in its own process."""
+    out = {"note": "plus-times FP32; cold = first call in a fresh process (host wall clock, "
+                   "kernel loading and allocations included), warm = median of 5 later "
+                   "calls (host wall clock)"}
+    for name, what in FLOAT_STANDINS.items():
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cold-warm", name],
+                           capture_output=True, text=True)
+        try:
+            res = json.loads(r.stdout.strip().splitlines()[-1])
+        except Exception:
+            res = {"error": (r.stderr or r.stdout)[-300:]}
+        res["matrix"] = what
+        out[name] = res
+    return out
+
+
+def run_reference(args, rank):
+    """Reference arm: the CPU oracle on a bounded row sample per step.  Only
+    the oracle is built and loaded here, never the CUDA library."""
+    if rank != 0:
+        return 0
+    import oracle.build as _ob
+    _ob.build()
     import oracle
     from paper_2504_06408_gb300 import inputs as I
     A = I.rmat(SCALE, dtype=np.float32, seed=1)
@@ -388,7 +612,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cold-warm", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the learned / batched vs plain comparisons")
@@ -400,6 +625,9 @@ def main():
     world, rank, local = dist_info()
     if args.impl == "reference":
         return run_reference(args, rank)
+    if args.cold_warm:
+        print(json.dumps(cold_warm_one(args.cold_warm)), flush=True)
+        return 0
 
     import torch
     import __graft_entry__
@@ -501,7 +729,12 @@ def main():
             print(f"e2e left out: {world} ranks need {need / 1e9:.0f} GB of pinned host memory, "
                   f"{(avail or 0) / 1e9:.0f} GB available", file=sys.stderr, flush=True)
     if run_e2e:
-        pin = lambda n, dt: torch.empty(n, dtype=dt, pin_memory=True).numpy()
+        pinned = []
+
+        def pin(n, dt):
+            t = torch.empty(n, dtype=dt, pin_memory=True)
+            pinned.append(t)
+            return t.numpy()
         hA = I.CSR(A.nrows, A.ncols, pin(A.nrows + 1, torch.int64), pin(A.nnz, torch.int32),
                    pin(A.nnz, torch.float32))
         hA.rp[:] = A.rp
@@ -509,6 +742,9 @@ def main():
         hA.val[:] = A.val
         out = {"rp": pin(A.nrows + 1, torch.int64), "col": pin(nnz, torch.int32),
                "val": pin(nnz * 4, torch.uint8)}
+        # first touch of the output pages outside the timed region
+        out["col"][::1024] = 0
+        out["val"][::4096] = 0
         h2 = api.Handle()
         h2.host_multiply(sr, hA, hA, out=out)         # warm-up (device buffers allocated)
         et = []
@@ -521,9 +757,22 @@ def main():
         e_s = max_over_ranks(statistics.mean(et), dist)
         h2d = (A.nrows + 1) * 8 + A.nnz * 8
         d2h = (A.nrows + 1) * 8 + nnz * 8
+        # the same run's device-to-host bandwidth into the same pinned buffers
+        # (C's columns and values from the device step): the e2e floor
+        t_col, t_val = pinned[-2], pinned[-1]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        t_col.copy_(c_col, non_blocking=True)
+        t_val.copy_(c_val.view(torch.uint8), non_blocking=True)
+        torch.cuda.synchronize()
+        d2h_s = time.perf_counter() - t0
+        d2h_gbs = nnz * 8 / d2h_s / 1e9
         e2e = {"value": world * 2.0 * P / e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e_s}
-        del h2
+               "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e_s, "steps": len(et),
+               "step_ms": [1e3 * x for x in et],
+               "d2h_gbs_same_run": d2h_gbs, "d2h_floor_ms": 1e3 * d2h / (d2h_gbs * 1e9),
+               "host": host_placement()}
+        del h2, pinned, hA, out
 
     forms = None
     if not args.no_forms:
@@ -532,12 +781,19 @@ def main():
         params, meta = L.load()
         reps = args.form_reps
         forms = {"note": "median of %d CUDA-event timings per form, L2 flushed before each; "
-                         "every form gives the same C; plain_ms of the headline workload = "
-                         "ms_per_step" % reps}
+                         "each form's C is compared with the plain C on the device "
+                         "(same_* keys); plain_ms of the headline workload = ms_per_step"
+                         % reps}
         del c_col, c_val, step
         torch.cuda.empty_cache()
-        forms[f"rmat{args.scale}_min_plus"] = learned_forms(api, h, sr, dA, dA, flush, reps, ms_per_step,
-                                                 params, meta)
+        forms[f"rmat{args.scale}_min_plus"] = learned_forms(api, h, sr, dA, dA, flush, reps,
+                                                            ms_per_step, params, meta)
+        torch.cuda.empty_cache()
+        forms[f"rmat{args.scale}_bool"] = bool_form(api, h, A, flush, reps, peak)
+        del dA
+        torch.cuda.empty_cache()
+        forms["er4096"] = er_forms(api, h, flush)
+        forms["kmer_overlap"] = kmer_form(api, h, flush, reps, peak)
         torch.cuda.empty_cache()
         lap = I.laplacian(2048)
         dL = api.DeviceCSR.from_host(lap, val_dtype=np.float64)
@@ -546,15 +802,16 @@ def main():
             api, h, api.PLUS_TIMES_F64, dL, dL, flush, reps, pms, params, meta)
         del dL
         torch.cuda.empty_cache()
-        A64 = I.rmat(args.scale, dtype=np.float64, seed=1)
+        A64 = I.rmat(args.scale, dtype=np.float64, seed=1, lo=0.0, hi=1.0)
         dA64 = api.DeviceCSR.from_host(A64, val_dtype=np.float64)
-        pms, _ = plain_ms_of(api, h, api.PLUS_TIMES_F64, dA64, dA64, flush, reps)
+        pms, _, ref = plain_ms_of(api, h, api.PLUS_TIMES_F64, dA64, dA64, flush, reps, keep=True)
         torch.cuda.empty_cache()
-        sf = summa_forms(api, Summa, h, api.PLUS_TIMES_F64, dA64, flush, reps)
+        sf = summa_forms(api, Summa, h, api.PLUS_TIMES_F64, dA64, flush, reps, ref=ref)
         sf["plain_unblocked_ms"] = pms
         forms[f"rmat{args.scale}_plus_times_f64_summa4x4"] = sf
-        del dA64
+        del dA64, ref
         torch.cuda.empty_cache()
+        forms["float_cold_warm"] = cold_warm_forms()
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

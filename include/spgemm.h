@@ -26,8 +26,10 @@
  *   is the legacy default stream) and runs asynchronously, except where a
  *   call returns a host count (it then synchronises that stream).
  * - Argument errors are returned synchronously.  Errors found by kernels
- *   (hash-table overflow, timeouts) are recorded in the workspace and
- *   reported by the next call that synchronises, or by spgemm_check().
+ *   (hash-table overflow, counts that disagree with the row pointers given)
+ *   are recorded in the workspace and reported by the next call that
+ *   synchronises, or by spgemm_check().  No kernel of the library waits on
+ *   another kernel, a flag or a peer, so no call can time out.
  * - B.nrows must equal A.ncols.  Empty matrices and empty rows are valid and
  *   give empty output rows.
  */
@@ -45,11 +47,13 @@ typedef enum {
     SPG_OK = 0,
     SPG_ERR_INVALID_ARG = 1,   /* a NULL pointer, a bad id or mismatched shapes      */
     SPG_ERR_INVALID_CSR = 2,   /* spgemm_validate_csr found a malformed matrix       */
-    SPG_ERR_OOM = 3,           /* a host-side allocation of the host API failed      */
+    SPG_ERR_OOM = 3,           /* a device buffer of the host API could not be had:
+                                  cudaMalloc failed, or the buffers would exceed
+                                  spg_tuning.host_alloc_limit                       */
     SPG_ERR_CUDA = 4,          /* a CUDA runtime call failed (see spgemm_last_error) */
     SPG_ERR_UNSUPPORTED = 5,   /* shape beyond the library's index range             */
     SPG_ERR_OVERFLOW = 6,      /* a hash table ran out of slots (capacity too small) */
-    SPG_ERR_TIMEOUT = 7,       /* a bounded device wait gave up                      */
+                               /* 7: not used                                        */
     SPG_ERR_WORKSPACE = 8      /* workspace NULL or smaller than required            */
 } spg_status;
 
@@ -99,7 +103,11 @@ typedef struct {
                                    order of A's entries (k ascending, a left fold from
                                    the first product): bit-identical run to run and to a
                                    sequential Gustavson; costs an extra ordered pass    */
-    int64_t reserved[1];
+    int64_t host_alloc_limit;   /* host API: most device bytes the handle may hold for
+                                   its copies of A, B, C and the workspace; the buffer
+                                   that would cross it is not allocated and the call
+                                   returns SPG_ERR_OOM (buffers already held stay with
+                                   the handle).  0: no limit beyond the device's        */
 } spg_tuning;
 
 /* Counters of the last analysis on a handle (host copy, filled by spgemm_symbolic). */
@@ -241,9 +249,12 @@ spg_status spgemm_split_columns(spg_handle* handle, const spg_csr* M, int nparts
 spg_status spgemm_check(spg_handle* handle, void* workspace, void* stream);
 
 /*
- * CSR validity check (row_ptr monotone from 0 to nnz, columns in range and
- * strictly ascending per row).  Synchronises `stream`.  Needs 64 bytes of
- * workspace.  Returns SPG_OK or SPG_ERR_INVALID_CSR.
+ * CSR validity check: row_ptr non-decreasing from row_ptr[0] >= 0 to
+ * row_ptr[0] + nnz (row_ptr[0] > 0 for a row view), columns in [0, ncols) and
+ * strictly ascending per row.  A malformed matrix is never read beyond its
+ * bounds: a row whose bounds are out of range is reported without reading
+ * its columns.  Synchronises `stream`.  Needs 64 bytes of workspace.  Returns
+ * SPG_OK or SPG_ERR_INVALID_CSR.
  */
 spg_status spgemm_validate_csr(spg_handle* handle, const spg_csr* M, void* workspace,
                                size_t workspace_bytes, void* stream);

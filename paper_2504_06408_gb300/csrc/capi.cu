@@ -43,6 +43,8 @@ struct spg_handle {
     cudaEvent_t ev_done[2] = {}, ev_copied[2] = {};
     bool pipe_events = false;
     DevBuf p_rp[2], p_col[2], p_val[2];        // double-buffered panel outputs
+    // checked build: device status of the input validation (256 bytes)
+    void* chk_status = nullptr;
     // learned path: values fixed by the last spgemm_learned_plan
     int lrn_sr = -1;
     int64_t lrn_entries = -1, lrn_warp_max = 0, lrn_block_max = 0, lrn_rows = -1;
@@ -273,6 +275,7 @@ spg_status spgemm_create(spg_handle** handle) {
 spg_status spgemm_destroy(spg_handle* h) {
     if (!h) return SPG_ERR_INVALID_ARG;
     if (h->pinned) cudaFreeHost(h->pinned);
+    if (h->chk_status) cudaFree(h->chk_status);
     if (h->timer_events)
         for (int i = 0; i < StageTimer::kMax; ++i) cudaEventDestroy(h->timer.ev[i]);
     for (DevBuf* b : {&h->a_rp, &h->a_col, &h->a_val, &h->b_rp, &h->b_col, &h->b_val, &h->ws,
@@ -360,11 +363,48 @@ static spg_status read_status(spg_handle* h, const WsPtrs& w, cudaStream_t st) {
     if (hs->overflow)
         return fail(h, SPG_ERR_OVERFLOW, "hash table overflow or inconsistent counts (flat row %lld)",
                     (long long)hs->info[0]);
-    if (hs->timeout) return fail(h, SPG_ERR_TIMEOUT, "a bounded device wait gave up");
     if (hs->invalid)
         return fail(h, SPG_ERR_INVALID_CSR, "invalid CSR (row %lld)", (long long)hs->info[1]);
     return SPG_OK;
 }
+
+#ifdef SPG_CHECKS
+// Checked build: the input matrices are validated on the device (bounds-safe,
+// spgemm_validate_csr's kernel) and the call returns SPG_ERR_INVALID_CSR
+// before any product kernel is queued on a malformed matrix.  Synchronises.
+static spg_status checked_inputs(spg_handle* h, int n, const spg_csr* const* mats,
+                                 cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    if (!h->chk_status) e = cudaMalloc(&h->chk_status, 256);
+    if (e != cudaSuccess) return cuda_fail(h, e, "checked build status");
+    DevStatus* ds = (DevStatus*)h->chk_status;
+    e = cudaMemsetAsync(ds, 0, sizeof(DevStatus), st);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        const spg_csr* M = mats[i];
+        bool seen = false;   // the same matrix passed twice (A = B) is checked once
+        for (int j = 0; j < i; ++j)
+            seen |= mats[j]->row_ptr == M->row_ptr && mats[j]->col == M->col &&
+                    mats[j]->nrows == M->nrows && mats[j]->ncols == M->ncols;
+        if (!seen) e = launch_validate(to_dcsr(M), M->nnz, ds, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "validate");
+    WsPtrs w{};
+    w.status = ds;
+    spg_status s = read_status(h, w, st);
+    if (s == SPG_ERR_INVALID_CSR) h->err = "checked build: an input matrix is not valid CSR (" + h->err + ")";
+    return s;
+}
+
+static spg_status checked_pairs(spg_handle* h, int nprob, const spg_csr* A, const spg_csr* B,
+                                cudaStream_t st) {
+    std::vector<const spg_csr*> mats;
+    for (int p = 0; p < nprob; ++p) {
+        mats.push_back(A + p);
+        mats.push_back(B + p);
+    }
+    return checked_inputs(h, (int)mats.size(), mats.data(), st);
+}
+#endif
 
 // ---- symbolic / numeric, single and batched ---------------------------------------
 
@@ -426,6 +466,12 @@ static spg_status symbolic_launch(spg_handle* h, int sr, int nprob, const spg_cs
     if (!workspace || workspace_bytes < L.total)
         return fail(h, SPG_ERR_WORKSPACE, "workspace needs %zu bytes", L.total);
     const WsPtrs w = ws_ptrs(workspace, L);
+#ifdef SPG_CHECKS
+    {
+        const spg_status cs = checked_pairs(h, nprob, A, B, st);
+        if (cs != SPG_OK) return cs;
+    }
+#endif
     h->launches = 0;
     h->timer.n = 0;
     cudaError_t e = reset_status ? cudaMemsetAsync(workspace, 0, L.probs, st)   // status + counters
@@ -484,12 +530,32 @@ static spg_status numeric_impl(spg_handle* h, int sr, int nprob, const spg_csr* 
     if (!workspace || workspace_bytes < L.total)
         return fail(h, SPG_ERR_WORKSPACE, "workspace needs %zu bytes", L.total);
     const WsPtrs w = ws_ptrs(workspace, L);
+#ifdef SPG_CHECKS
+    {
+        const spg_status cs = checked_pairs(h, nprob, A, B, st);
+        if (cs != SPG_OK) return cs;
+    }
+#endif
     h->launches = 0;
     h->timer.n = 0;
     ProbTable* tab = new ProbTable;
     fill_probs(tab, nprob, A, B, const_cast<int64_t* const*>(c_row_ptr), c_col, c_val);
     cudaError_t e = launch_write_probs(*tab, nprob, w, h->dev, st);
     delete tab;
+#ifdef SPG_CHECKS
+    // C's row pointers must be those of the symbolic call that left this
+    // workspace (their last entry its nnz(C)): no kernel writes C otherwise
+    if (e == cudaSuccess) e = launch_check_rowptr(w, nprob, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "row pointer check");
+    {
+        const spg_status cs = read_status(h, w, st);
+        if (cs == SPG_ERR_INVALID_CSR) {
+            h->err = "checked build: C's row pointers are not those of the symbolic call (" + h->err + ")";
+            return cs;
+        }
+        if (cs != SPG_OK) return cs;
+    }
+#endif
     if (e == cudaSuccess)
         e = launch_numeric(sr, w, to_dcsr(B), nprob, L.R, t, max_ncols(nprob, B), h->dev, st);
     if (e == cudaSuccess && h->user.deterministic)
@@ -769,21 +835,48 @@ spg_status spgemm_transpose(spg_handle* h, const spg_csr* A, int value_bytes,
 
 // ---- host-memory API ------------------------------------------------------------
 
-static cudaError_t ensure(DevBuf& b, size_t bytes) {
-    if (bytes <= b.bytes && b.p) return cudaSuccess;
+// device bytes held by the handle's host-API buffers
+static size_t held_bytes(const spg_handle* h) {
+    const DevBuf* all[] = {&h->a_rp, &h->a_col, &h->a_val, &h->b_rp, &h->b_col, &h->b_val,
+                           &h->ws, &h->c_rp, &h->c_col, &h->c_val, &h->p_rp[0], &h->p_rp[1],
+                           &h->p_col[0], &h->p_col[1], &h->p_val[0], &h->p_val[1]};
+    size_t n = 0;
+    for (const DevBuf* b : all) n += b->bytes;
+    return n;
+}
+
+// b holds at least `bytes` afterwards.  SPG_ERR_OOM when the handle's buffers
+// would exceed spg_tuning.host_alloc_limit (checked before anything is freed
+// or allocated) or when cudaMalloc runs out of memory.
+static spg_status ensure(spg_handle* h, DevBuf& b, size_t bytes, const char* what) {
+    if (bytes <= b.bytes && b.p) return SPG_OK;
+    const size_t n = bytes ? bytes : 16;
+    const int64_t lim = h->user.host_alloc_limit;
+    if (lim > 0 && held_bytes(h) - b.bytes + n > (size_t)lim)
+        return fail(h, SPG_ERR_OOM, "%s: %zu more bytes would exceed host_alloc_limit (%lld)",
+                    what, n, (long long)lim);
     if (b.p) cudaFree(b.p);
     b.p = nullptr;
     b.bytes = 0;
-    const size_t n = bytes ? bytes : 16;
-    cudaError_t e = cudaMalloc(&b.p, n);
-    if (e == cudaSuccess) b.bytes = n;
-    return e;
+    const cudaError_t e = cudaMalloc(&b.p, n);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(h, SPG_ERR_OOM, "%s: cudaMalloc of %zu bytes: out of device memory", what, n);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, what);
+    b.bytes = n;
+    return SPG_OK;
 }
 
-static cudaError_t upload(DevBuf& b, const void* src, size_t bytes, cudaStream_t st) {
-    cudaError_t e = ensure(b, bytes);
-    if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(b.p, src, bytes, cudaMemcpyHostToDevice, st);
-    return e;
+static spg_status upload(spg_handle* h, DevBuf& b, const void* src, size_t bytes,
+                         cudaStream_t st, const char* what) {
+    spg_status s = ensure(h, b, bytes, what);
+    if (s != SPG_OK) return s;
+    if (bytes) {
+        const cudaError_t e = cudaMemcpyAsync(b.p, src, bytes, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "upload");
+    }
+    return SPG_OK;
 }
 
 spg_status spgemm_host_symbolic(spg_handle* h, spg_semiring sr, const spg_csr* A,
@@ -798,15 +891,16 @@ spg_status spgemm_host_symbolic(spg_handle* h, spg_semiring sr, const spg_csr* A
     const int vb = in_bytes(sr);
     const bool same = A->row_ptr == B->row_ptr && A->col == B->col && A->val == B->val &&
                       A->nrows == B->nrows && A->nnz == B->nnz;
-    e = upload(h->a_rp, A->row_ptr, sizeof(int64_t) * (size_t)(A->nrows + 1), st);
-    if (e == cudaSuccess) e = upload(h->a_col, A->col, sizeof(int32_t) * (size_t)A->nnz, st);
-    if (e == cudaSuccess && vb) e = upload(h->a_val, A->val, (size_t)vb * (size_t)A->nnz, st);
+    s = upload(h, h->a_rp, A->row_ptr, sizeof(int64_t) * (size_t)(A->nrows + 1), st, "A.row_ptr");
+    if (s == SPG_OK) s = upload(h, h->a_col, A->col, sizeof(int32_t) * (size_t)A->nnz, st, "A.col");
+    if (s == SPG_OK && vb) s = upload(h, h->a_val, A->val, (size_t)vb * (size_t)A->nnz, st, "A.val");
     if (!same) {
-        if (e == cudaSuccess) e = upload(h->b_rp, B->row_ptr, sizeof(int64_t) * (size_t)(B->nrows + 1), st);
-        if (e == cudaSuccess) e = upload(h->b_col, B->col, sizeof(int32_t) * (size_t)B->nnz, st);
-        if (e == cudaSuccess && vb) e = upload(h->b_val, B->val, (size_t)vb * (size_t)B->nnz, st);
+        if (s == SPG_OK)
+            s = upload(h, h->b_rp, B->row_ptr, sizeof(int64_t) * (size_t)(B->nrows + 1), st, "B.row_ptr");
+        if (s == SPG_OK) s = upload(h, h->b_col, B->col, sizeof(int32_t) * (size_t)B->nnz, st, "B.col");
+        if (s == SPG_OK && vb) s = upload(h, h->b_val, B->val, (size_t)vb * (size_t)B->nnz, st, "B.val");
     }
-    if (e != cudaSuccess) return cuda_fail(h, e, "upload");
+    if (s != SPG_OK) return s;
     h->hA = spg_csr{A->nrows, A->ncols, A->nnz, (const int64_t*)h->a_rp.p,
                     (const int32_t*)h->a_col.p, vb ? h->a_val.p : nullptr};
     h->hB = same ? h->hA
@@ -815,9 +909,9 @@ spg_status spgemm_host_symbolic(spg_handle* h, spg_semiring sr, const spg_csr* A
     size_t wsb = 0;
     s = spgemm_workspace_size(h, sr, &h->hA, &h->hB, &wsb);
     if (s != SPG_OK) return s;
-    e = ensure(h->ws, wsb);
-    if (e == cudaSuccess) e = ensure(h->c_rp, sizeof(int64_t) * (size_t)(A->nrows + 1));
-    if (e != cudaSuccess) return cuda_fail(h, e, "allocation");
+    s = ensure(h, h->ws, wsb, "workspace");
+    if (s == SPG_OK) s = ensure(h, h->c_rp, sizeof(int64_t) * (size_t)(A->nrows + 1), "C.row_ptr");
+    if (s != SPG_OK) return s;
     s = spgemm_symbolic(h, sr, &h->hA, &h->hB, (int64_t*)h->c_rp.p, c_nnz, h->ws.p, h->ws.bytes, st);
     if (s != SPG_OK) return s;
     e = cudaMemcpyAsync(c_row_ptr, h->c_rp.p, sizeof(int64_t) * (size_t)(A->nrows + 1),
@@ -879,12 +973,13 @@ static spg_status host_numeric_pipelined(spg_handle* h, int sr, int32_t* c_col, 
         }
         if (e == cudaSuccess) h->pipe_events = true;
     }
-    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
-        e = ensure(h->p_rp[b], sizeof(int64_t) * (size_t)(max_rows + 1));
-        if (e == cudaSuccess) e = ensure(h->p_col[b], sizeof(int32_t) * (size_t)max_nnz);
-        if (e == cudaSuccess && ob) e = ensure(h->p_val[b], (size_t)ob * (size_t)max_nnz);
+    if (e != cudaSuccess) return cuda_fail(h, e, "panel streams");
+    for (int b = 0; b < 2; ++b) {
+        spg_status s = ensure(h, h->p_rp[b], sizeof(int64_t) * (size_t)(max_rows + 1), "panel row_ptr");
+        if (s == SPG_OK) s = ensure(h, h->p_col[b], sizeof(int32_t) * (size_t)max_nnz, "panel col");
+        if (s == SPG_OK && ob) s = ensure(h, h->p_val[b], (size_t)ob * (size_t)max_nnz, "panel val");
+        if (s != SPG_OK) return s;
     }
-    if (e != cudaSuccess) return cuda_fail(h, e, "panel buffers");
     cudaStream_t st = h->hstream, cs = h->cstream;
     // no host synchronisation inside the loop: the panels' sizes are known from
     // the symbolic call on the whole of A, and a device-to-host copy on the
@@ -941,10 +1036,11 @@ spg_status spgemm_host_numeric(spg_handle* h, spg_semiring sr, int32_t* c_col, v
         (int64_t)h->host_crp.size() == h->hA.nrows + 1 && h->hA.nrows >= 2)
         return host_numeric_pipelined(h, sr, c_col, c_val);
     cudaStream_t st = h->hstream;
-    cudaError_t e = ensure(h->c_col, sizeof(int32_t) * (size_t)nnz);
-    if (e == cudaSuccess && ob) e = ensure(h->c_val, (size_t)ob * (size_t)nnz);
-    if (e != cudaSuccess) return cuda_fail(h, e, "allocation");
-    spg_status s = spgemm_numeric(h, sr, &h->hA, &h->hB, (const int64_t*)h->c_rp.p,
+    spg_status s = ensure(h, h->c_col, sizeof(int32_t) * (size_t)nnz, "C.col");
+    if (s == SPG_OK && ob) s = ensure(h, h->c_val, (size_t)ob * (size_t)nnz, "C.val");
+    if (s != SPG_OK) return s;
+    cudaError_t e = cudaSuccess;
+    s = spgemm_numeric(h, sr, &h->hA, &h->hB, (const int64_t*)h->c_rp.p,
                                   (int32_t*)h->c_col.p, ob ? h->c_val.p : nullptr, h->ws.p,
                                   h->ws.bytes, st);
     if (s != SPG_OK) return s;
@@ -1045,6 +1141,12 @@ spg_status spgemm_learned_plan(spg_handle* h, spg_semiring sr, const spg_csr* A,
     cudaStream_t st = (cudaStream_t)stream;
     const WsPtrs w = ws_ptrs(workspace, L);
     const LearnedWs lw = learned_ptrs(workspace, M, nullptr, 0);
+#ifdef SPG_CHECKS
+    {
+        const spg_status cs = checked_pairs(h, 1, A, B, st);
+        if (cs != SPG_OK) return cs;
+    }
+#endif
     h->launches = 0;
     h->timer.n = 0;
     h->lrn_sr = -1;
@@ -1300,6 +1402,13 @@ spg_status spgemm_masked_symbolic(spg_handle* h, spg_semiring sr, const spg_csr*
         return fail(h, SPG_ERR_WORKSPACE, "workspace needs %zu bytes", L.total);
     cudaStream_t st = (cudaStream_t)stream;
     char* b = (char*)workspace;
+#ifdef SPG_CHECKS
+    {
+        const spg_csr* mats[3] = {A, B, M};
+        const spg_status cs = checked_inputs(h, 3, mats, st);
+        if (cs != SPG_OK) return cs;
+    }
+#endif
     h->launches = 0;
     cudaError_t e = cudaMemsetAsync(b + L.status, 0, sizeof(DevStatus), st);
     if (e == cudaSuccess)

@@ -36,7 +36,7 @@ struct Prob {
 // Kernel-detected errors, kept in the workspace.
 struct DevStatus {
     int32_t overflow;    // a hash table ran out of slots
-    int32_t timeout;     // a bounded wait gave up
+    int32_t unused;
     int32_t invalid;     // validation failure
     int32_t pad;
     int64_t info[5];     // first offending flat row etc.
@@ -140,6 +140,12 @@ SPG_DEV int find_prob(const Prob* probs, int nprob, int64_t g) {
 
 SPG_DEV void flag_overflow(DevStatus* st, int64_t g) {
     if (atomicExch(&st->overflow, 1) == 0) st->info[0] = g;
+}
+
+// A data-dependent index found out of range (checked build): recorded, and the
+// access it would have made is skipped.
+SPG_DEV void flag_invalid(DevStatus* st, int64_t info) {
+    if (atomicExch(&st->invalid, 1) == 0) st->info[1] = info;
 }
 
 }  // namespace spg

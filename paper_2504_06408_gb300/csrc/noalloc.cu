@@ -19,11 +19,14 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
+// Per device: the array's device address, looked up by the first call that
+// succeeds (a lookup that failed, e.g. during a stream capture, is retried by
+// the next call rather than remembered).
 struct DeviceSetup {
-    std::once_flag once;
+    std::mutex mu;
+    bool done = false;
     void* scratch = nullptr;   // device address of g_noalloc_scratch on this device
     int sms = 0;
-    cudaError_t err = cudaSuccess;
 };
 DeviceSetup g_setup[kMaxDevices];
 
@@ -44,15 +47,28 @@ extern "C" spg_status spgemm_transpose_noalloc(const spg_csr* A, int value_bytes
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SPG_ERR_CUDA;
     // once per device, with that device current: the array's device address
     DeviceSetup& s = g_setup[dev];
-    std::call_once(s.once, [&s, dev]() {
-        s.err = cudaGetSymbolAddress(&s.scratch, g_noalloc_scratch);
-        if (s.err == cudaSuccess)
-            s.err = cudaDeviceGetAttribute(&s.sms, cudaDevAttrMultiProcessorCount, dev);
-    });
-    if (s.err != cudaSuccess || !s.scratch) return SPG_ERR_CUDA;
-    spg::DevInfo di{s.sms, 0};
+    void* scratch = nullptr;
+    int sms = 0;
+    {
+        std::lock_guard<std::mutex> lock(s.mu);
+        if (!s.done) {
+            void* p = nullptr;
+            int n = 0;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p ||
+                cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+                cudaGetLastError();   // clear the error so the next call can retry
+                return SPG_ERR_CUDA;
+            }
+            s.scratch = p;
+            s.sms = n;
+            s.done = true;
+        }
+        scratch = s.scratch;
+        sms = s.sms;
+    }
+    spg::DevInfo di{sms, 0};
     const spg::DCsr a{A->nrows, A->ncols, A->row_ptr, A->col, A->val};
     const cudaError_t e = spg::launch_transpose(a, A->nnz, value_bytes, t_row_ptr, t_col, t_val,
-                                                s.scratch, di, (cudaStream_t)stream);
+                                                scratch, di, (cudaStream_t)stream);
     return e == cudaSuccess ? SPG_OK : SPG_ERR_CUDA;
 }

@@ -679,6 +679,8 @@ struct RankAccOp {
     int32_t r1;         // rank of the pass's first output, plus one
     int32_t clo;        // columns of this pass: [clo, clo + width)
     uint32_t width;
+    int32_t cnt;        // outputs of the pass (checked build: ranks must fall below it)
+    DevStatus* st;
     SPG_DEV void any(int32_t col, typename S::In a, typename S::In b, bool valid) {
         if (!valid) return;
         if constexpr (kFilter) {
@@ -687,6 +689,14 @@ struct RankAccOp {
         const uint2 e = bw[col >> 5];
         // bits of the word at or below col's bit (col's own bit is set): its rank + 1
         const int r = (int)e.y + __popc(e.x << (~col & 31)) - r1;
+#ifdef SPG_CHECKS
+        // a column missing from the row's bitmap (B's pattern changed since the
+        // symbolic call) or a rank outside the pass: skip the write
+        if (!((e.x >> (col & 31)) & 1u) || (uint32_t)r >= (uint32_t)cnt) {
+            flag_invalid(st, col);
+            return;
+        }
+#endif
         S::acc(vals + r, a, b);
         cols[r] = col;
     }
@@ -918,11 +928,13 @@ __global__ void __launch_bounds__(kRankThreads, 1)
                     // with the slab table the walk covers only the pass's slabs;
                     // without it every product is visited and filtered
                     if (sp != nullptr || (s0 == 0 && s1 >= nslabs)) {
-                        RankAccOp<S, false> op{vals, cols, bw, r0 + 1, clo, (uint32_t)(chi - clo)};
+                        RankAccOp<S, false> op{vals, cols, bw, r0 + 1, clo, (uint32_t)(chi - clo),
+                                               cnt, st};
                         cta_range_products<In, S::kVal>(P.A, P.B, a0, a1, le, mode, sp, sp_stride,
                                                         nslabs, s0, s1, bs, op);
                     } else {
-                        RankAccOp<S, true> op{vals, cols, bw, r0 + 1, clo, (uint32_t)(chi - clo)};
+                        RankAccOp<S, true> op{vals, cols, bw, r0 + 1, clo, (uint32_t)(chi - clo),
+                                              cnt, st};
                         cta_range_products<In, S::kVal>(P.A, P.B, a0, a1, le, mode, sp, sp_stride,
                                                         nslabs, 0, nslabs, bs, op);
                     }

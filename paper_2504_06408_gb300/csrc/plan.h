@@ -135,6 +135,9 @@ cudaError_t launch_numeric(int sr, const WsPtrs& w, const DCsr& B0, int nprob, i
                            const Tuning& t, int64_t max_ncols, const DevInfo& dev,
                            cudaStream_t st);
 cudaError_t launch_validate(const DCsr& M, int64_t nnz, DevStatus* status, cudaStream_t st);
+// C's row pointers of every product against the nnz its symbolic call counted
+// (status->invalid on a mismatch); used by the checked build
+cudaError_t launch_check_rowptr(const WsPtrs& w, int nprob, cudaStream_t st);
 // masked product (masked.cu): accumulators per mask entry; cnt = C's row
 // pointers (R + 1), counted then scanned in place
 size_t masked_slot_bytes(int sr);

@@ -473,15 +473,20 @@ __global__ void k_write_rowptr(const Prob* __restrict__ probs, const int64_t* __
 
 // ---- CSR validity check -----------------------------------------------------------
 
+// Reads only M.rp[0 .. nrows] and the entries a row's bounds allow: a row
+// whose bounds are decreasing or outside [rp[0], rp[0] + nnz) is reported
+// without reading its columns, so a malformed matrix is never read out of
+// bounds.  (M may be a row view: its entries start at rp[0].)
 __global__ void k_validate(DCsr M, int64_t nnz, DevStatus* st) {
     const int lane = lane_id();
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t e0 = M.rp[0];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        if (M.rp[0] != 0 || M.rp[M.nrows] != nnz) atomicExch(&st->invalid, 1);
+        if (e0 < 0 || M.rp[M.nrows] != e0 + nnz) atomicExch(&st->invalid, 1);
     }
     for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); i < M.nrows; i += nw) {
         const int64_t a = M.rp[i], b = M.rp[i + 1];
-        bool bad = b < a;
+        bool bad = b < a || a < e0 || b > e0 + nnz || e0 < 0;
         if (!bad) {
             for (int64_t q = a + lane; q < b; q += 32) {
                 const int32_t c = M.col[q];
@@ -494,7 +499,31 @@ __global__ void k_validate(DCsr M, int64_t nnz, DevStatus* st) {
     }
 }
 
+// C's row pointers handed to a numeric call against the counts of the
+// symbolic call that left its workspace: c_rp[0] = 0, non-decreasing,
+// c_rp[nrows] = that call's nnz(C) for the product (blockIdx.y).
+__global__ void k_check_rowptr(const Prob* __restrict__ probs, const Counters* ctr,
+                               DevStatus* st) {
+    const Prob& P = probs[blockIdx.y];
+    const int64_t n = P.A.nrows;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (P.c_rp[0] != 0 || P.c_rp[n] != ctr->nnz[blockIdx.y]) {
+            if (atomicExch(&st->invalid, 1) == 0) st->info[1] = P.row_base + n;
+        }
+    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (P.c_rp[i + 1] < P.c_rp[i] && atomicExch(&st->invalid, 1) == 0)
+            st->info[1] = P.row_base + i;
+    }
+}
+
 // ---- launchers -------------------------------------------------------------------
+
+cudaError_t launch_check_rowptr(const WsPtrs& w, int nprob, cudaStream_t st) {
+    k_check_rowptr<<<dim3(64, nprob), 256, 0, st>>>(w.probs, w.ctr, w.status);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_write_probs(const ProbTable& tab, int nprob, const WsPtrs& w,
                                const DevInfo& dev, cudaStream_t st) {

@@ -4,12 +4,15 @@
 //
 // 1. t_rp[j] = number of entries in column j (atomics), exclusive scan.
 // 2. Every entry e of A is scattered to a free position of its column's
-//    segment (atomic cursor); what is scattered is e itself.  Entry numbers
-//    grow with the row index, so sorting a segment by e orders it by row.
+//    segment (atomic cursor); what is scattered is e - A.rp[0], its number
+//    inside A (A may be a row view whose first entry is far into the
+//    arrays), which fits int32 because nnz < 2^31 - 1.  Entry numbers grow
+//    with the row index, so sorting a segment by them orders it by row.
 // 3. Each segment is sorted (warp registers <= 32, CTA shared memory <= 16384,
 //    otherwise a CTA bitonic sort in a global scratch area of next_pow2(len)
 //    <= 2 len slots at 2 * t_rp[j]).
-// 4. Gather: t_col = row of e (binary search in A's row pointers), t_val = A.val[e].
+// 4. Gather: e = A.rp[0] + the stored number; t_col = row of e (binary search
+//    in A's row pointers), t_val = A.val[e].
 #include "plan.h"
 #include "rowwork.cuh"
 
@@ -32,7 +35,7 @@ __global__ void k_t_scatter(DCsr A, int64_t nnz, const int64_t* t_rp, int32_t* c
          e += (int64_t)gridDim.x * blockDim.x) {
         const int32_t j = A.col[e];
         const int32_t r = atomicAdd(cursor + j, 1);
-        t_col[t_rp[j] + r] = (int32_t)e;
+        t_col[t_rp[j] + r] = (int32_t)(e - e0);
     }
 }
 
@@ -96,9 +99,10 @@ __global__ void __launch_bounds__(512) k_t_sort_block(const int64_t* t_rp, int32
 }
 
 __global__ void k_t_gather(DCsr A, int64_t nnz, int value_bytes, int32_t* t_col, void* t_val) {
+    const int64_t e0 = A.rp[0];
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz;
          p += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t e = t_col[p];
+        const int64_t e = e0 + t_col[p];
         // row of entry e: last i with rp[i] <= e
         int64_t lo = 0, hi = A.nrows - 1;
         while (lo < hi) {

@@ -25,6 +25,8 @@ pattern-only boolean semiring).
 """
 from __future__ import annotations
 
+import hashlib
+import os
 from dataclasses import dataclass
 from typing import Optional
 
@@ -45,6 +47,41 @@ class CSR:
 
     def with_values(self, val: Optional[np.ndarray]) -> "CSR":
         return CSR(self.nrows, self.ncols, self.rp, self.col, val)
+
+
+# Large generated matrices are kept on disk between processes (the tests and
+# the benchmark draw the same seeded inputs); the directory is outside the
+# repository.  SPGEMM_INPUT_CACHE="" turns the cache off.
+_CACHE_DIR = os.environ.get("SPGEMM_INPUT_CACHE", "/tmp/spgemm_inputs")
+_CACHE_MIN_NNZ = 4_000_000
+
+
+def _cached(name: str, key: tuple, make):
+    """make() on a miss; the CSR's arrays are stored under a name derived from
+    the generator's arguments and read back on later calls."""
+    if not _CACHE_DIR:
+        return make()
+    tag = hashlib.sha256(repr((name, key)).encode()).hexdigest()[:20]
+    path = os.path.join(_CACHE_DIR, f"{name}_{tag}.npz")
+    try:
+        with np.load(path, allow_pickle=False) as z:
+            val = z["val"] if "val" in z.files else None
+            return CSR(int(z["shape"][0]), int(z["shape"][1]), z["rp"], z["col"], val)
+    except (OSError, KeyError, ValueError):
+        pass
+    M = make()
+    if M.nnz >= _CACHE_MIN_NNZ:
+        try:
+            os.makedirs(_CACHE_DIR, exist_ok=True)
+            tmp = f"{path}.{os.getpid()}.tmp.npz"
+            arrays = {"shape": np.array([M.nrows, M.ncols], np.int64), "rp": M.rp, "col": M.col}
+            if M.val is not None:
+                arrays["val"] = M.val
+            np.savez(tmp, **arrays)
+            os.replace(tmp, path)
+        except OSError:
+            pass
+    return M
 
 
 def _from_sorted_coo(nrows: int, ncols: int, rows: np.ndarray, cols: np.ndarray,
@@ -97,6 +134,18 @@ def rmat_edges(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.
 def rmat(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19,
          c: float = 0.19, seed: int = 1, dtype=np.float32, lo: float = 1.0,
          hi: float = 100.0) -> CSR:
+    """Symmetric R-MAT adjacency matrix with one weight per undirected edge
+    (see _rmat); large ones are kept in the input cache."""
+    make = lambda: _rmat(scale, edge_factor, a, b, c, seed, dtype, lo, hi)  # noqa: E731
+    if scale < 17:
+        return make()
+    key = (scale, edge_factor, a, b, c, seed, None if dtype is None else np.dtype(dtype).str,
+           lo, hi)
+    return _cached("rmat", key, make)
+
+
+def _rmat(scale: int, edge_factor: int, a: float, b: float, c: float, seed: int, dtype,
+          lo: float, hi: float) -> CSR:
     """Symmetric R-MAT adjacency matrix with one weight per undirected edge.
 
     ``dtype=None`` gives a pattern-only matrix.
@@ -141,6 +190,67 @@ def laplacian(g: int = 2048, dtype=np.float64) -> CSR:
     return CSR(n, n, rp, cols[mask].astype(np.int32), v)
 
 
+def trigrid(g: int, dtype=np.float32, seed: int = 1) -> CSR:
+    """Triangular lattice on a g x g grid: every vertex joined to its 6
+    neighbours (x +- 1, y +- 1, and the diagonal (x + 1, y - 1), (x - 1, y + 1)),
+    no diagonal entries, weights U[0, 1) per undirected edge.  Stand-in for a
+    planar Delaunay triangulation (delaunay_n22: 4.19M rows, 6.0 entries per
+    row)."""
+    n = g * g
+    idx = np.arange(n, dtype=np.int64)
+    x, y = idx % g, idx // g
+    deltas = sorted([(1, -1), (0, -1), (-1, 0), (1, 0), (0, 1), (-1, 1)],
+                    key=lambda d: d[1] * g + d[0])
+    cols = np.full((n, 6), -1, dtype=np.int64)
+    for t, (dx, dy) in enumerate(deltas):
+        ok = (x + dx >= 0) & (x + dx < g) & (y + dy >= 0) & (y + dy < g)
+        cols[ok, t] = idx[ok] + dy * g + dx
+    mask = cols >= 0
+    rp = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(mask.sum(axis=1), out=rp[1:])
+    col = cols[mask]
+    if dtype is None:
+        return CSR(n, n, rp, col.astype(np.int32), None)
+    # one weight per undirected edge {min, max}: symmetric values
+    rows = np.repeat(idx, mask.sum(axis=1))
+    lo, hi = np.minimum(rows, col), np.maximum(rows, col)
+    rng = np.random.default_rng(seed)
+    w_edge = _uniform(rng, n * 3 + 1, 0.0, 1.0, np.float64)
+    key = lo * 3 + np.select([hi - lo == 1, hi - lo == g - 1], [0, 1], 2)
+    return CSR(n, n, rp, col.astype(np.int32), w_edge[key].astype(dtype))
+
+
+def stencil3d(g: int, points: int = 7, dtype=np.float32) -> CSR:
+    """Dirichlet 3D stencil on a g x g x g grid (x fastest): 7 points (faces,
+    value 6 on the diagonal and -1 off it) or 27 points (the full 3 x 3 x 3
+    neighbourhood, 26 and -1).  Stand-ins for the PDE matrices of the
+    paper's experiments (atmosmodd: 1.27M rows, 8.8M entries, about a 7-point
+    108^3 grid; Long_dt_Coup0: a 3D coupled problem)."""
+    if points not in (7, 27):
+        raise ValueError("points must be 7 or 27")
+    n = g * g * g
+    idx = np.arange(n, dtype=np.int64)
+    x, y, z = idx % g, (idx // g) % g, idx // (g * g)
+    if points == 7:
+        deltas = [(0, 0, -1), (0, -1, 0), (-1, 0, 0), (0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1)]
+    else:
+        deltas = [(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+    # ascending column order: offsets dz * g^2 + dy * g + dx are increasing in this order
+    deltas.sort(key=lambda d: d[2] * g * g + d[1] * g + d[0])
+    cols = np.full((n, len(deltas)), -1, dtype=np.int64)
+    vals = np.zeros((n, len(deltas)), dtype=np.float64)
+    for t, (dx, dy, dz) in enumerate(deltas):
+        ok = ((x + dx >= 0) & (x + dx < g) & (y + dy >= 0) & (y + dy < g) &
+              (z + dz >= 0) & (z + dz < g))
+        cols[ok, t] = idx[ok] + dz * g * g + dy * g + dx
+        vals[ok, t] = (len(deltas) - 1.0) if (dx, dy, dz) == (0, 0, 0) else -1.0
+    mask = cols >= 0
+    rp = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(mask.sum(axis=1), out=rp[1:])
+    v = None if dtype is None else vals[mask].astype(dtype)
+    return CSR(n, n, rp, cols[mask].astype(np.int32), v)
+
+
 def _zipf_cdf(nranks: int, s: float) -> np.ndarray:
     w = np.arange(1, nranks + 1, dtype=np.float64) ** (-s)
     cdf = np.cumsum(w)
@@ -150,6 +260,13 @@ def _zipf_cdf(nranks: int, s: float) -> np.ndarray:
 
 def kmer(nrows: int = 200_000, ncols: int = 1 << 24, len_lo: int = 50, len_hi: int = 200,
          s: float = 1.1, col_cap: int = 64, seed: int = 1, max_rounds: int = 100000) -> CSR:
+    """Reads x k-mers matrix (see _kmer), kept in the input cache."""
+    return _cached("kmer", (nrows, ncols, len_lo, len_hi, s, col_cap, seed, max_rounds),
+                   lambda: _kmer(nrows, ncols, len_lo, len_hi, s, col_cap, seed, max_rounds))
+
+
+def _kmer(nrows: int, ncols: int, len_lo: int, len_hi: int, s: float, col_cap: int, seed: int,
+          max_rounds: int) -> CSR:
     """Reads x k-mers matrix; value = position of the k-mer in its read.
 
     Row lengths are uniform in [len_lo, len_hi].  Each slot draws a Zipf(s)

@@ -16,6 +16,9 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libspgemm.so")
+# the same library built with -DSPG_CHECKS (inputs validated on the device
+# before any product kernel, C's row pointers and ranks checked)
+CHECKS_LIB_PATH = os.path.join(HERE, "_build_checks", "libspgemm_checks.so")
 
 # semiring ids (spg_semiring)
 PLUS_TIMES_F64, BOOL_OR_AND, MIN_PLUS_F32, OVERLAP_I32, PLUS_TIMES_I64, PLUS_TIMES_F32 = range(6)
@@ -31,7 +34,7 @@ OUT_BYTES = {PLUS_TIMES_F64: 8, BOOL_OR_AND: 0, MIN_PLUS_F32: 4, OVERLAP_I32: 20
 
 STATUS = {0: "SPG_OK", 1: "SPG_ERR_INVALID_ARG", 2: "SPG_ERR_INVALID_CSR", 3: "SPG_ERR_OOM",
           4: "SPG_ERR_CUDA", 5: "SPG_ERR_UNSUPPORTED", 6: "SPG_ERR_OVERFLOW",
-          7: "SPG_ERR_TIMEOUT", 8: "SPG_ERR_WORKSPACE"}
+          8: "SPG_ERR_WORKSPACE"}
 
 
 class SpgemmError(RuntimeError):
@@ -50,7 +53,7 @@ class spg_tuning(ctypes.Structure):
                 ("num_warp_max_nnz", ctypes.c_int64), ("num_block_max_nnz", ctypes.c_int64),
                 ("dense_slab_cols", ctypes.c_int64), ("sym_slab_cols", ctypes.c_int64),
                 ("bitmap_cache_bytes", ctypes.c_int64), ("host_panel_bytes", ctypes.c_int64),
-                ("deterministic", ctypes.c_int64), ("reserved", ctypes.c_int64 * 1)]
+                ("deterministic", ctypes.c_int64), ("host_alloc_limit", ctypes.c_int64)]
 
 
 class spg_stats(ctypes.Structure):
@@ -75,7 +78,7 @@ STAGES = ["", "analysis", "sym_dense", "sym_block", "sym_warp", "scan", "num_bin
           "slab_table", "num_dense", "num_block", "num_warp", "merge", "learned"]
 
 
-_lib = None
+_libs = {}
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _CSR = ctypes.POINTER(spg_csr)
@@ -83,9 +86,8 @@ _CSR = ctypes.POINTER(spg_csr)
 
 def load_library(path: str = LIB_PATH):
     """Load the CUDA library (raises if it has not been built)."""
-    global _lib
-    if _lib is not None:
-        return _lib
+    if path in _libs:
+        return _libs[path]
     if not os.path.exists(path):
         raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
     lib = ctypes.CDLL(path)
@@ -152,7 +154,7 @@ def load_library(path: str = LIB_PATH):
     lib.spgemm_last_error.restype = ctypes.c_char_p
     lib.spgemm_mlp_train_workspace_size.argtypes = [_I64]
     lib.spgemm_mlp_train_workspace_size.restype = ctypes.c_size_t
-    _lib = lib
+    _libs[path] = lib
     return lib
 
 
@@ -217,8 +219,8 @@ def _stream_ptr(stream=None):
 class Handle:
     """spg_handle wrapper; one per thread, reusable across calls."""
 
-    def __init__(self, tuning: Optional[dict] = None):
-        self.lib = load_library()
+    def __init__(self, tuning: Optional[dict] = None, lib_path: str = LIB_PATH):
+        self.lib = load_library(lib_path)
         self._h = ctypes.c_void_p()
         self._ok(self.lib.spgemm_create(ctypes.byref(self._h)))
         if tuning:

@@ -32,9 +32,10 @@ def test_library_exports_every_declared_symbol():
     import __graft_entry__ as g
     g.build()
     from paper_2504_06408_gb300 import spgemm as api
-    lib = ctypes.CDLL(api.LIB_PATH)
-    missing = [n for n in _declared() if not hasattr(lib, n)]
-    assert not missing, missing
+    for path in (api.LIB_PATH, api.CHECKS_LIB_PATH):   # the library and its checked build
+        lib = ctypes.CDLL(path)
+        missing = [n for n in _declared() if not hasattr(lib, n)]
+        assert not missing, (path, missing)
     # the Python binding covers every declared function
     assert set(_declared()) <= set(api.exported_symbols())
 
@@ -42,12 +43,7 @@ def test_library_exports_every_declared_symbol():
 def test_binding_fails_loudly_without_library(tmp_path):
     from paper_2504_06408_gb300 import spgemm as api
     with pytest.raises(RuntimeError):
-        saved = api._lib
-        api._lib = None
-        try:
-            api.load_library(str(tmp_path / "missing.so"))
-        finally:
-            api._lib = saved
+        api.load_library(str(tmp_path / "missing.so"))
 
 
 def test_argument_errors_are_synchronous():

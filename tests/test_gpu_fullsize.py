@@ -1,11 +1,13 @@
-"""Parity at the full sizes of the benchmark configurations, on sampled rows
-the oracle computes one by one (stratified: the heaviest rows, random rows of
-every size, empty rows), plus properties that hold at any size.
+"""Parity at the full sizes of the benchmark configurations, plus properties
+that hold at any size.
 
 * R-MAT 18 A^2 (262,144 vertices), min-plus FP32 and boolean: exactly the
-  bench product and launch configuration.
+  bench product and launch configuration; EVERY row of C is compared with
+  the oracle, streamed in row panels (the oracle computes a panel's rows on
+  all host cores, the GPU panel is copied to the host, both are compared
+  and freed).
 * k-mer reads x k-mers (200,000 x 2^24), C = A A^T over the overlap semiring,
-  A^T by the GPU transpose.
+  A^T by the GPU transpose; every row against the oracle, streamed.
 * 5-point Laplacian on a 2048 x 2048 grid, A^2 plus-times FP64: every entry
   against the closed form.
 """
@@ -54,6 +56,27 @@ def check_rows(sr, A, B, C_dev, rows, row_offset=0):
         assert_values(sr, got.val, exp.val)
 
 
+def compare_all_rows_streamed(sr, A, B, C, ub, panel_products=6e8):
+    """Every row of C against the oracle, in contiguous row panels of about
+    panel_products products each."""
+    rp = C.rp.cpu().numpy()
+    csum = np.concatenate([[0], np.cumsum(ub)])
+    r0, npanels = 0, 0
+    while r0 < A.nrows:
+        r1 = int(np.searchsorted(csum, csum[r0] + panel_products, side="right")) - 1
+        r1 = min(max(r1, r0 + 1), A.nrows)
+        exp = oracle.spgemm(sr, A, B, rows=np.arange(r0, r1))
+        a, b = int(rp[r0]), int(rp[r1])
+        assert_pattern_equal(rp[r0:r1 + 1] - a, C.col[a:b].cpu().numpy(), exp.rp, exp.col,
+                             f"rows [{r0}, {r1})")
+        if sr != api.BOOL_OR_AND:
+            assert_values(sr, C.val[a:b].cpu().numpy(), exp.val, what=f"rows [{r0}, {r1})")
+        del exp
+        r0 = r1
+        npanels += 1
+    return npanels
+
+
 @pytest.mark.parametrize("sr", [api.MIN_PLUS_F32, api.BOOL_OR_AND])
 def test_rmat18_bench_product(sr):
     A = I.rmat(18, dtype=np.float32, seed=1)
@@ -69,7 +92,7 @@ def test_rmat18_bench_product(sr):
     # row sums of the counts equal the scanned row pointers' differences
     rp = C.rp.cpu().numpy()
     assert rp[0] == 0 and np.all(np.diff(rp) >= 0) and np.all(np.diff(rp) <= ub)
-    check_rows(sr, A, A, C, sample_rows(ub))
+    assert compare_all_rows_streamed(sr, A, A, C, ub) > 1
     if sr == api.MIN_PLUS_F32:   # symmetric weights: C[i,i] = 2 x lightest edge
         rows = sample_rows(ub, k_rand=2000, seed=5)
         rows = rows[ub[rows] > 0]
@@ -90,8 +113,8 @@ def test_kmer_full_overlap():
     C = api.spgemm(api.OVERLAP_I32, dA, dAt, handle=h)
     At = oracle.transpose(A, np.int32)
     ub = oracle.row_upper_bounds(A, At)
+    assert compare_all_rows_streamed(api.OVERLAP_I32, A, At, C, ub, panel_products=2e8) > 1
     rows = sample_rows(ub, k_heavy=20, k_rand=400)
-    check_rows(api.OVERLAP_I32, A, At, C, rows)
     # diagonal of every sampled row: {len, (0,0), (1,1)}
     got = api.to_host_rows(C, api.OVERLAP_I32, rows)
     for t, i in enumerate(rows):

@@ -58,3 +58,24 @@ def test_host_api_same_arrays_and_repeat():
         assert np.array_equal(col[:n], exp.col)
         assert np.array_equal(val[:n * 4].view(np.float32).view(np.uint32),
                               exp.val.view(np.uint32))
+
+
+def test_host_api_allocation_limit_gives_oom_and_recovers():
+    """A handle whose device buffers would exceed spg_tuning.host_alloc_limit
+    returns SPG_ERR_OOM (the allocation that would cross the limit is never
+    made); with the limit raised the same handle computes the product."""
+    sr = api.MIN_PLUS_F32
+    A = values_for(sr, I.rmat(11, seed=4, dtype=None), 6)
+    exp = oracle.spgemm(sr, A, A)
+    h = api.Handle(tuning={"host_alloc_limit": 64 << 10})   # far below A's own copy
+    with pytest.raises(api.SpgemmError) as e:
+        h.host_multiply(sr, A, A)
+    assert e.value.status == 3   # SPG_ERR_OOM
+    assert "host_alloc_limit" in str(e.value)
+    rp = np.empty(A.nrows + 1, np.int64)
+    col = np.empty(exp.nnz, np.int32)
+    val = np.empty(exp.nnz * 4, np.uint8)
+    h.set_tuning(host_alloc_limit=1 << 40)
+    rp2, col2, val2, n = h.host_multiply(sr, A, A, out={"rp": rp, "col": col, "val": val})
+    assert np.array_equal(rp2, exp.rp) and np.array_equal(col2[:n], exp.col)
+    assert np.array_equal(val2[:n * 4].view(np.uint32), exp.val.view(np.uint32))
