@@ -39,9 +39,11 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
-# the comparison forms allocate and free tens of GB in turn
-if "PYTORCH_CUDA_ALLOC_CONF" not in os.environ:
-    os.environ.setdefault("PYTORCH_ALLOC_CONF", "expandable_segments:True")
+# the comparison forms allocate and free tens of GB in turn (both names: the
+# variable was renamed between PyTorch releases)
+if "PYTORCH_CUDA_ALLOC_CONF" not in os.environ and "PYTORCH_ALLOC_CONF" not in os.environ:
+    os.environ["PYTORCH_CUDA_ALLOC_CONF"] = "expandable_segments:True"
+    os.environ["PYTORCH_ALLOC_CONF"] = "expandable_segments:True"
 
 METRIC = "semiring SpGEMM GFLOPS (2*products/s), R-MAT scale 18 A^2 over min-plus FP32"
 METRIC_SCALED = "semiring SpGEMM GFLOPS (2*products/s), R-MAT scale %d A^2 over min-plus FP32"
@@ -386,15 +388,23 @@ def block_matches(ref, r0, r1, c0, c1, blk, chunk=1 << 27):
     return ok, worst
 
 
-def summa_forms(api, Summa, h, sr, dA, flush, reps, ref=None):
-    """4 x 4 Sparse-SUMMA block grid: one batched launch per phase (and a CUDA
-    graph of numeric + merge) against one call per block product and merge.
-    With ref (the unblocked C), every C block of every form is compared with
-    the same block of the unblocked product."""
+def summa_forms(api, Summa, h, sr, dA, flush, reps, ref=None, tuning=None):
+    """4 x 4 Sparse-SUMMA block grid.  Batched: one launch per kernel tier over
+    all 64 block products and one merge call, timed eagerly (host
+    synchronisations between the phases) and as one CUDA graph of the whole
+    product (analysis, symbolic, numeric and merge of every block, no host
+    synchronisation); also with autotuned tier limits.  Unbatched: one call per
+    block product and per merge.  With ref (the unblocked C), every C block of
+    every form is compared with the same block of the unblocked product."""
     import torch
     out = {}
-    for batched in (True, False):
-        sm = Summa(h, sr, dA, dA, q=4, batched=batched)
+    forms = [("batched", True, None), ("unbatched", False, None)]
+    if tuning:
+        forms.insert(1, ("batched_tuned", True, tuning))
+        out["tuning"] = tuning
+    for key, batched, tun in forms:
+        hh = api.Handle(tuning=tun) if tun else h
+        sm = Summa(hh, sr, dA, dA, q=4, batched=batched)
         sm.plan()
 
         def full():
@@ -403,16 +413,12 @@ def summa_forms(api, Summa, h, sr, dA, flush, reps, ref=None):
             sm.merge_count()
             sm.merge_write()
 
-        def numeric_merge():
-            sm.run()
-
-        key = "batched" if batched else "unbatched"
         out[f"{key}_full_ms"] = _time_ms(full, reps, flush)
         if batched:
-            sm.capture()
-            out["batched_graph_numeric_merge_ms"] = _time_ms(numeric_merge, reps, flush)
+            sm.capture(full=True)
+            out[f"{key}_graph_full_ms"] = _time_ms(sm.run, reps, flush)
         else:
-            out["unbatched_numeric_merge_ms"] = _time_ms(numeric_merge, reps, flush)
+            out["unbatched_numeric_merge_ms"] = _time_ms(sm.run, reps, flush)
         out[f"{key}_nnz_c"] = int(sum(sm.c_nnz))
         out["partial_entries"] = int(sum(sm.p_nnz))
         if ref is not None:
@@ -430,9 +436,28 @@ def summa_forms(api, Summa, h, sr, dA, flush, reps, ref=None):
         del sm
         torch.cuda.empty_cache()
     out["speedup_full"] = out["unbatched_full_ms"] / out["batched_full_ms"]
-    out["speedup_numeric_merge"] = (out["unbatched_numeric_merge_ms"]
-                                    / out["batched_graph_numeric_merge_ms"])
+    best = min(out.get("batched_tuned_graph_full_ms", float("inf")), out["batched_graph_full_ms"])
+    out["speedup_graph_full_vs_unbatched"] = out["unbatched_full_ms"] / best
     return out
+
+
+def summa_tuning(api, scale):
+    """Tier limits of the batched SUMMA form, tuned by coordinate descent on a
+    calibration product two R-MAT scales smaller (same generator, other seed),
+    cached per GPU in the autotuner's JSON file."""
+    import torch
+    from paper_2504_06408_gb300 import autotune
+    from paper_2504_06408_gb300 import inputs as I
+    tag = f"summa4x4_rmat{scale - 2}_seed2"
+    t = autotune.load(api.PLUS_TIMES_F64, tag)
+    if t is None:
+        Ac = I.rmat(max(scale - 2, 10), dtype=np.float64, seed=2, lo=0.0, hi=1.0)
+        dAc = api.DeviceCSR.from_host(Ac, val_dtype=np.float64)
+        t = autotune.tune_summa(api.PLUS_TIMES_F64, dAc, dAc, reps=3, sweeps=1)
+        autotune.save(api.PLUS_TIMES_F64, tag, t)
+        del dAc
+        torch.cuda.empty_cache()
+    return t
 
 
 def t_alg_bytes(n, nnz_a, P, nnz_c, s_in, s_out):
@@ -486,6 +511,111 @@ def kmer_form(api, h, flush, reps, peak):
     torch.cuda.empty_cache()
     return {"ms": ms, "gflops": 2.0 * P / (ms * 1e-3) / 1e9, "products": P, "nnz_c": nnz,
             "algorithmic_bytes": t, "hbm_roofline_frac": t / (ms * 1e-3) / 1e9 / peak}
+
+
+def panel_budget(frac=0.12, cap=32 << 30):
+    """Output bytes per row panel: a fraction of the free device memory (the
+    panel's C, its partials and workspaces must fit at once)."""
+    import torch
+    free, _ = torch.cuda.mem_get_info()
+    return int(min(cap, free * frac))
+
+
+def config4_form(api, peak):
+    """R-MAT 20 A^2 over plus-times FP64 (1,048,576 vertices, FP64 weights
+    U[0,1)) as a 4 x 4 Sparse-SUMMA emulation: C is about 294 GB, so the
+    product runs in row panels, each a full 4 x 4 grid (batched: one launch
+    per tier over its 64 block products; unbatched: one call per block and
+    merge), against the unblocked product in the same panels."""
+    import torch
+    from paper_2504_06408_gb300 import inputs as I
+    from paper_2504_06408_gb300.summa import summa_panels
+    sr = api.PLUS_TIMES_F64
+    A = I.rmat(20, dtype=np.float64, seed=1, lo=0.0, hi=1.0)
+    dA = api.DeviceCSR.from_host(A, val_dtype=np.float64)
+    h = api.Handle()
+    budget = panel_budget()
+    out = {"workload": "R-MAT scale 20 A^2, plus-times FP64, 4 x 4 grid, row panels",
+           "panel_output_bytes": budget}
+    nnz = {}
+    st = {}
+    nnz["plain"], out["plain_panels"] = api.panel_product(
+        sr, dA, dA, budget, lambda a, b, C: None, handle=h, stats=st)
+    out["plain_ms"] = sum(st["panel_ms"])
+    for key, batched in (("summa_batched", True), ("summa_unbatched", False)):
+        st = {}
+        tot = [0]
+
+        def on_panel(r0, r1, sm, tot=tot):
+            tot[0] += int(sum(sm.c_nnz))
+
+        out[f"{key}_panels"] = summa_panels(h, sr, dA, dA, budget, on_panel, q=4,
+                                            batched=batched, stats=st)
+        out[f"{key}_ms"] = sum(st["panel_ms"])
+        nnz[key] = tot[0]
+        torch.cuda.empty_cache()
+    ws = torch.empty(h.workspace_size(sr, dA, dA), dtype=torch.uint8, device="cuda")
+    rp = torch.empty(A.nrows + 1, dtype=torch.int64, device="cuda")
+    h.symbolic(sr, dA, dA, rp, ws)
+    P = h.stats()["products"]
+    del ws
+    out["products"] = P
+    out["nnz_c"] = nnz["plain"]
+    out["same_nnz_all_forms"] = len(set(nnz.values())) == 1
+    t = t_alg_bytes(A.nrows, A.nnz, P, nnz["plain"], 8, 8)
+    for key in ("plain", "summa_batched", "summa_unbatched"):
+        ms = out[f"{key}_ms"]
+        out[f"{key}_gflops"] = 2.0 * P / (ms * 1e-3) / 1e9
+        out[f"{key}_hbm_roofline_frac"] = t / (ms * 1e-3) / 1e9 / peak
+    out["summa_batched_vs_unbatched"] = out["summa_unbatched_ms"] / out["summa_batched_ms"]
+    out["summa_batched_vs_unblocked"] = out["summa_batched_ms"] / out["plain_ms"]
+    del dA
+    torch.cuda.empty_cache()
+    return out
+
+
+def config5_form(api, params, meta, peak):
+    """R-MAT 21 A^2 over plus-times FP64 (2,097,152 vertices, FP64 weights
+    U[0,1)): C is about 757 GB, so every form runs in row panels: plain,
+    learned sizing with ub-sized capacities, learned sizing with the trained
+    network."""
+    import torch
+    from paper_2504_06408_gb300 import inputs as I
+    sr = api.PLUS_TIMES_F64
+    A = I.rmat(21, dtype=np.float64, seed=1, lo=0.0, hi=1.0)
+    dA = api.DeviceCSR.from_host(A, val_dtype=np.float64)
+    h = api.Handle()
+    budget = panel_budget()
+    out = {"workload": "R-MAT scale 21 A^2, plus-times FP64, row panels",
+           "panel_output_bytes": budget}
+    nnz = {}
+    forms = (("plain", None), ("learned_ub_sized", {}),
+             ("learned_network", {"model": params, "margin": meta["margin"],
+                                  "exact_max_ub": meta["exact_max_ub"]}))
+    for key, learned in forms:
+        st = {}
+        nnz[key], out[f"{key}_panels"] = api.panel_product(
+            sr, dA, dA, budget, lambda a, b, C: None, handle=h, learned=learned, stats=st)
+        out[f"{key}_ms"] = sum(st["panel_ms"])
+        torch.cuda.empty_cache()
+    ws = torch.empty(h.workspace_size(sr, dA, dA), dtype=torch.uint8, device="cuda")
+    rp = torch.empty(A.nrows + 1, dtype=torch.int64, device="cuda")
+    h.symbolic(sr, dA, dA, rp, ws)
+    P = h.stats()["products"]
+    del ws
+    out["products"] = P
+    out["nnz_c"] = nnz["plain"]
+    out["same_nnz_all_forms"] = len(set(nnz.values())) == 1
+    t = t_alg_bytes(A.nrows, A.nnz, P, nnz["plain"], 8, 8)
+    for key, _ in forms:
+        ms = out[f"{key}_ms"]
+        out[f"{key}_gflops"] = 2.0 * P / (ms * 1e-3) / 1e9
+        out[f"{key}_hbm_roofline_frac"] = t / (ms * 1e-3) / 1e9 / peak
+        if key != "plain":
+            out[f"{key}_speedup_vs_plain"] = out["plain_ms"] / ms
+    del dA
+    torch.cuda.empty_cache()
+    return out
 
 
 # Stand-ins shaped like the paper's Table 2 matrices, multiplied over the
@@ -618,6 +748,8 @@ def main():
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the learned / batched vs plain comparisons")
     ap.add_argument("--form-reps", type=int, default=3)
+    ap.add_argument("--no-big-forms", action="store_true",
+                    help="skip the R-MAT 20 / 21 forms whose C exceeds device memory")
     ap.add_argument("--scale", type=int, default=SCALE,
                     help="R-MAT scale of the product (18 = the headline workload; smaller "
                          "scales are for profiling captures)")
@@ -668,7 +800,7 @@ def main():
     h.check(ws)
     torch.cuda.synchronize()
     h.set_timing(True)
-    times, dense_ms, launches = [], [], 0
+    times, dense_ms, launches, stages = [], [], 0, []
     sampler = ClockSampler(torch.cuda.current_device())
     with sampler:
         barrier()
@@ -680,11 +812,14 @@ def main():
             e0.record(stream)
             h.symbolic(sr, dA, dA, c_rp, ws)
             launches += h.stats()["launches"]
+            sym_st = h.stage_times()
             h.numeric(sr, dA, dA, c_rp, c_col, c_val, ws)
             e1.record(stream)
             torch.cuda.synchronize()
             launches += h.stats()["launches"]
-            dense_ms.append(h.stage_times()["num_dense"])
+            num_st = h.stage_times()
+            dense_ms.append(num_st["num_dense"])
+            stages.append({k: v for st_ in (sym_st, num_st) for k, v in st_.items() if v > 0})
             times.append(e0.elapsed_time(e1))
         torch.cuda.synchronize()
         barrier()
@@ -806,12 +941,20 @@ def main():
         dA64 = api.DeviceCSR.from_host(A64, val_dtype=np.float64)
         pms, _, ref = plain_ms_of(api, h, api.PLUS_TIMES_F64, dA64, dA64, flush, reps, keep=True)
         torch.cuda.empty_cache()
-        sf = summa_forms(api, Summa, h, api.PLUS_TIMES_F64, dA64, flush, reps, ref=ref)
+        tuning = summa_tuning(api, args.scale)
+        sf = summa_forms(api, Summa, h, api.PLUS_TIMES_F64, dA64, flush, reps, ref=ref,
+                         tuning=tuning)
         sf["plain_unblocked_ms"] = pms
+        best = min(sf.get("batched_tuned_graph_full_ms", float("inf")),
+                   sf["batched_graph_full_ms"])
+        sf["batched_graph_full_vs_unblocked"] = best / pms
         forms[f"rmat{args.scale}_plus_times_f64_summa4x4"] = sf
         del dA64, ref
         torch.cuda.empty_cache()
         forms["float_cold_warm"] = cold_warm_forms()
+        if not args.no_big_forms:
+            forms["rmat20_plus_times_f64_summa4x4_panels"] = config4_form(api, peak)
+            forms["rmat21_plus_times_f64_learned_panels"] = config5_form(api, params, meta, peak)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -829,7 +972,10 @@ def main():
                "hbm_compulsory_frac_step": (t_min / (ms_per_step * 1e-3) / 1e9) / peak,
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                "clocks": sampler.summary(), "gpu_launches": launches,
-               "step_ms": times, "forms": forms}
+               "step_ms": times,
+               "stage_ms": {k: statistics.median([st.get(k, 0.0) for st in stages])
+                            for k in sorted({k for st in stages for k in st})},
+               "forms": forms}
         print(json.dumps(res), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -187,6 +187,11 @@ spg_status spgemm_numeric(spg_handle* handle, spg_semiring sr, const spg_csr* A,
  * them, heaviest rows first.  Arrays of nprob descriptors / pointers:
  *   c_row_ptr[p] : device int64 [A_p.nrows + 1];  c_nnz : HOST int64 [nprob].
  * Same workspace rules as the single form (spgemm_workspace_size_batched).
+ * c_nnz may be NULL in spgemm_symbolic_batched: the call then queues its
+ * work and returns without copying anything to the host or synchronising
+ * (kernel-detected errors surface in spgemm_check); the caller has sized C
+ * from an earlier call on the same patterns.  Such a call can be captured
+ * in a CUDA graph together with the numeric and merge calls.
  */
 spg_status spgemm_workspace_size_batched(spg_handle* handle, spg_semiring sr, int nprob,
                                          const spg_csr* A, const spg_csr* B, size_t* bytes);
@@ -219,7 +224,12 @@ spg_status spgemm_merge_stages(spg_handle* handle, spg_semiring sr, int nstages,
                                size_t workspace_bytes, void* stream);
 /* Batched merges (1 <= nmerge <= 32): merge m combines parts[off_m ..
  * off_m + nparts[m]) with off_m = nparts[0] + ... + nparts[m-1].  Count call:
- * c_col == NULL (the array); c_nnz HOST [nmerge]. */
+ * c_col == NULL (the array); c_nnz HOST [nmerge], or NULL: no host copy and
+ * no synchronisation (as spgemm_symbolic_batched with c_nnz NULL).
+ * Merges of at most 2^18 columns run row by row (a warp sorts rows of at
+ * most 32 entries in registers; a CTA merges a longer row through a bitmap of
+ * its columns) and need no copy of the partials' entries in the workspace;
+ * wider ones sort every entry into its merged position. */
 spg_status spgemm_merge_stages_batched(spg_handle* handle, spg_semiring sr, int nmerge,
                                        const int* nparts, const spg_csr* parts,
                                        int64_t* const* c_row_ptr, int64_t* c_nnz,

@@ -73,6 +73,39 @@ def tune(sr: int, dA: api.DeviceCSR, dB: api.DeviceCSR, reps: int = 3, sweeps: i
     return descend(measure, SPACE, best, sweeps, log)
 
 
+def tune_summa(sr: int, dA: api.DeviceCSR, dB: api.DeviceCSR, q: int = 4, reps: int = 3,
+               sweeps: int = 1, start: Optional[Dict[str, int]] = None, log=None,
+               space: Optional[Dict[str, list]] = None) -> Dict[str, int]:
+    """Coordinate descent for the batched Sparse-SUMMA form: each candidate
+    tuning times the CUDA-graph replay of the whole batched product (block
+    symbolic and numeric phases and the merge of the stage partials)."""
+    import torch
+    from .summa import Summa
+
+    def measure(cfg):
+        h = api.Handle(tuning=cfg or None)
+        sm = Summa(h, sr, dA, dB, q=q, batched=True)
+        sm.plan()
+        sm.capture(full=True)
+        sm.run()
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            sm.run()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        sm.check()
+        del sm
+        torch.cuda.empty_cache()
+        return statistics.median(ts)
+
+    return descend(measure, space or SPACE, dict(start or {}), sweeps, log)
+
+
 def descend(measure: Callable[[Dict[str, int]], float], space: Dict[str, list],
             start: Dict[str, int], sweeps: int = 2, log=None) -> Dict[str, int]:
     """Coordinate descent: every field of ``space`` in turn is tried at each

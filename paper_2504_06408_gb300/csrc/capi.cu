@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -54,20 +55,8 @@ namespace spg {
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Slab-start table of B for the numeric dense tier: (nrows_b + 1) x (slabs + 1)
-// int32, kept only while it is no larger than twice B's column array (plus
-// 64 MB); otherwise the dense tier advances per-entry cursors instead.
-static size_t slab_ptr_table_bytes(int64_t nrows_b, int64_t ncols_b, int64_t nnz_b,
-                                   int64_t slab_cols) {
-    if (slab_cols <= 0 || ncols_b <= slab_cols) return 0;
-    const int64_t nslabs = (ncols_b + slab_cols - 1) / slab_cols;
-    const size_t need = (size_t)(nrows_b + 1) * (size_t)(nslabs + 1) * 4;
-    const size_t cap = (size_t)nnz_b * 8 + ((size_t)64 << 20);
-    return need <= cap ? need : 0;
-}
-
-WsLayout ws_layout(int64_t R, int64_t E, int64_t nrows_b, int64_t ncols_b, int64_t nnz_b,
-                   int64_t slab_cols, int64_t cache_bytes) {
+WsLayout ws_layout(int64_t R, int64_t E, size_t slab_bytes, int64_t ncols_b,
+                   int64_t cache_bytes, size_t words_bytes) {
     WsLayout L{};
     L.R = R;
     L.E = E;
@@ -82,7 +71,7 @@ WsLayout ws_layout(int64_t R, int64_t E, int64_t nrows_b, int64_t ncols_b, int64
     const int64_t nparts = (R + 2047) / 2048;
     L.scan_part = o; o = align256(o + sizeof(int64_t) * (size_t)(nparts + 1));
     L.cursor = o;    o = align256(o + sizeof(int32_t) * (size_t)E);
-    L.slab_ptr_bytes = slab_ptr_table_bytes(nrows_b, ncols_b, nnz_b, slab_cols);
+    L.slab_ptr_bytes = slab_bytes;
     L.slab_ptr = o;  o = align256(o + L.slab_ptr_bytes);
     // bitmap cache: one bitmap of ncols_b bits per cached row (rank kernel rows only)
     L.bm_cache_words = (ncols_b + 1023) / 1024 * 32;
@@ -94,6 +83,8 @@ WsLayout ws_layout(int64_t R, int64_t E, int64_t nrows_b, int64_t ncols_b, int64
     L.row_slot = o;  o = align256(o + (L.bm_cache_slots ? sizeof(int32_t) * (size_t)R : 0));
     L.bm_cache_bytes = (size_t)L.bm_cache_slots * (size_t)L.bm_cache_words * 4;
     L.bm_cache = o;  o = align256(o + L.bm_cache_bytes);
+    L.words_bytes = words_bytes;
+    L.words = o;     o = align256(o + words_bytes);
     L.total = o;
     return L;
 }
@@ -207,16 +198,115 @@ static Tuning effective_tuning(const spg_handle* h, int sr) {
     return clamp_tuning(t, sr);
 }
 
+static DCsr to_dcsr(const spg_csr* M) {
+    return DCsr{M->nrows, M->ncols, M->row_ptr, M->col, M->val};
+}
+
+// Distinct B matrices of a call (the same arrays passed for several products
+// count once): idx[p] = the index of product p's B among them; returns their
+// number.
+static int distinct_b(int nprob, const spg_csr* B, int* idx, int* first) {
+    int n = 0;
+    for (int p = 0; p < nprob; ++p) {
+        int j = 0;
+        for (; j < n; ++j) {
+            const spg_csr& o = B[first[j]];
+            if (o.row_ptr == B[p].row_ptr && o.col == B[p].col && o.nrows == B[p].nrows &&
+                o.nnz == B[p].nnz && o.ncols == B[p].ncols)
+                break;
+        }
+        if (j == n) first[n++] = p;
+        idx[p] = j;
+    }
+    return n;
+}
+
+// Room for the word-packed copies of the distinct B matrices (0: the call
+// walks B's columns; the packing pays only for large enough B).
+static size_t words_bytes_for(int nprob, const spg_csr* B) {
+    int idx[kMaxProb], first[kMaxProb];
+    const int n = distinct_b(nprob, B, idx, first);
+    int64_t nnz = 0;
+    size_t bytes = 0;
+    for (int j = 0; j < n; ++j) {
+        nnz += B[first[j]].nnz;
+        bytes += word_pack_bytes(B[first[j]].nrows, B[first[j]].nnz);
+    }
+    return nnz >= kWordPackMinNnz ? bytes : 0;
+}
+
+// Slab-start tables of the numeric dense tier: one per distinct B, all with
+// the launch's slab count (from the widest B); a B whose table would be
+// larger than twice its column array (plus 64 MB) gets none (its rows use
+// per-entry cursors).  Returns the bytes; with `out`, also carves the tables
+// out of `base` and points the products at them.
+static size_t slab_tables(int nprob, const spg_csr* B, const Tuning& t, void* base,
+                          ProbTable* tab, SlabTables* out) {
+    int64_t maxc = 0;
+    for (int p = 0; p < nprob; ++p) maxc = B[p].ncols > maxc ? B[p].ncols : maxc;
+    int64_t slab;
+    int nslabs;
+    dense_slabs(t, maxc, &slab, &nslabs);
+    if (out) {
+        out->n = 0;
+        out->slab = slab;
+        out->nslabs = nslabs;
+    }
+    if (nslabs <= 1) return 0;
+    int idx[kMaxProb], first[kMaxProb];
+    const int n = distinct_b(nprob, B, idx, first);
+    size_t total = 0;
+    int32_t* table[kMaxProb];
+    for (int j = 0; j < n; ++j) {
+        const spg_csr& b = B[first[j]];
+        const size_t need = (size_t)(b.nrows + 1) * (size_t)(nslabs + 1) * 4;
+        const size_t cap = (size_t)b.nnz * 8 + ((size_t)64 << 20);
+        table[j] = nullptr;
+        if (need > cap || b.nnz == 0) continue;
+        if (out) {
+            table[j] = (int32_t*)((char*)base + total);
+            out->B[out->n] = to_dcsr(&b);
+            out->sp[out->n] = table[j];
+            ++out->n;
+        }
+        total += align256(need);
+    }
+    if (tab)
+        for (int p = 0; p < nprob; ++p) tab->p[p].sp = table[idx[p]];
+    return total;
+}
+
+static size_t slab_bytes_for(int nprob, const spg_csr* B, const Tuning& t) {
+    return slab_tables(nprob, B, t, nullptr, nullptr, nullptr);
+}
+
 // workspace of one product: the bitmap cache is kept only when the symbolic
 // dense tier sees whole rows in one slab and SR is not pattern-free of use
 static WsLayout layout_for(const spg_csr* A, const spg_csr* B, const Tuning& t) {
     const int64_t cache = (t.bitmap_cache_bytes > 0 && B->ncols <= t.sym_slab_cols)
                               ? t.bitmap_cache_bytes : 0;
-    return ws_layout(A->nrows, A->nnz, B->nrows, B->ncols, B->nnz, t.dense_slab_cols, cache);
+    return ws_layout(A->nrows, A->nnz, slab_bytes_for(1, B, t), B->ncols, cache,
+                     words_bytes_for(1, B));
 }
 
-static DCsr to_dcsr(const spg_csr* M) {
-    return DCsr{M->nrows, M->ncols, M->row_ptr, M->col, M->val};
+
+
+// Points every product's Prob::Bw at its B's word-packed copy in the
+// workspace (when the layout has room for them) and lists the copies to
+// build; returns whether the symbolic dense tier walks them.
+static bool plan_words(int nprob, const spg_csr* B, void* workspace, const WsLayout& L,
+                       ProbTable* tab, WordPack* wp) {
+    wp->n = 0;
+    if (L.words_bytes == 0) return false;
+    int idx[kMaxProb], first[kMaxProb];
+    wp->n = distinct_b(nprob, B, idx, first);
+    for (int j = 0; j < wp->n; ++j) {
+        wp->src[j] = to_dcsr(B + first[j]);
+        wp->nnz[j] = B[first[j]].nnz;
+    }
+    word_pack_plan(*wp, (char*)workspace + L.words);
+    for (int p = 0; p < nprob; ++p) tab->p[p].Bw = wp->dst[idx[p]];
+    return true;
 }
 
 static spg_status check_csr_arg(spg_handle* h, const spg_csr* M, const char* name, int sr,
@@ -434,7 +524,7 @@ static WsLayout layout_batch(int nprob, const spg_csr* A, const spg_csr* B, cons
     }
     // no slab table for batches (segments come from per-entry cursors)
     const int64_t cache = (t.bitmap_cache_bytes > 0 && maxc <= t.sym_slab_cols) ? t.bitmap_cache_bytes : 0;
-    return ws_layout(R, E, 0, maxc, 0, t.dense_slab_cols, cache);
+    return ws_layout(R, E, slab_bytes_for(nprob, B, t), maxc, cache, words_bytes_for(nprob, B));
 }
 
 static void fill_probs(ProbTable* tab, int nprob, const spg_csr* A, const spg_csr* B,
@@ -442,8 +532,9 @@ static void fill_probs(ProbTable* tab, int nprob, const spg_csr* A, const spg_cs
     std::memset(tab, 0, sizeof *tab);
     int64_t rb = 0, eb = 0;
     for (int p = 0; p < nprob; ++p) {
-        tab->p[p] = Prob{to_dcsr(A + p), to_dcsr(B + p), c_rp[p], c_col ? c_col[p] : nullptr,
-                         c_val ? c_val[p] : nullptr, rb, eb};
+        tab->p[p] = Prob{to_dcsr(A + p), to_dcsr(B + p), DCsr{},   // Bw: set by plan_words
+                         nullptr,                                    // sp: set by plan_slab_tables
+                         c_rp[p], c_col ? c_col[p] : nullptr, c_val ? c_val[p] : nullptr, rb, eb};
         rb += A[p].nrows;
         eb += A[p].nnz;
     }
@@ -480,11 +571,16 @@ static spg_status symbolic_launch(spg_handle* h, int sr, int nprob, const spg_cs
         e = cudaMemsetAsync(w.row_slot, 0xff, sizeof(int32_t) * (size_t)L.R, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "memset");
     ProbTable* tab = new ProbTable;
+    WordPack* wp = new WordPack;
     fill_probs(tab, nprob, A, B, c_row_ptr, nullptr, nullptr);
+    const bool words = plan_words(nprob, B, workspace, L, tab, wp);
     e = launch_write_probs(*tab, nprob, w, h->dev, st);
     delete tab;
     if (e == cudaSuccess) e = launch_analyze(w, nprob, L.R, t, h->dev, st);
-    if (e == cudaSuccess) e = launch_symbolic(w, nprob, L.R, t, max_ncols(nprob, B), h->dev, st);
+    if (e == cudaSuccess && words) e = launch_word_pack(*wp, w.ctr, h->dev, st);
+    delete wp;
+    if (e == cudaSuccess)
+        e = launch_symbolic(w, nprob, L.R, t, max_ncols(nprob, B), h->dev, st, words);
     if (e == cudaSuccess) e = launch_scan_rowptr(w, nprob, L.R, h->dev, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "symbolic launch");
     if (Lout) *Lout = L;
@@ -500,6 +596,7 @@ static spg_status symbolic_impl(spg_handle* h, int sr, int nprob, const spg_csr*
     spg_status s = symbolic_launch(h, sr, nprob, A, B, c_row_ptr, workspace, workspace_bytes, st,
                                    true, &L, &w);
     if (s != SPG_OK) return s;
+    if (!c_nnz) return SPG_OK;   // no host copy, no synchronisation (see the header)
     // bring back nnz, products, bin counts and the status in one copy
     Counters* hc = (Counters*)((char*)h->pinned);
     static_assert(sizeof(Counters) <= kPinnedBytes, "staging buffer too small");
@@ -538,17 +635,23 @@ static spg_status numeric_impl(spg_handle* h, int sr, int nprob, const spg_csr* 
 #endif
     h->launches = 0;
     h->timer.n = 0;
-    ProbTable* tab = new ProbTable;
-    fill_probs(tab, nprob, A, B, const_cast<int64_t* const*>(c_row_ptr), c_col, c_val);
+    std::unique_ptr<ProbTable> tab(new ProbTable);
+    std::unique_ptr<SlabTables> spt(new SlabTables);
+    fill_probs(tab.get(), nprob, A, B, const_cast<int64_t* const*>(c_row_ptr), c_col, c_val);
+    if (w.slab_ptr) slab_tables(nprob, B, t, w.slab_ptr, tab.get(), spt.get());
     cudaError_t e = launch_write_probs(*tab, nprob, w, h->dev, st);
-    delete tab;
 #ifdef SPG_CHECKS
     // C's row pointers must be those of the symbolic call that left this
-    // workspace (their last entry its nnz(C)): no kernel writes C otherwise
-    if (e == cudaSuccess) e = launch_check_rowptr(w, nprob, st);
+    // workspace (their last entry its nnz(C)): no kernel writes C otherwise.
+    // The result goes to the handle's own status, so a refused call leaves
+    // the workspace's error flags as they were.
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->chk_status, 0, sizeof(DevStatus), st);
+    if (e == cudaSuccess) e = launch_check_rowptr(w, nprob, (DevStatus*)h->chk_status, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "row pointer check");
     {
-        const spg_status cs = read_status(h, w, st);
+        WsPtrs cw{};
+        cw.status = (DevStatus*)h->chk_status;
+        const spg_status cs = read_status(h, cw, st);
         if (cs == SPG_ERR_INVALID_CSR) {
             h->err = "checked build: C's row pointers are not those of the symbolic call (" + h->err + ")";
             return cs;
@@ -557,7 +660,8 @@ static spg_status numeric_impl(spg_handle* h, int sr, int nprob, const spg_csr* 
     }
 #endif
     if (e == cudaSuccess)
-        e = launch_numeric(sr, w, to_dcsr(B), nprob, L.R, t, max_ncols(nprob, B), h->dev, st);
+        e = launch_numeric(sr, w, to_dcsr(B), nprob, L.R, t, max_ncols(nprob, B), h->dev, st,
+                           spt.get(), tab.get());
     if (e == cudaSuccess && h->user.deterministic)
         e = launch_det_values(sr, w, nprob, L.R, h->dev, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "numeric launch");
@@ -598,7 +702,7 @@ spg_status spgemm_symbolic_batched(spg_handle* h, spg_semiring sr, int nprob, co
                                    void* workspace, size_t workspace_bytes, void* stream) {
     spg_status s = check_batch(h, sr, nprob, A, B, false);
     if (s != SPG_OK) return s;
-    if (!c_row_ptr || !c_nnz) return fail(h, SPG_ERR_INVALID_ARG, "c_row_ptr / c_nnz is NULL");
+    if (!c_row_ptr) return fail(h, SPG_ERR_INVALID_ARG, "c_row_ptr is NULL");
     for (int p = 0; p < nprob; ++p)
         if (!c_row_ptr[p]) return fail(h, SPG_ERR_INVALID_ARG, "c_row_ptr[%d] is NULL", p);
     return symbolic_impl(h, sr, nprob, A, B, c_row_ptr, c_nnz, workspace, workspace_bytes,
@@ -620,13 +724,14 @@ spg_status spgemm_numeric_batched(spg_handle* h, spg_semiring sr, int nprob, con
 
 static spg_status merge_check(spg_handle* h, int sr, int nmerge, const int* nparts,
                               const spg_csr* parts, int64_t* R, int64_t* T, int64_t* maxp,
-                              int* maxs) {
+                              int* maxs, int64_t* maxc) {
     if (!h) return SPG_ERR_INVALID_ARG;
     if (!sr_valid(sr)) return fail(h, SPG_ERR_INVALID_ARG, "unknown semiring id %d", sr);
     if (nmerge < 1 || nmerge > kMaxMerge || !nparts || !parts)
         return fail(h, SPG_ERR_INVALID_ARG, "merges: 1..%d, nparts and parts non-NULL", kMaxMerge);
     *R = *T = *maxp = 0;
     *maxs = 0;
+    *maxc = 0;
     int off = 0;
     for (int m = 0; m < nmerge; ++m) {
         if (nparts[m] < 1 || nparts[m] > kMaxStages)
@@ -641,6 +746,7 @@ static spg_status merge_check(spg_handle* h, int sr, int nmerge, const int* npar
             if (P->nnz > *maxp) *maxp = P->nnz;
         }
         *R += parts[off].nrows;
+        if (parts[off].ncols > *maxc) *maxc = parts[off].ncols;
         if (nparts[m] > *maxs) *maxs = nparts[m];
         off += nparts[m];
     }
@@ -675,12 +781,12 @@ static void fill_merge_probs(MergeProbTable* tab, int nmerge, const int* nparts,
 
 spg_status spgemm_merge_workspace_size(spg_handle* h, spg_semiring sr, int nmerge,
                                        const int* nparts, const spg_csr* parts, size_t* bytes) {
-    int64_t R, T, mp;
+    int64_t R, T, mp, mc;
     int ms;
-    spg_status s = merge_check(h, sr, nmerge, nparts, parts, &R, &T, &mp, &ms);
+    spg_status s = merge_check(h, sr, nmerge, nparts, parts, &R, &T, &mp, &ms, &mc);
     if (s != SPG_OK) return s;
     if (!bytes) return fail(h, SPG_ERR_INVALID_ARG, "bytes is NULL");
-    *bytes = merge_ws_layout(nullptr, R, T, out_bytes(sr)).total;
+    *bytes = merge_ws_layout(nullptr, R, T, out_bytes(sr), mc).total;
     return SPG_OK;
 }
 
@@ -689,14 +795,14 @@ spg_status spgemm_merge_stages_batched(spg_handle* h, spg_semiring sr, int nmerg
                                        int64_t* const* c_row_ptr, int64_t* c_nnz,
                                        int32_t* const* c_col, void* const* c_val,
                                        void* workspace, size_t workspace_bytes, void* stream) {
-    int64_t R, T, maxp;
+    int64_t R, T, maxp, maxc;
     int maxs;
-    spg_status s = merge_check(h, sr, nmerge, nparts, parts, &R, &T, &maxp, &maxs);
+    spg_status s = merge_check(h, sr, nmerge, nparts, parts, &R, &T, &maxp, &maxs, &maxc);
     if (s != SPG_OK) return s;
     if (!c_row_ptr) return fail(h, SPG_ERR_INVALID_ARG, "c_row_ptr is NULL");
     for (int m = 0; m < nmerge; ++m)
         if (!c_row_ptr[m]) return fail(h, SPG_ERR_INVALID_ARG, "c_row_ptr[%d] is NULL", m);
-    const MergeWs w = merge_ws_layout(workspace, R, T, out_bytes(sr));
+    const MergeWs w = merge_ws_layout(workspace, R, T, out_bytes(sr), maxc);
     if (!workspace || workspace_bytes < w.total)
         return fail(h, SPG_ERR_WORKSPACE, "workspace needs %zu bytes", w.total);
     cudaStream_t st = (cudaStream_t)stream;
@@ -706,15 +812,13 @@ spg_status spgemm_merge_stages_batched(spg_handle* h, spg_semiring sr, int nmerg
     fill_merge_probs(tab, nmerge, nparts, parts, c_row_ptr, c_col, c_val);
     cudaError_t e;
     if (!c_col) {   // count: C row pointers and nnz
-        if (!c_nnz) {
-            delete tab;
-            return fail(h, SPG_ERR_INVALID_ARG, "c_nnz is NULL");
-        }
         e = cudaMemsetAsync(workspace, 0, (char*)w.probs - (char*)workspace, st);
-        if (e == cudaSuccess) e = launch_merge_count(sr, *tab, nmerge, R, maxp, maxs, w, h->dev, st);
+        if (e == cudaSuccess)
+            e = launch_merge_count(sr, *tab, nmerge, R, maxp, maxs, maxc, w, h->dev, st);
         if (e == cudaSuccess) e = launch_merge_rowptr(w, nmerge, h->dev, st);
         delete tab;
         if (e != cudaSuccess) return cuda_fail(h, e, "merge count");
+        if (!c_nnz) return SPG_OK;   // no host copy, no synchronisation (see the header)
         Counters* hc = (Counters*)h->pinned;
         e = cudaMemcpyAsync(hc, w.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -727,7 +831,7 @@ spg_status spgemm_merge_stages_batched(spg_handle* h, spg_semiring sr, int nmerg
             delete tab;
             return fail(h, SPG_ERR_INVALID_ARG, "c_col / c_val of merge %d is NULL", m);
         }
-    e = launch_merge_write(sr, *tab, nmerge, R, w, h->dev, st);
+    e = launch_merge_write(sr, *tab, nmerge, R, maxc, w, h->dev, st);
     delete tab;
     if (e != cudaSuccess) return cuda_fail(h, e, "merge write");
     return SPG_OK;
@@ -798,7 +902,7 @@ spg_status spgemm_split_columns(spg_handle* h, const spg_csr* M, int nparts, con
 
 spg_status spgemm_check(spg_handle* h, void* workspace, void* stream) {
     if (!h || !workspace) return SPG_ERR_INVALID_ARG;
-    const WsLayout L = ws_layout(0, 0);
+    const WsLayout L = ws_layout(0, 0, 0, 0, 0, 0);
     return read_status(h, ws_ptrs(workspace, L), (cudaStream_t)stream);
 }
 
@@ -1214,14 +1318,18 @@ spg_status spgemm_learned_symbolic(spg_handle* h, spg_semiring sr, const spg_csr
         e = cudaMemsetAsync(w.row_slot, 0xff, sizeof(int32_t) * (size_t)L.R, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "memset");
     ProbTable* tab = new ProbTable;
+    WordPack* wp = new WordPack;
     fill_probs(tab, 1, A, B, &c_row_ptr, nullptr, nullptr);
+    const bool words = plan_words(1, B, workspace, L, tab, wp);
     e = launch_write_probs(*tab, 1, w, h->dev, st);
     delete tab;
     if (e == cudaSuccess)
         e = launch_learned_direct(sr, w, lw, 1, L.R, h->lrn_warp_max, h->lrn_block_max, h->dev, st);
     w.skip = lw.skip;
     if (e == cudaSuccess) e = launch_analyze(w, 1, L.R, t, h->dev, st);
-    if (e == cudaSuccess) e = launch_symbolic(w, 1, L.R, t, B->ncols, h->dev, st);
+    if (e == cudaSuccess && words) e = launch_word_pack(*wp, w.ctr, h->dev, st);
+    delete wp;
+    if (e == cudaSuccess) e = launch_symbolic(w, 1, L.R, t, B->ncols, h->dev, st, words);
     if (e == cudaSuccess) e = launch_scan_rowptr(w, 1, L.R, h->dev, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "learned symbolic launch");
     Counters* hc = (Counters*)h->pinned;
@@ -1263,13 +1371,17 @@ spg_status spgemm_learned_numeric(spg_handle* h, spg_semiring sr, const spg_csr*
     h->launches = 0;
     h->timer.n = 0;
     ProbTable* tab = new ProbTable;
+    SlabTables* spt = new SlabTables;
     int64_t* rp = const_cast<int64_t*>(c_row_ptr);
     fill_probs(tab, 1, A, B, &rp, &c_col, &c_val);
+    if (w.slab_ptr) slab_tables(1, B, t, w.slab_ptr, tab, spt);
     cudaError_t e = launch_write_probs(*tab, 1, w, h->dev, st);
-    delete tab;
     if (e == cudaSuccess) e = launch_learned_compact(sr, w, lw, 1, L.R, h->dev, st);
     w.skip = lw.skip;
-    if (e == cudaSuccess) e = launch_numeric(sr, w, to_dcsr(B), 1, L.R, t, B->ncols, h->dev, st);
+    if (e == cudaSuccess)
+        e = launch_numeric(sr, w, to_dcsr(B), 1, L.R, t, B->ncols, h->dev, st, spt, tab);
+    delete spt;
+    delete tab;
     w.skip = nullptr;
     if (e == cudaSuccess && h->user.deterministic)
         e = launch_det_values(sr, w, 1, L.R, h->dev, st);

@@ -25,6 +25,14 @@ struct DCsr {
 // g - row_base of A.
 struct Prob {
     DCsr A, B;
+    // B packed by 32-column words for the symbolic dense tier: row k lists the
+    // distinct words w of B_k's columns (ascending, col = w) with the mask of
+    // B_k's columns in w (val, uint32); rp == nullptr when not built
+    DCsr Bw;
+    // slab starts of B's rows for the numeric dense tier: sp[k * stride + s] =
+    // offset in row k of its first column >= s * slab width (stride = the
+    // launch's slab count + 1); nullptr: none (per-entry cursors instead)
+    const int32_t* sp;
     int64_t* c_rp;       // output row pointers [A.nrows + 1]
     int32_t* c_col;      // output columns [nnz(C)]
     void* c_val;         // output values  [nnz(C)]

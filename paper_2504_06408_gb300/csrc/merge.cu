@@ -141,6 +141,205 @@ __global__ void k_merge_write(const MergeProb* __restrict__ mp, int nprob, int64
     }
 }
 
+
+// ---- merge by rows (merges of at most kMergeBitmapCols columns) ------------------
+//
+// Light rows (at most 32 entries over all partials): a warp loads them, one
+// per lane, sorts (column, stage) in registers and folds each run of equal
+// columns in stage order.  Heavy rows: a CTA ORs the row's columns into a
+// shared-memory bitmap; the prefix count of the bitmap words gives every
+// column its rank in the merged row (the count is the last prefix); the
+// stages are then taken in order (a barrier between stages): an entry whose
+// column has not been written yet writes C at its rank, a later one folds its
+// value into it with (+).  Both are deterministic: every column's value is the
+// stage-order fold of the definition, as in the sequence-sort path above.
+
+constexpr int kMergeThreads = 256;
+constexpr int kClMergeHeavy = 14;   // Counters::claim slot: length of the heavy-row list
+
+// stage of entry q of a row from the stages' inclusive prefix ends (held by
+// lanes 0..nparts-1): the number of stages whose end is <= q (all lanes call)
+SPG_DEV int merge_stage_of(int64_t incl, int nparts, int64_t q) {
+    int s = 0;
+    for (int t = 0; t < nparts; ++t) s += (__shfl_sync(kFull, incl, t) <= q) ? 1 : 0;
+    return s;
+}
+
+template <class S, bool kWrite>
+__global__ void __launch_bounds__(256)
+    k_merge_light(const MergeProb* __restrict__ mp, int nprob, int64_t R, int64_t* cnt,
+                  int32_t* heavy, Counters* ctr, DevStatus* st) {
+    using Out = typename S::Out;
+    const int lane = lane_id();
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); g < R; g += nw) {
+        const MergeProb& M = mp[nprob == 1 ? 0 : find_merge_prob(mp, nprob, g)];
+        const int64_t i = g - M.row_base;
+        int64_t a = 0, len = 0;
+        if (lane < M.nparts) {
+            a = ld_i64(M.rp[lane] + i);
+            len = ld_i64(M.rp[lane] + i + 1) - a;
+        }
+        const int64_t incl = warp_incl_scan(len);
+        const int64_t total = __shfl_sync(kFull, incl, 31);
+        if (total > 32) {   // heavy row: listed by the count call, merged by k_merge_heavy
+            if (!kWrite && lane == 0) heavy[atomicAdd(&ctr->claim[kClMergeHeavy], 1)] = (int32_t)g;
+            continue;
+        }
+        if (total == 0) {
+            if (!kWrite && lane == 0) cnt[g] = 0;
+            continue;
+        }
+        // lane q < total takes entry q of the row (stages in order, columns in order)
+        const int s = merge_stage_of(incl, M.nparts, lane);
+        const int64_t ex = __shfl_sync(kFull, incl - len, s & 31);
+        const int64_t as = __shfl_sync(kFull, a, s & 31);
+        uint64_t key = ~0ull;
+        Out v{};
+        if (lane < total) {
+            const int64_t q = as + (lane - ex);
+            const int32_t c = ld_i32(M.col[s] + q);
+            key = ((uint64_t)(uint32_t)c << 9) | ((uint64_t)s << 5) | (uint64_t)lane;
+            if constexpr (kWrite && S::kVal) v = reinterpret_cast<const Out*>(M.val[s])[q];
+        }
+        // ascending bitonic sort of the keys (column, stage, source lane)
+#pragma unroll
+        for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                const uint64_t o = __shfl_xor_sync(kFull, key, j);
+                const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
+                key = keep_min ? (o < key ? o : key) : (o > key ? o : key);
+            }
+        }
+        const bool valid = key != ~0ull;
+        const uint32_t col = (uint32_t)(key >> 9);
+        const uint32_t prev = __shfl_up_sync(kFull, col, 1);
+        const bool head = valid && (lane == 0 || prev != col);
+        const unsigned hm = __ballot_sync(kFull, head);
+        if constexpr (!kWrite) {
+            if (lane == 0) cnt[g] = __popc(hm);
+        } else {
+            // the values in sorted order, then each run folded left to right
+            const Out sv = shfl_words<0>(v, (int)(key & 31u));
+            Out acc = sv;
+            bool run = head;
+            for (int d = 1; d < kMaxStages; ++d) {   // a run holds at most one entry per stage
+                const Out nv = shfl_words<2>(sv, d);
+                const uint32_t nc = __shfl_down_sync(kFull, col, d);
+                const uint64_t nk = __shfl_down_sync(kFull, key, d);
+                run = run && lane + d < 32 && nk != ~0ull && nc == col;
+                if constexpr (S::kVal) {
+                    if (run) acc = S::add(acc, nv);
+                }
+                if (!__any_sync(kFull, run)) break;
+            }
+            const int64_t off = M.c_rp[i], n = M.c_rp[i + 1] - off;
+            if (head) {
+                const int r = __popc(hm & ((1u << lane) - 1u));
+                if (r < n) {
+                    M.c_col[off + r] = (int32_t)col;
+                    if constexpr (S::kVal) reinterpret_cast<Out*>(M.c_val)[off + r] = acc;
+                } else {
+                    flag_overflow(st, g);
+                }
+            }
+        }
+    }
+}
+
+// shared-memory bytes of k_merge_heavy for rows of `ncols` columns
+__host__ __device__ inline size_t merge_heavy_smem(int64_t ncols) {
+    const size_t words = (size_t)((ncols + 31) >> 5);
+    return (words + 1) * 8 + words * 4;
+}
+
+template <class S, bool kWrite>
+__global__ void __launch_bounds__(kMergeThreads)
+    k_merge_heavy(const MergeProb* __restrict__ mp, int nprob, const int32_t* __restrict__ heavy,
+                  const Counters* __restrict__ ctr, int64_t* cnt, DevStatus* st) {
+    using Out = typename S::Out;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_wsum[kMergeThreads / 32];
+    const int tid = threadIdx.x, lane = lane_id(), wid = warp_id();
+    constexpr int nwarps = kMergeThreads / 32;
+    const int nheavy = ctr->claim[kClMergeHeavy];
+    for (int r = blockIdx.x; r < nheavy; r += gridDim.x) {
+        const int64_t g = heavy[r];
+        const MergeProb& M = mp[nprob == 1 ? 0 : find_merge_prob(mp, nprob, g)];
+        const int64_t i = g - M.row_base;
+        const int words = (int)((M.ncols + 31) >> 5);
+        // (word, prefix) pairs of the row's bitmap, then the written bits
+        uint2* pw = reinterpret_cast<uint2*>(smem_raw);
+        uint32_t* done = reinterpret_cast<uint32_t*>(smem_raw + ((size_t)words + 1) * 8);
+        for (int w = tid; w < words; w += kMergeThreads) {
+            pw[w] = make_uint2(0u, 0u);
+            if (kWrite) done[w] = 0u;
+        }
+        __syncthreads();
+        for (int s = 0; s < M.nparts; ++s) {
+            const int64_t a = ld_i64(M.rp[s] + i), b = ld_i64(M.rp[s] + i + 1);
+            for (int64_t q = a + tid; q < b; q += kMergeThreads) {
+                const int32_t c = ld_i32(M.col[s] + q);
+                const uint32_t bit = 1u << (c & 31);
+                uint32_t* wp = &pw[c >> 5].x;
+                if (!(*wp & bit)) atomicOr(wp, bit);
+            }
+        }
+        __syncthreads();
+        // prefix count of the words (contiguous words per thread)
+        const int wpt = (words + kMergeThreads - 1) / kMergeThreads;
+        const int w0 = tid * wpt;
+        int mine = 0;
+        for (int j = 0; j < wpt; ++j)
+            if (w0 + j < words) mine += __popc(pw[w0 + j].x);
+        const int incl = warp_incl_scan(mine);
+        if (lane == 31) s_wsum[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            const int x = lane < nwarps ? s_wsum[lane] : 0;
+            const int xi = warp_incl_scan(x);
+            if (lane < nwarps) s_wsum[lane] = xi - x;
+            if (!kWrite && lane == 31) cnt[g] = xi;   // lanes >= nwarps add nothing
+        }
+        __syncthreads();
+        if constexpr (kWrite) {
+            int run = s_wsum[wid] + incl - mine;
+            for (int j = 0; j < wpt; ++j)
+                if (w0 + j < words) {
+                    pw[w0 + j].y = (uint32_t)run;
+                    run += __popc(pw[w0 + j].x);
+                }
+            __syncthreads();
+            const int64_t off = M.c_rp[i], n = M.c_rp[i + 1] - off;
+            Out* cv = reinterpret_cast<Out*>(M.c_val);
+            for (int s = 0; s < M.nparts; ++s) {   // stage order: (+) folds left to right
+                const int64_t a = ld_i64(M.rp[s] + i), b = ld_i64(M.rp[s] + i + 1);
+                for (int64_t q = a + tid; q < b; q += kMergeThreads) {
+                    const int32_t c = ld_i32(M.col[s] + q);
+                    const uint2 e = pw[c >> 5];
+                    const uint32_t bit = 1u << (c & 31);
+                    const int64_t rk = (int64_t)e.y + __popc(e.x & (bit - 1u));
+                    if (rk >= n) {
+                        flag_overflow(st, g);
+                        continue;
+                    }
+                    if (!(done[c >> 5] & bit)) {   // the first stage that holds this column
+                        M.c_col[off + rk] = c;
+                        if constexpr (S::kVal) cv[off + rk] = reinterpret_cast<const Out*>(M.val[s])[q];
+                        atomicOr(done + (c >> 5), bit);
+                    } else {
+                        if constexpr (S::kVal)
+                            cv[off + rk] = S::add(cv[off + rk], reinterpret_cast<const Out*>(M.val[s])[q]);
+                    }
+                }
+                __syncthreads();   // this stage's values land before the next stage folds into them
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // ---- column split --------------------------------------------------------------
 
 // warp per row: counts of each part's columns in the row -> prp[p][i + 1]
@@ -220,9 +419,39 @@ struct MergeLaunch {
     bool count_only;
     const DevInfo* dev;
     cudaStream_t st;
+    int64_t max_ncols = 0;
     cudaError_t err = cudaSuccess;
+    template <class S> void row_path() {
+        int64_t blocks = (R + 7) / 8;
+        if (blocks > (int64_t)dev->sms * 16) blocks = (int64_t)dev->sms * 16;
+        if (blocks < 1) blocks = 1;
+        const size_t smem = merge_heavy_smem(max_ncols);
+        if (count_only) {
+            k_merge_light<S, false><<<(unsigned)blocks, 256, 0, st>>>(w->probs, nprob, R, w->cnt,
+                                                                       w->heavy, w->ctr, w->status);
+            err = cudaFuncSetAttribute(k_merge_heavy<S, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (err != cudaSuccess) return;
+            k_merge_heavy<S, false><<<dev->sms * 4, kMergeThreads, smem, st>>>(
+                w->probs, nprob, w->heavy, w->ctr, w->cnt, w->status);
+        } else {
+            k_merge_light<S, true><<<(unsigned)blocks, 256, 0, st>>>(w->probs, nprob, R, w->cnt,
+                                                                      w->heavy, w->ctr, w->status);
+            err = cudaFuncSetAttribute(k_merge_heavy<S, true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (err != cudaSuccess) return;
+            k_merge_heavy<S, true><<<dev->sms * 4, kMergeThreads, smem, st>>>(
+                w->probs, nprob, w->heavy, w->ctr, w->cnt, w->status);
+        }
+        count_launch(*dev, 2);
+        err = cudaGetLastError();
+    }
     template <class S> void operator()() {
         using Out = typename S::Out;
+        if (w->row_path) {
+            row_path<S>();
+            return;
+        }
         Out* tval = reinterpret_cast<Out*>(w->tval);
         if (count_only) {
             int64_t gx = (max_part_nnz + 255) / 256;
@@ -250,21 +479,24 @@ struct MergeLaunch {
 };
 
 cudaError_t launch_merge_count(int sr, const MergeProbTable& tab, int nprob, int64_t R,
-                               int64_t max_part_nnz, int max_parts, const MergeWs& w,
-                               const DevInfo& dev, cudaStream_t st) {
+                               int64_t max_part_nnz, int max_parts, int64_t max_ncols,
+                               const MergeWs& w, const DevInfo& dev, cudaStream_t st) {
     mark_stage(dev, kStBegin, st);
     k_write_merge_probs<<<1, kMaxProb, 0, st>>>(tab, nprob, w.probs);
     count_launch(dev);
-    if (R > 0) {
-        int64_t blocks = (R + 255) / 256;
-        if (blocks > (int64_t)dev.sms * 8) blocks = (int64_t)dev.sms * 8;
-        k_merge_rowlen<<<(unsigned)blocks, 256, 0, st>>>(w.probs, nprob, R, w.trp);
-        count_launch(dev);
+    cudaError_t e = cudaSuccess;
+    if (!w.row_path) {
+        if (R > 0) {
+            int64_t blocks = (R + 255) / 256;
+            if (blocks > (int64_t)dev.sms * 8) blocks = (int64_t)dev.sms * 8;
+            k_merge_rowlen<<<(unsigned)blocks, 256, 0, st>>>(w.probs, nprob, R, w.trp);
+            count_launch(dev);
+        }
+        e = launch_scan_inplace(w.trp, R, w.part, st);   // trp -> row starts
+        if (e != cudaSuccess) return e;
+        count_launch(dev, R > 0 ? 3 : 0);
     }
-    cudaError_t e = launch_scan_inplace(w.trp, R, w.part, st);   // trp -> row starts
-    if (e != cudaSuccess) return e;
-    count_launch(dev, R > 0 ? 3 : 0);
-    MergeLaunch f{&w, nprob, R, max_part_nnz, max_parts, true, &dev, st};
+    MergeLaunch f{&w, nprob, R, max_part_nnz, max_parts, true, &dev, st, max_ncols};
     if (!dispatch_semiring(sr, f)) return cudaErrorInvalidValue;
     if (f.err != cudaSuccess) return f.err;
     e = launch_scan_inplace(w.cnt, R, w.part, st);                // cnt -> C row starts (flat)
@@ -279,29 +511,35 @@ cudaError_t launch_merge_rowptr(const MergeWs& w, int nprob, const DevInfo& dev,
     return cudaGetLastError();
 }
 
-MergeWs merge_ws_layout(void* base, int64_t R, int64_t T, int out_bytes) {
+MergeWs merge_ws_layout(void* base, int64_t R, int64_t T, int out_bytes, int64_t max_ncols) {
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     char* b = (char*)base;
     MergeWs w{};
+    // merges of at most kMergeBitmapCols columns take the row kernels, which
+    // need no copy of the partials' entries
+    w.row_path = max_ncols <= kMergeBitmapCols;
+    const int64_t Tt = w.row_path ? 0 : T;
     size_t o = 0;
     w.status = (DevStatus*)(b + o);  o = al(o + sizeof(DevStatus));
     w.ctr = (Counters*)(b + o);      o = al(o + sizeof(Counters));
     w.probs = (MergeProb*)(b + o);   o = al(o + sizeof(MergeProb) * kMaxMerge);
-    w.trp = (int64_t*)(b + o);       o = al(o + sizeof(int64_t) * (size_t)(R + 1));
+    w.trp = (int64_t*)(b + o);       o = al(o + (w.row_path ? 0 : sizeof(int64_t) * (size_t)(R + 1)));
     w.cnt = (int64_t*)(b + o);       o = al(o + sizeof(int64_t) * (size_t)(R + 1));
-    w.tcol = (int32_t*)(b + o);      o = al(o + sizeof(int32_t) * (size_t)T);
-    w.tval = (void*)(b + o);         o = al(o + (size_t)out_bytes * (size_t)T);
+    w.heavy = (int32_t*)(b + o);     o = al(o + (w.row_path ? sizeof(int32_t) * (size_t)R : 0));
+    w.tcol = (int32_t*)(b + o);      o = al(o + sizeof(int32_t) * (size_t)Tt);
+    w.tval = (void*)(b + o);         o = al(o + (size_t)out_bytes * (size_t)Tt);
     w.part = (int64_t*)(b + o);      o = al(o + sizeof(int64_t) * (size_t)scan_parts_needed(R));
     w.total = o;
     return w;
 }
 
 cudaError_t launch_merge_write(int sr, const MergeProbTable& tab, int nprob, int64_t R,
-                               const MergeWs& w, const DevInfo& dev, cudaStream_t st) {
+                               int64_t max_ncols, const MergeWs& w, const DevInfo& dev,
+                               cudaStream_t st) {
     mark_stage(dev, kStBegin, st);
     k_write_merge_probs<<<1, kMaxProb, 0, st>>>(tab, nprob, w.probs);
     count_launch(dev);
-    MergeLaunch f{&w, nprob, R, 0, 0, false, &dev, st};
+    MergeLaunch f{&w, nprob, R, 0, 0, false, &dev, st, max_ncols};
     if (!dispatch_semiring(sr, f)) return cudaErrorInvalidValue;
     mark_stage(dev, kStMerge, st);
     return f.err;

@@ -22,11 +22,34 @@ SPG_DEV int64_t dev_next_pow2_n(int64_t x) {
     return x <= 1 ? 1 : (int64_t)1 << (64 - __clzll(x - 1));
 }
 
-SPG_DEV int num_tier(int64_t nnz, const Tuning& t) {
+// block_max: the block tier's limit in effect (the tuning's, or the compact
+// overlap tier's when the positions allow it, set on the device)
+SPG_DEV int num_tier(int64_t nnz, const Tuning& t, int64_t block_max) {
     if (nnz == 0) return kTierEmpty;
     if (nnz <= t.num_warp_max_nnz) return kTierWarp;
-    if (nnz <= t.num_block_max_nnz) return kTierBlock;
+    if (nnz <= block_max) return kTierBlock;
     return kTierDense;
+}
+
+SPG_DEV int64_t block_limit(const Tuning& t, const Counters* ctr) {
+    return ctr->num_block_max > 0 ? ctr->num_block_max : t.num_block_max_nnz;
+}
+
+// Overlap semiring: positions of A and B all in [0, 2^16)?  Clears
+// ctr->num_block_max (block 0) and raises ctr->ovl_wide on a position outside.
+__global__ void k_ovl_check(DCsr M, Counters* ctr) {
+    const int64_t e0 = M.rp[0], e1 = M.rp[M.nrows];
+    const int32_t* v = reinterpret_cast<const int32_t*>(M.val);
+    bool wide = false;
+    for (int64_t e = e0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < e1;
+         e += (int64_t)gridDim.x * blockDim.x)
+        wide |= (uint32_t)ld_i32(v + e) > 0xffffu;
+    if (__any_sync(kFull, wide) && lane_id() == 0) atomicExch(&ctr->ovl_wide, 1);
+}
+
+// block-tier limit of the compact overlap tier when every position fits 16 bits
+__global__ void k_ovl_limit(Counters* ctr, int64_t compact_max) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) ctr->num_block_max = ctr->ovl_wide ? 0 : compact_max;
 }
 
 // as the symbolic bins: tiny rows (ub <= 32) of the warp tier in its last sub-bin
@@ -55,7 +78,7 @@ __global__ void __launch_bounds__(256) k_num_hist(const Prob* __restrict__ probs
          g += (int64_t)gridDim.x * blockDim.x) {
         const Prob* P;
         const int64_t n = row_nnz(probs, nprob, g, &P);
-        const int tier = (skip && skip[g]) ? kTierEmpty : num_tier(n, t);
+        const int tier = (skip && skip[g]) ? kTierEmpty : num_tier(n, t, block_limit(t, ctr));
         atomicAdd(&s_hist[num_bin_key(tier, ub[g])], 1);
     }
     __syncthreads();
@@ -89,7 +112,8 @@ __global__ void __launch_bounds__(1024) k_num_scatter(const Prob* __restrict__ p
     if (g < R) {
         const Prob* P;
         const int64_t n = row_nnz(probs, nprob, g, &P);
-        key = num_bin_key((skip && skip[g]) ? kTierEmpty : num_tier(n, t), ub[g]);
+        key = num_bin_key((skip && skip[g]) ? kTierEmpty : num_tier(n, t, block_limit(t, ctr)),
+                          ub[g]);
         rank = atomicAdd(&s_cnt[key], 1);
     }
     __syncthreads();
@@ -267,13 +291,20 @@ __global__ void __launch_bounds__(kWarpTierWarps * 32)
 template <class S>
 __global__ void __launch_bounds__(kBlockThreads)
     k_num_block(const Prob* __restrict__ probs, int nprob, const int32_t* __restrict__ rows,
-                Counters* ctr, DevStatus* st, int Tb) {
+                Counters* ctr, DevStatus* st, int Tb, int only_wide) {
     using Slot = typename S::Slot;
     using In = typename S::In;
+    // compact overlap slots: tables up to 3/4 full and a sort buffer of a
+    // whole table (the rows are twice as long for the same memory)
+    constexpr bool kC = std::is_same<S, SrOverlapC>::value;
+    // the compact kernel runs when every position fits 16 bits, the 24-byte
+    // one launched beside it (only_wide) when one does not
+    if (kC && ctr->ovl_wide) return;
+    if (only_wide && !ctr->ovl_wide) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Slot* vals = reinterpret_cast<Slot*>(smem_raw);
     int32_t* keys = reinterpret_cast<int32_t*>(smem_raw + (size_t)Tb * sizeof(Slot));
-    int32_t* sbuf = keys + Tb;
+    int32_t* sbuf = keys + Tb;   // [Tb / 2], or [Tb] with compact slots
     __shared__ BatchSmem<In> bs;
     __shared__ int s_row, s_m;
     const int lane = lane_id();
@@ -293,7 +324,7 @@ __global__ void __launch_bounds__(kBlockThreads)
         const int64_t i = g - P.row_base;
         const int64_t off = P.c_rp[i];
         const int n = (int)(P.c_rp[i + 1] - off);
-        int T = (int)dev_next_pow2_n(2 * (int64_t)n);
+        int T = (int)dev_next_pow2_n(kC ? (4 * (int64_t)n + 2) / 3 : 2 * (int64_t)n);
         if (T < 32) T = 32;
         if (T > Tb) {
             if (threadIdx.x == 0) flag_overflow(st, g);
@@ -317,7 +348,7 @@ __global__ void __launch_bounds__(kBlockThreads)
             if (lane == 0 && occ) b = atomicAdd(&s_m, __popc(occ));
             b = __shfl_sync(kFull, b, 0);
             const int pos = b + __popc(occ & ((1u << lane) - 1));
-            if (k != kEmptyKey && pos < T / 2) sbuf[pos] = k;
+            if (k != kEmptyKey && pos < (kC ? T : T / 2)) sbuf[pos] = k;
         }
         __syncthreads();
         const int m = s_m;
@@ -429,8 +460,7 @@ SPG_DEV void small_row_slab_products(const DCsr& B, const SmallRowSmem<typename 
 template <class S>
 __global__ void __launch_bounds__(kBlockThreads, 2)
     k_num_dense(const Prob* __restrict__ probs, int nprob, const int32_t* __restrict__ rows,
-                Counters* ctr, DevStatus* st, int32_t* cursor, int slab_cols,
-                const int32_t* __restrict__ sp, int sp_stride) {
+                Counters* ctr, DevStatus* st, int32_t* cursor, int slab_cols, int sp_stride) {
     using Slot = typename S::Slot;
     using In = typename S::In;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -462,6 +492,7 @@ __global__ void __launch_bounds__(kBlockThreads, 2)
         const int64_t a0 = ld_i64(P.A.rp + i), a1 = ld_i64(P.A.rp + i + 1);
         const int64_t ncols = P.B.ncols;
         const int nslabs = (int)((ncols + slab_cols - 1) / slab_cols);
+        const int32_t* __restrict__ sp = P.sp;
         // small rows: <= 32 entries, slab table available (or one slab)
         const bool small = a1 - a0 <= 32 && (sp != nullptr || nslabs == 1);
         const bool one_batch = !small && a1 - a0 <= kBatch;
@@ -731,7 +762,7 @@ __host__ __device__ inline size_t rank_region_bytes(int64_t cap) {
 template <class S>
 __global__ void __launch_bounds__(kRankThreads, 1)
     k_num_rank(const Prob* __restrict__ probs, int nprob, const int32_t* __restrict__ rows,
-               Counters* ctr, DevStatus* st, const int32_t* __restrict__ sp, int sp_stride,
+               Counters* ctr, DevStatus* st, int sp_stride,
                int slab_cols, int bm_words, int cap, const uint32_t* __restrict__ bm_cache,
                const int32_t* __restrict__ row_slot, int cache_words, int64_t cache_slots,
                int stage_words) {
@@ -775,6 +806,7 @@ __global__ void __launch_bounds__(kRankThreads, 1)
         const int ncols = (int)P.B.ncols;
         const int words = (ncols + 31) >> 5;
         const int nslabs = (ncols + slab_cols - 1) / slab_cols;
+        const int32_t* __restrict__ sp = P.sp;   // this product's slab-start table, or null
         const RowEntries mode = a1 - a0 <= 32 ? kEntriesPerLane
                                 : a1 - a0 <= kRankThreads ? kEntriesPerThread : kEntriesBatched;
         // (a slot outside the cache means the workspace did not come from this
@@ -1119,24 +1151,25 @@ struct NumericLaunch {
     int64_t max_ncols;
     const DevInfo* dev;
     cudaStream_t st;
+    const SlabTables* tables;
     cudaError_t err = cudaSuccess;
     template <class S> void operator()() {
         cudaError_t e;
         {   // dense tier
-            int64_t slab = t->dense_slab_cols;
-            if (slab > max_ncols) slab = (max_ncols + 1023) / 1024 * 1024;
-            if (slab < 1024) slab = 1024;
+            int64_t slab;
+            int nslabs;
+            dense_slabs(*t, max_ncols, &slab, &nslabs);
             const size_t smem = num_dense_bytes<S>(slab);
             e = cudaFuncSetAttribute(k_num_dense<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem);
             if (e != cudaSuccess) { err = e; return; }
-            const int nslabs = (int)((max_ncols + slab - 1) / slab);
-            const int32_t* sp = nullptr;
-            if (nprob == 1 && w->slab_ptr &&
-                (size_t)(B0.nrows + 1) * (nslabs + 1) * 4 <= w->slab_ptr_bytes && nslabs > 1) {
-                k_slab_ptr<<<dev->sms * 8, 256, 0, st>>>(B0, (int)slab, nslabs, w->slab_ptr, w->ctr);
+            // the slab-start table of every distinct B (skipped on the device
+            // when no row is in the dense tier)
+            const bool sp = tables && tables->n > 0;
+            for (int j = 0; sp && j < tables->n; ++j) {
+                k_slab_ptr<<<dev->sms * 8, 256, 0, st>>>(tables->B[j], (int)slab, nslabs,
+                                                         tables->sp[j], w->ctr);
                 count_launch(*dev);
-                sp = w->slab_ptr;
             }
             mark_stage(*dev, kStSlabPtr, st);
             // rank-indexed kernel when the row bitmap, its prefix and a value
@@ -1164,7 +1197,7 @@ struct NumericLaunch {
                 const int grid = occupancy_grid((const void*)k_num_rank<S>, kRankThreads, rsmem, *dev);
                 const bool cached = w->bm_cache && w->bm_cache_words >= bm_words;
                 k_num_rank<S><<<grid, kRankThreads, rsmem, st>>>(
-                    w->probs, nprob, w->rows_num, w->ctr, w->status, sp, nslabs + 1, (int)slab,
+                    w->probs, nprob, w->rows_num, w->ctr, w->status, nslabs + 1, (int)slab,
                     (int)bm_words, (int)cap, cached ? w->bm_cache : nullptr,
                     cached ? w->row_slot : nullptr, (int)w->bm_cache_words, w->bm_cache_slots,
                     stage_words);
@@ -1172,13 +1205,29 @@ struct NumericLaunch {
             } else {
                 const int grid = occupancy_grid((const void*)k_num_dense<S>, kBlockThreads, smem, *dev);
                 k_num_dense<S><<<grid, kBlockThreads, smem, st>>>(w->probs, nprob, w->rows_num, w->ctr,
-                                                                  w->status, w->cursor, (int)slab, sp,
+                                                                  w->status, w->cursor, (int)slab,
                                                                   nslabs + 1);
                 count_launch(*dev);
             }
             mark_stage(*dev, kStNumDense, st);
         }
         {   // block tier
+            int only_wide = 0;
+            if constexpr (std::is_same<S, SrOverlap>::value) {
+                // compact slots first (they leave every row to the 24-byte
+                // kernel when a position needs more than 16 bits)
+                const int64_t Tc = next_pow2((4 * kOvlCompactMax + 2) / 3);
+                const size_t smc = (size_t)Tc * (sizeof(OvSlotC) + 8);
+                e = cudaFuncSetAttribute(k_num_block<SrOverlapC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
+                if (e != cudaSuccess) { err = e; return; }
+                const int gc = occupancy_grid((const void*)k_num_block<SrOverlapC>, kBlockThreads,
+                                              smc, *dev);
+                k_num_block<SrOverlapC><<<gc, kBlockThreads, smc, st>>>(
+                    w->probs, nprob, w->rows_num, w->ctr, w->status, (int)Tc, 0);
+                count_launch(*dev);
+                only_wide = 1;
+            }
             int64_t T = next_pow2(2 * t->num_block_max_nnz);
             if (T < 32) T = 32;
             const size_t smem = num_block_bytes<S>(*t);
@@ -1187,7 +1236,7 @@ struct NumericLaunch {
             if (e != cudaSuccess) { err = e; return; }
             const int grid = occupancy_grid((const void*)k_num_block<S>, kBlockThreads, smem, *dev);
             k_num_block<S><<<grid, kBlockThreads, smem, st>>>(w->probs, nprob, w->rows_num, w->ctr,
-                                                              w->status, (int)T);
+                                                              w->status, (int)T, only_wide);
             count_launch(*dev);
             mark_stage(*dev, kStNumBlock, st);
         }
@@ -1210,13 +1259,38 @@ struct NumericLaunch {
     }
 };
 
+void dense_slabs(const Tuning& t, int64_t max_ncols, int64_t* slab, int* nslabs) {
+    int64_t s = t.dense_slab_cols;
+    if (s > max_ncols) s = (max_ncols + 1023) / 1024 * 1024;
+    if (s < 1024) s = 1024;
+    *slab = s;
+    *nslabs = (int)((max_ncols + s - 1) / s);
+}
+
 cudaError_t launch_numeric(int sr, const WsPtrs& w, const DCsr& B0, int nprob, int64_t R,
                            const Tuning& t, int64_t max_ncols, const DevInfo& dev,
-                           cudaStream_t st) {
+                           cudaStream_t st, const SlabTables* tables, const ProbTable* probs_host) {
     if (R == 0) return cudaSuccess;
     // reset numeric bins and claims
     cudaMemsetAsync(w.ctr->num_bin_count, 0, sizeof(w.ctr->num_bin_count), st);
     cudaMemsetAsync(&w.ctr->claim[2], 0, 2 * sizeof(int32_t), st);
+    cudaMemsetAsync(&w.ctr->ovl_wide, 0, sizeof(int32_t), st);
+    cudaMemsetAsync(&w.ctr->num_block_max, 0, sizeof(int64_t), st);
+    if (sr == SR_OVERLAP && t.num_block_max_nnz < kOvlCompactMax) {
+        // the compact overlap block tier, when every position of every A and
+        // B fits 16 bits
+        for (int p = 0; p < nprob && probs_host; ++p) {
+            const DCsr* mats[2] = {&probs_host->p[p].A, &probs_host->p[p].B};
+            for (const DCsr* M : mats) {
+                int64_t blocks = (M->nrows + 255) / 256;
+                if (blocks > (int64_t)dev.sms * 8) blocks = (int64_t)dev.sms * 8;
+                if (blocks < 1) blocks = 1;
+                if (M->val) k_ovl_check<<<(unsigned)blocks, 256, 0, st>>>(*M, w.ctr);
+            }
+        }
+        k_ovl_limit<<<1, 32, 0, st>>>(w.ctr, probs_host ? kOvlCompactMax : 0);
+        count_launch(dev, 2 * nprob + 1);
+    }
     int64_t blocks = (R + 255) / 256;
     if (blocks > (int64_t)dev.sms * 8) blocks = (int64_t)dev.sms * 8;
     k_num_hist<<<(unsigned)blocks, 256, 0, st>>>(w.probs, nprob, R, t, w.ub, w.ctr, w.skip);
@@ -1227,7 +1301,7 @@ cudaError_t launch_numeric(int sr, const WsPtrs& w, const DCsr& B0, int nprob, i
     mark_stage(dev, kStNumBin, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    NumericLaunch f{&w, B0, nprob, &t, max_ncols, &dev, st};
+    NumericLaunch f{&w, B0, nprob, &t, max_ncols, &dev, st, tables};
     if (!dispatch_semiring(sr, f)) return cudaErrorInvalidValue;
     return f.err;
 }

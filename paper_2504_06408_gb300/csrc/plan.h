@@ -46,22 +46,28 @@ struct Counters {
     int32_t claim[16];                  // per-kernel dynamic row counters
     int32_t bm_next;                    // next free bitmap cache slot
     unsigned long long products;        // sum of ub over all rows
+    unsigned long long dense_products;  // sum of ub over the symbolic dense tier's rows
+    int32_t words_ready;                // the word-packed copies of B were built
+    int32_t ovl_wide;                   // overlap semiring: a position is outside [0, 2^16)
+    int64_t num_block_max;              // numeric: block-tier limit in effect (0: the tuning's)
     unsigned long long learned_nnz;     // learned path: entries of the rows it finished
     int64_t nnz[kMaxProb];              // per-product nnz(C)
 };
 
 struct WsLayout {
     size_t status, counters, probs, ub, cnt, rows_sym, rows_num, scan_part, cursor, slab_ptr,
-        slab_ptr_bytes, row_slot, bm_cache, bm_cache_bytes, total;
+        slab_ptr_bytes, row_slot, bm_cache, bm_cache_bytes, words, words_bytes, total;
     int64_t bm_cache_words, bm_cache_slots;
     int64_t R;          // flat rows
     int64_t E;          // flat entries of A (cursor array length)
 };
 
-// R flat rows, E flat entries of A; nrows_b / ncols_b / nnz_b of B and the
-// numeric dense slab width size the optional slab-start table
-WsLayout ws_layout(int64_t R, int64_t E, int64_t nrows_b = 0, int64_t ncols_b = 0,
-                   int64_t nnz_b = 0, int64_t slab_cols = 0, int64_t cache_bytes = 0);
+// R flat rows, E flat entries of A; slab_bytes: the slab-start tables of the
+// distinct B matrices; ncols_b: columns of the widest B (bitmap cache rows);
+// words_bytes: room for the word-packed copies of B (word_pack_bytes of each
+// distinct B)
+WsLayout ws_layout(int64_t R, int64_t E, size_t slab_bytes, int64_t ncols_b,
+                   int64_t cache_bytes, size_t words_bytes);
 
 struct WsPtrs {
     DevStatus* status;
@@ -114,13 +120,42 @@ inline void mark_stage(const DevInfo& d, int tag, cudaStream_t st) {
     }
 }
 
+// ---- word-packed B for the symbolic dense tier (symbolic.cu) ----
+//
+// Row k of Bw holds one entry per distinct 32-column word of B_k: col = the
+// word index (column >> 5), val = the uint32 mask of B_k's columns in that
+// word.  The symbolic dense tier ORs whole masks into the row bitmap: one
+// product per word instead of one per column.
+// Bytes of one packed copy (worst case: every entry in its own word).
+size_t word_pack_bytes(int64_t nrows, int64_t nnz);
+// Use the packed walk at all: B large enough that packing pays for its launches.
+constexpr int64_t kWordPackMinNnz = 65536;
+struct WordPack {
+    int n = 0;                  // distinct B matrices to pack
+    DCsr src[kMaxProb];
+    int64_t nnz[kMaxProb];      // entries of each src (its row pointers may be a view's)
+    DCsr dst[kMaxProb];         // dst.rp / col / val point into the workspace
+    int64_t* part[kMaxProb];    // scan scratch of each
+};
+// carves the copies out of [base, base + word_pack_bytes...) and fills dst
+void word_pack_plan(WordPack& wp, void* base);
+// packs every src into dst when the symbolic dense tier's products are at
+// least 4 x the entries of all src (packing costs about one pass over B):
+// decided on the device from launch_analyze's counters, which then carry
+// words_ready for the symbolic dense tier
+cudaError_t launch_word_pack(const WordPack& wp, Counters* ctr, const DevInfo& dev,
+                             cudaStream_t st);
+
 // ---- launchers (asynchronous on `st`; return the launch error) ----
 cudaError_t launch_write_probs(const ProbTable& tab, int nprob, const WsPtrs& w,
                                const DevInfo& dev, cudaStream_t st);
 cudaError_t launch_analyze(const WsPtrs& w, int nprob, int64_t R, const Tuning& t,
                            const DevInfo& dev, cudaStream_t st);
+// words: every product's Prob.Bw is built (launch_word_pack): the dense tier
+// walks the packed copies
 cudaError_t launch_symbolic(const WsPtrs& w, int nprob, int64_t R, const Tuning& t,
-                            int64_t max_ncols, const DevInfo& dev, cudaStream_t st);
+                            int64_t max_ncols, const DevInfo& dev, cudaStream_t st,
+                            bool words = false);
 cudaError_t launch_scan_rowptr(const WsPtrs& w, int nprob, int64_t R, const DevInfo& dev,
                                cudaStream_t st);
 // in-place exclusive scan of cnt[0, R) (int64), cnt[R] = total; part holds
@@ -131,13 +166,28 @@ cudaError_t launch_transpose(const DCsr& A, int64_t nnz, int value_bytes, int64_
                              int32_t* t_col, void* t_val, void* ws, const DevInfo& dev,
                              cudaStream_t st);
 size_t transpose_ws_bytes(int64_t ncols, int64_t nnz);
+// Slab-start tables of the numeric dense tier, one per distinct B of a call
+// (Prob::sp points into them): built by launch_numeric before its kernels.
+struct SlabTables {
+    int n = 0;
+    int64_t slab = 0;           // slab width (columns)
+    int nslabs = 0;             // slabs of the widest B; every table's stride is nslabs + 1
+    DCsr B[kMaxProb];
+    int32_t* sp[kMaxProb];
+};
+// effective slab width and count of a launch over B's of at most max_ncols columns
+void dense_slabs(const Tuning& t, int64_t max_ncols, int64_t* slab, int* nslabs);
 cudaError_t launch_numeric(int sr, const WsPtrs& w, const DCsr& B0, int nprob, int64_t R,
                            const Tuning& t, int64_t max_ncols, const DevInfo& dev,
-                           cudaStream_t st);
+                           cudaStream_t st, const SlabTables* tables = nullptr,
+                           const ProbTable* probs_host = nullptr);
+// overlap semiring: rows of up to this many outputs take the CTA hash tier
+// with 12-byte slots when every position of A and B is below 2^16
+constexpr int64_t kOvlCompactMax = 6144;
 cudaError_t launch_validate(const DCsr& M, int64_t nnz, DevStatus* status, cudaStream_t st);
 // C's row pointers of every product against the nnz its symbolic call counted
 // (status->invalid on a mismatch); used by the checked build
-cudaError_t launch_check_rowptr(const WsPtrs& w, int nprob, cudaStream_t st);
+cudaError_t launch_check_rowptr(const WsPtrs& w, int nprob, DevStatus* status, cudaStream_t st);
 // masked product (masked.cu): accumulators per mask entry; cnt = C's row
 // pointers (R + 1), counted then scanned in place
 size_t masked_slot_bytes(int sr);
@@ -190,7 +240,12 @@ SPG_DEV int find_merge_prob(const MergeProb* mp, int nprob, int64_t g) {
     return lo;
 }
 
+// merges of at most this many columns run row by row (bitmap per heavy row)
+constexpr int64_t kMergeBitmapCols = (int64_t)1 << 18;
+
 struct MergeWs {
+    bool row_path;   // row kernels (else: sort every entry into the merged sequence)
+    int32_t* heavy;  // [R] rows with more than 32 entries (row path)
     DevStatus* status;
     Counters* ctr;
     MergeProb* probs;
@@ -201,14 +256,15 @@ struct MergeWs {
     int64_t* part;   // scan partials
     size_t total;
 };
-MergeWs merge_ws_layout(void* base, int64_t R, int64_t T, int out_bytes);
+MergeWs merge_ws_layout(void* base, int64_t R, int64_t T, int out_bytes, int64_t max_ncols);
 
 cudaError_t launch_merge_count(int sr, const MergeProbTable& tab, int nprob, int64_t R,
-                               int64_t max_part_nnz, int max_parts, const MergeWs& w,
-                               const DevInfo& dev, cudaStream_t st);
+                               int64_t max_part_nnz, int max_parts, int64_t max_ncols,
+                               const MergeWs& w, const DevInfo& dev, cudaStream_t st);
 cudaError_t launch_merge_rowptr(const MergeWs& w, int nprob, const DevInfo& dev, cudaStream_t st);
 cudaError_t launch_merge_write(int sr, const MergeProbTable& tab, int nprob, int64_t R,
-                               const MergeWs& w, const DevInfo& dev, cudaStream_t st);
+                               int64_t max_ncols, const MergeWs& w, const DevInfo& dev,
+                               cudaStream_t st);
 cudaError_t launch_split_columns(const DCsr& M, int nparts, const int32_t* cuts_dev,
                                  int64_t* prp, int64_t* part_base_dev, int32_t* pcol, void* pval,
                                  int vbytes, int64_t* part, const DevInfo& dev, cudaStream_t st);

@@ -188,6 +188,40 @@ struct SrOverlap {
     }
 };
 
+// The overlap semiring on positions below 2^16 (k-mer positions in reads of
+// fewer than 65,536 k-mers): a pair packs into 32 bits as a << 16 | b, whose
+// unsigned order is still lexicographic, so a slot is 12 bytes (count and
+// the two smallest packed pairs) instead of 24, and the CTA hash tier holds
+// rows of twice as many outputs.  Same (x), (+) and output record as
+// SrOverlap; used only after the inputs' positions were checked on the device.
+struct OvSlotC {
+    unsigned int m1, m2, count;
+};
+constexpr unsigned int kNoPairC = 0xffffffffu;
+
+struct SrOverlapC {
+    using In = int32_t;
+    using Slot = OvSlotC;
+    using Out = OvRecord;
+    static constexpr bool kVal = true, kBitmap = false;
+    static SPG_DEV Slot empty() { return OvSlotC{kNoPairC, kNoPairC, 0u}; }
+    static SPG_DEV void acc(Slot* s, In a, In b) {
+        const unsigned int x = ((unsigned int)a << 16) | (unsigned int)b;
+        atomicAdd(&s->count, 1u);
+        if (x >= *(volatile unsigned int*)&s->m2) return;
+        const unsigned int old = atomicMin(&s->m1, x);
+        atomicMin(&s->m2, old > x ? old : x);
+    }
+    static SPG_DEV bool touched(const Slot& v) { return v.count != 0u; }
+    static SPG_DEV int32_t hi(unsigned int x) { return x == kNoPairC ? INT32_MAX : (int32_t)(x >> 16); }
+    static SPG_DEV int32_t lo(unsigned int x) { return x == kNoPairC ? INT32_MAX : (int32_t)(x & 0xffffu); }
+    static SPG_DEV Out out(const Slot& v) {
+        return OvRecord{(int32_t)v.count, hi(v.m1), lo(v.m1), hi(v.m2), lo(v.m2)};
+    }
+    static SPG_DEV Out prod(In a, In b) { return SrOverlap::prod(a, b); }
+    static SPG_DEV Out add(const Out& x, const Out& y) { return SrOverlap::add(x, y); }
+};
+
 // Calls f.template operator()<S>() with the semiring type of a runtime id.
 template <class F>
 inline bool dispatch_semiring(int sr, F&& f) {

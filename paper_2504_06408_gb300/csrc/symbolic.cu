@@ -8,6 +8,8 @@
 //   block : one CTA per row, key-only hash table in the CTA's shared memory
 //   dense : one CTA per row, a bitmap over a slab of columns in shared
 //           memory, slab after slab; nnz = popcount.
+#include <type_traits>
+
 #include "plan.h"
 #include "rowwork.cuh"
 #include "semiring.cuh"
@@ -43,21 +45,27 @@ __global__ void k_write_probs(ProbTable tab, int nprob, Prob* dst) {
 // ub_i, the empty rows' counts, the symbolic bin histogram and P = sum ub:
 // pass 1, 32 consecutive rows per warp; rows with more than kRowShort entries
 // go to the long list (skipped rows keep the ub they have).
-SPG_DEV void analyze_add(int* s_hist, unsigned long long& prod, int64_t g, int64_t s, bool skipped,
-                         const Tuning& t, int64_t* ub, int64_t* cnt) {
+SPG_DEV void analyze_add(int* s_hist, unsigned long long& prod, unsigned long long& dprod,
+                         int64_t g, int64_t s, bool skipped, const Tuning& t, int64_t* ub,
+                         int64_t* cnt) {
     if (skipped) {
         s = ub[g];
     } else {
         ub[g] = s;
         if (s == 0) cnt[g] = 0;
     }
-    atomicAdd(&s_hist[bin_key(skipped ? kTierEmpty : sym_tier(s, t), s)], 1);
+    const int tier = skipped ? kTierEmpty : sym_tier(s, t);
+    atomicAdd(&s_hist[bin_key(tier, s)], 1);
     prod += (unsigned long long)s;
+    if (tier == kTierDense) dprod += (unsigned long long)s;
 }
 
-SPG_DEV void analyze_flush(int* s_hist, unsigned long long prod, Counters* ctr) {
+SPG_DEV void analyze_flush(int* s_hist, unsigned long long prod, unsigned long long dprod,
+                           Counters* ctr) {
     prod = warp_sum(prod);
+    dprod = warp_sum(dprod);
     if (lane_id() == 0 && prod) atomicAdd(&ctr->products, prod);
+    if (lane_id() == 0 && dprod) atomicAdd(&ctr->dense_products, dprod);
     __syncthreads();
     for (int b = threadIdx.x; b < kNumBins; b += blockDim.x)
         if (s_hist[b]) atomicAdd(&ctr->sym_bin_count[b], s_hist[b]);
@@ -72,7 +80,7 @@ __global__ void __launch_bounds__(256) k_analyze(const Prob* __restrict__ probs,
     for (int b = threadIdx.x; b < kNumBins; b += blockDim.x) s_hist[b] = 0;
     __syncthreads();
     const int lane = lane_id();
-    unsigned long long prod = 0;
+    unsigned long long prod = 0, dprod = 0;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t g0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id()) * 32; g0 < R;
          g0 += nw * 32) {
@@ -88,14 +96,14 @@ __global__ void __launch_bounds__(256) k_analyze(const Prob* __restrict__ probs,
             } else {
                 int64_t s, mx;
                 lane_row_counts(probs[rr.pi], rr.a0, na, s, mx);
-                analyze_add(s_hist, prod, g, s, false, t, ub, cnt);
+                analyze_add(s_hist, prod, dprod, g, s, false, t, ub, cnt);
             }
         } else if (skipped) {
-            analyze_add(s_hist, prod, g, 0, true, t, ub, cnt);
+            analyze_add(s_hist, prod, dprod, g, 0, true, t, ub, cnt);
         }
         append_rows(is_long, g, long_rows, ctr);
     }
-    analyze_flush(s_hist, prod, ctr);
+    analyze_flush(s_hist, prod, dprod, ctr);
 }
 
 // pass 2: a warp per long row
@@ -106,7 +114,7 @@ __global__ void __launch_bounds__(256) k_analyze_long(const Prob* __restrict__ p
     __shared__ int s_hist[kNumBins];
     for (int b = threadIdx.x; b < kNumBins; b += blockDim.x) s_hist[b] = 0;
     __syncthreads();
-    unsigned long long prod = 0;
+    unsigned long long prod = 0, dprod = 0;
     const int n = ctr->claim[kClLongRows];
     const int nw = gridDim.x * (blockDim.x >> 5);
     for (int r = blockIdx.x * (blockDim.x >> 5) + warp_id(); r < n; r += nw) {
@@ -114,9 +122,9 @@ __global__ void __launch_bounds__(256) k_analyze_long(const Prob* __restrict__ p
         const RowRange rr = row_range(probs, nprob, g);
         int64_t s, mx;
         warp_row_long(probs[rr.pi], rr.a0, rr.a1, s, mx);
-        if (lane_id() == 0) analyze_add(s_hist, prod, g, s, false, t, ub, cnt);
+        if (lane_id() == 0) analyze_add(s_hist, prod, dprod, g, s, false, t, ub, cnt);
     }
-    analyze_flush(s_hist, prod, ctr);
+    analyze_flush(s_hist, prod, dprod, ctr);
 }
 
 // exclusive scan of the kNumBins bin counts (tiny: one thread)
@@ -313,22 +321,182 @@ struct BitOrOp {
     SPG_DEV void sorted(int32_t col, char a, char b, bool valid) { any(col, a, b, valid); }
 };
 
+// The same on the word-packed B: one entry = the mask of B_k's columns in one
+// 32-column word (w relative to the slab's first word lo); the word is ORed
+// in whole, after a read, so words whose columns are all set already cost no
+// atomic.
+struct BitOrMaskOp {
+    uint32_t* bm;
+    int32_t lo;
+    SPG_DEV void any(int32_t w, uint32_t, uint32_t mask, bool valid) {
+        if (!valid) return;
+        uint32_t* p = bm + (w - lo);
+        if ((*p & mask) != mask) atomicOr(p, mask);
+    }
+    SPG_DEV void sorted(int32_t w, uint32_t a, uint32_t mask, bool valid) { any(w, a, mask, valid); }
+};
+
+// ---- word-packed B ----------------------------------------------------------------
+
+__device__ __forceinline__ bool no_dense_rows(const Counters* ctr) {
+    return ctr->sym_bin_off[(kTierDense + 1) * kSubBins] == ctr->sym_bin_off[kTierDense * kSubBins];
+}
+
+// pack only when the dense tier's walk visits B's entries many times over
+__device__ __forceinline__ bool pack_pays(const Counters* ctr, int64_t min_products) {
+    return !no_dense_rows(ctr) && ctr->dense_products >= (unsigned long long)min_products;
+}
+
+// distinct words of each row of B (a warp per row, 32 entries at a time):
+// wrp[k] = count (scanned into row pointers afterwards)
+__global__ void k_bw_count(DCsr B, int64_t* wrp, Counters* ctr, int64_t min_products) {
+    if (!pack_pays(ctr, min_products)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctr->words_ready = 1;
+    const int lane = lane_id();
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); k < B.nrows; k += nw) {
+        const int64_t rs = ld_i64(B.rp + k), re = ld_i64(B.rp + k + 1);
+        int32_t carry = -1;   // word of the previous chunk's last entry
+        int64_t n = 0;
+        for (int64_t q0 = rs; q0 < re; q0 += 32) {
+            const int64_t q = q0 + lane;
+            const bool v = q < re;
+            const int32_t w = v ? (ld_i32(B.col + q) >> 5) : -1;
+            int32_t prev = __shfl_up_sync(kFull, w, 1);
+            if (lane == 0) prev = carry;
+            n += __popc(__ballot_sync(kFull, v && w != prev));
+            const int last = (int)min((int64_t)31, re - 1 - q0);
+            carry = __shfl_sync(kFull, w, last);
+        }
+        if (lane == 0) wrp[k] = n;
+    }
+}
+
+// the packed rows: word ids and the OR of their columns' bits; a run of equal
+// words (columns ascending) gets one entry, continued across 32-entry chunks
+__global__ void k_bw_fill(DCsr B, DCsr Bw, const Counters* ctr, int64_t min_products) {
+    if (!pack_pays(ctr, min_products)) return;
+    const int lane = lane_id();
+    int32_t* wcol = const_cast<int32_t*>(Bw.col);
+    uint32_t* wmask = reinterpret_cast<uint32_t*>(const_cast<void*>(Bw.val));
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp_id(); k < B.nrows; k += nw) {
+        const int64_t rs = ld_i64(B.rp + k), re = ld_i64(B.rp + k + 1);
+        const int64_t base = ld_i64(Bw.rp + k);
+        int32_t cw = -1;       // last word of the previous chunk and its mask so far
+        uint32_t cm = 0u;
+        int64_t heads = 0;     // entries written for this row so far
+        for (int64_t q0 = rs; q0 < re; q0 += 32) {
+            const int64_t q = q0 + lane;
+            const bool v = q < re;
+            const int32_t c = v ? ld_i32(B.col + q) : 0;
+            const int32_t w = v ? (c >> 5) : -1 - lane;   // invalid lanes: distinct words
+            int32_t prev = __shfl_up_sync(kFull, w, 1);
+            if (lane == 0) prev = cw;
+            const bool head = v && w != prev;
+            const unsigned hm = __ballot_sync(kFull, head);
+            // entry of this lane's run: heads so far, counting its own (the
+            // first run may continue the previous chunk's last entry)
+            const int64_t idx = base + heads + __popc(hm & (0xffffffffu >> (31 - lane))) - 1;
+            uint32_t m = v ? (1u << (c & 31)) : 0u;
+            if (lane == 0 && v && !head) m |= cm;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t om = __shfl_up_sync(kFull, m, d);
+                const int32_t ow = __shfl_up_sync(kFull, w, d);
+                if (lane >= d && ow == w) m |= om;
+            }
+            const int32_t nxt = __shfl_down_sync(kFull, w, 1);
+            const bool tail = v && (lane == 31 || nxt != w);
+            if (tail) {
+                wcol[idx] = w;
+                wmask[idx] = m;
+            }
+            heads += __popc(hm);
+            const int last = (int)min((int64_t)31, re - 1 - q0);
+            cw = __shfl_sync(kFull, w, last);
+            cm = __shfl_sync(kFull, m, last);
+            __syncwarp();   // a run continued by the next chunk rewrites its entry after this
+        }
+    }
+}
+
+size_t word_pack_bytes(int64_t nrows, int64_t nnz) {
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    return al(sizeof(int64_t) * (size_t)(nrows + 1)) + 2 * al(sizeof(int32_t) * (size_t)nnz) +
+           al(sizeof(int64_t) * (size_t)scan_parts_needed(nrows + 1));
+}
+
+void word_pack_plan(WordPack& wp, void* base) {
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    char* b = (char*)base;
+    for (int i = 0; i < wp.n; ++i) {
+        const DCsr& B = wp.src[i];
+        DCsr& D = wp.dst[i];
+        D.nrows = B.nrows;
+        D.ncols = (B.ncols + 31) / 32;
+        D.rp = (const int64_t*)b;
+        b += al(sizeof(int64_t) * (size_t)(B.nrows + 1));
+        D.col = (const int32_t*)b;
+        b += al(sizeof(int32_t) * (size_t)wp.nnz[i]);
+        D.val = (const void*)b;
+        b += al(sizeof(int32_t) * (size_t)wp.nnz[i]);
+        wp.part[i] = (int64_t*)b;
+        b += al(sizeof(int64_t) * (size_t)scan_parts_needed(B.nrows + 1));
+    }
+}
+
+cudaError_t launch_word_pack(const WordPack& wp, Counters* ctr, const DevInfo& dev,
+                             cudaStream_t st) {
+    int64_t nnz = 0;
+    for (int i = 0; i < wp.n; ++i) nnz += wp.nnz[i];
+    const int64_t min_products = 4 * nnz;
+    for (int i = 0; i < wp.n; ++i) {
+        const DCsr& B = wp.src[i];
+        if (B.nrows == 0) continue;
+        int64_t blocks = (B.nrows + 7) / 8;
+        if (blocks > (int64_t)dev.sms * 16) blocks = (int64_t)dev.sms * 16;
+        int64_t* wrp = const_cast<int64_t*>(wp.dst[i].rp);
+        k_bw_count<<<(unsigned)blocks, 256, 0, st>>>(B, wrp, ctr, min_products);
+        cudaError_t e = launch_scan_inplace(wrp, B.nrows, wp.part[i], st);
+        if (e != cudaSuccess) return e;
+        k_bw_fill<<<(unsigned)blocks, 256, 0, st>>>(B, wp.dst[i], ctr, min_products);
+        count_launch(dev, 5);
+    }
+    return cudaGetLastError();
+}
+
 // 3 CTAs of 512 threads per SM (registers capped at 42): the walk is latency-bound,
 // more resident warps measured ~12% faster than 2 CTAs at 64 registers, and 6
-// windows of 32 products in flight per warp ~5% faster than 4
+// windows of 32 products in flight per warp ~5% faster than 4.
+// kWords: the walk goes over the word-packed B (Prob::Bw): one entry per
+// distinct 32-column word of each B row, its mask ORed into the bitmap; the
+// slab bounds, cursors and segment lengths are then in words and packed
+// entries.  The walk loads one value per A entry and per B entry; in the
+// packed walk B's value is the mask and A's is a placeholder (A's column
+// array, which has one element per entry of A and is never empty when a row
+// has entries).
 constexpr int kSymDenseWin = 6;
+template <bool kWords>
 __global__ void __launch_bounds__(kBlockThreads, 3)
     k_sym_dense(const Prob* __restrict__ probs, int nprob, const int32_t* __restrict__ rows,
                 Counters* ctr, int64_t* __restrict__ cnt, int32_t* cursor, int slab_cols,
                 uint32_t* bm_cache, int32_t* row_slot, int64_t cache_words, int64_t cache_slots) {
+    using In = typename std::conditional<kWords, uint32_t, char>::type;
+    using Op = typename std::conditional<kWords, BitOrMaskOp, BitOrOp>::type;
     extern __shared__ uint32_t smem_u32[];
     uint32_t* bm = smem_u32;
-    __shared__ BatchSmem<char> bs;
+    __shared__ BatchSmem<In> bs;
     __shared__ int s_row, s_slot;
     __shared__ unsigned long long s_tot;
+    // both walks are launched when the copies may have been built; the one
+    // that does not match words_ready leaves every row to the other
+    if ((ctr->words_ready != 0) != kWords) return;
     const int lane = lane_id();
     const int beg = ctr->sym_bin_off[kTierDense * kSubBins];
     const int end = ctr->sym_bin_off[(kTierDense + 1) * kSubBins];
+    // slab width in the walked matrix's columns (words when packed)
+    const int slab_x = kWords ? slab_cols / 32 : slab_cols;
     for (;;) {
         if (threadIdx.x == 0) {
             s_row = beg + atomicAdd(&ctr->claim[1], 1);
@@ -341,29 +509,32 @@ __global__ void __launch_bounds__(kBlockThreads, 3)
         const Prob& P = probs[nprob == 1 ? 0 : find_prob(probs, nprob, g)];
         const int64_t i = g - P.row_base;
         const int64_t a0 = ld_i64(P.A.rp + i), a1 = ld_i64(P.A.rp + i + 1);
-        const int64_t ncols = P.B.ncols;
-        const int nslabs = (int)((ncols + slab_cols - 1) / slab_cols);
+        DCsr Ax = P.A;
+        if constexpr (kWords) Ax.val = P.A.col;
+        const DCsr& Bx = kWords ? P.Bw : P.B;
+        const int64_t ncols_x = kWords ? (P.B.ncols + 31) / 32 : P.B.ncols;
+        const int nslabs = (int)((ncols_x + slab_x - 1) / slab_x);
         for (int s = 0; s < nslabs; ++s) {
-            const int32_t lo = (int32_t)((int64_t)s * slab_cols);
-            const int64_t hi64 = (int64_t)lo + slab_cols < ncols ? (int64_t)lo + slab_cols : ncols;
+            const int32_t lo = (int32_t)((int64_t)s * slab_x);
+            const int64_t hi64 = (int64_t)lo + slab_x < ncols_x ? (int64_t)lo + slab_x : ncols_x;
             const int32_t hi = (int32_t)hi64;
-            const int words = (hi - lo + 31) >> 5;
+            const int words = kWords ? hi - lo : (hi - lo + 31) >> 5;
             for (int w = threadIdx.x; w < words; w += blockDim.x) bm[w] = 0u;
             __syncthreads();
-            BitOrOp op{bm, lo};
+            Op op{bm, lo};
             if (nslabs == 1 && a1 - a0 <= 32) {
                 // <= 32 entries: every warp holds the entry table and takes an
                 // equal share of the products (no batch compaction)
-                LaneEntry<char, false> le;
-                le.load(P.A, P.B, a0 + lane, a0 + lane < a1);
+                LaneEntry<In, kWords> le;
+                le.load(Ax, Bx, a0 + lane, a0 + lane < a1);
                 int64_t b, e;
                 le.range(nullptr, 0, 1, 0, 1, b, e);
-                warp_table_walk<char, false, BitOrOp, kSymDenseWin>(P.B, b, e, char(), op);
+                warp_table_walk<In, kWords, Op, kSymDenseWin>(Bx, b, e, le.a, op);
                 __syncthreads();
             } else {
                 const Slab slab{lo, hi, s == 0, s == nslabs - 1, nslabs == 1, cursor, nullptr, 0, s};
-                cta_row_products<char, false, BitOrOp, kBatch, kSymDenseWin>(
-                    P.A, P.B, a0, a1, P.nnz_base + (a0 - ld_i64(P.A.rp)), slab, bs, op);
+                cta_row_products<In, kWords, Op, kBatch, kSymDenseWin>(
+                    Ax, Bx, a0, a1, P.nnz_base + (a0 - ld_i64(P.A.rp)), slab, bs, op);
             }
             if (nslabs == 1 && cache_slots > 0 && words <= cache_words) {
                 // keep the row's bitmap for the numeric phase while cache slots last
@@ -520,8 +691,8 @@ __global__ void k_check_rowptr(const Prob* __restrict__ probs, const Counters* c
 
 // ---- launchers -------------------------------------------------------------------
 
-cudaError_t launch_check_rowptr(const WsPtrs& w, int nprob, cudaStream_t st) {
-    k_check_rowptr<<<dim3(64, nprob), 256, 0, st>>>(w.probs, w.ctr, w.status);
+cudaError_t launch_check_rowptr(const WsPtrs& w, int nprob, DevStatus* status, cudaStream_t st) {
+    k_check_rowptr<<<dim3(64, nprob), 256, 0, st>>>(w.probs, w.ctr, status);
     return cudaGetLastError();
 }
 
@@ -570,24 +741,33 @@ static int occupancy(const void* fn, int threads, size_t smem, const DevInfo& de
     return per_sm * dev.sms;
 }
 
+template <bool kWords>
+static cudaError_t launch_sym_dense(const WsPtrs& w, int nprob, int64_t slab, size_t smem,
+                                   const DevInfo& dev, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(k_sym_dense<kWords>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = occupancy((const void*)k_sym_dense<kWords>, kBlockThreads, smem, dev);
+    k_sym_dense<kWords><<<grid, kBlockThreads, smem, st>>>(
+        w.probs, nprob, w.rows_sym, w.ctr, w.cnt, w.cursor, (int)slab, w.bm_cache, w.row_slot,
+        w.bm_cache_words, w.bm_cache_slots);
+    count_launch(dev);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_symbolic(const WsPtrs& w, int nprob, int64_t R, const Tuning& t,
-                            int64_t max_ncols, const DevInfo& dev, cudaStream_t st) {
+                            int64_t max_ncols, const DevInfo& dev, cudaStream_t st, bool words) {
     if (R == 0) return cudaSuccess;
-    cudaError_t e;
+    cudaError_t e = cudaSuccess;
     // dense tier first: it holds the heaviest rows
     {
         int64_t slab = t.sym_slab_cols;
         if (slab > max_ncols) slab = (max_ncols + 1023) / 1024 * 1024;
         if (slab < 1024) slab = 1024;
         const size_t smem = (size_t)slab / 8;
-        e = cudaFuncSetAttribute(k_sym_dense, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
+        if (words) e = launch_sym_dense<true>(w, nprob, slab, smem, dev, st);
+        if (e == cudaSuccess) e = launch_sym_dense<false>(w, nprob, slab, smem, dev, st);
         if (e != cudaSuccess) return e;
-        const int grid = occupancy((const void*)k_sym_dense, kBlockThreads, smem, dev);
-        k_sym_dense<<<grid, kBlockThreads, smem, st>>>(w.probs, nprob, w.rows_sym, w.ctr, w.cnt,
-                                                       w.cursor, (int)slab, w.bm_cache, w.row_slot,
-                                                       w.bm_cache_words, w.bm_cache_slots);
-        count_launch(dev);
         mark_stage(dev, kStSymDense, st);
     }
     {

@@ -359,14 +359,17 @@ class Handle:
                                                         ctypes.byref(n)))
         return n.value
 
-    def symbolic_batched(self, sr, As, Bs, c_rps, ws, stream=None):
+    def symbolic_batched(self, sr, As, Bs, c_rps, ws, stream=None, sync=True):
+        """Batched symbolic phase; returns nnz(C_p) per product.  sync=False
+        passes no host count array: nothing is copied back or synchronised
+        (returns None), e.g. inside a CUDA-graph capture."""
         a = (spg_csr * len(As))(*[x.c() for x in As])
         b = (spg_csr * len(Bs))(*[x.c() for x in Bs])
-        nnz = (ctypes.c_int64 * len(As))()
+        nnz = (ctypes.c_int64 * len(As))() if sync else None
         self._ok(self.lib.spgemm_symbolic_batched(self._h, sr, len(As), a, b, self._ptrs(c_rps),
                                                   nnz, ws.data_ptr(), ws.numel(),
                                                   _stream_ptr(stream)))
-        return list(nnz)
+        return list(nnz) if sync else None
 
     def numeric_batched(self, sr, As, Bs, c_rps, c_cols, c_vals, ws, stream=None):
         a = (spg_csr * len(As))(*[x.c() for x in As])
@@ -385,15 +388,17 @@ class Handle:
                                                       ctypes.byref(n)))
         return n.value
 
-    def merge_count(self, sr, groups, c_rps, ws, stream=None):
+    def merge_count(self, sr, groups, c_rps, ws, stream=None, sync=True):
+        """Row pointers of the merged C blocks; returns their nnz (None with
+        sync=False: no host copy, no synchronisation)."""
         flat = [p for g in groups for p in g]
         parts = (spg_csr * len(flat))(*[p.c() for p in flat])
         npart = (ctypes.c_int * len(groups))(*[len(g) for g in groups])
-        nnz = (ctypes.c_int64 * len(groups))()
+        nnz = (ctypes.c_int64 * len(groups))() if sync else None
         self._ok(self.lib.spgemm_merge_stages_batched(
             self._h, sr, len(groups), npart, parts, self._ptrs(c_rps), nnz, None, None,
             ws.data_ptr(), ws.numel(), _stream_ptr(stream)))
-        return list(nnz)
+        return list(nnz) if sync else None
 
     def merge_write(self, sr, groups, c_rps, c_cols, c_vals, ws, stream=None):
         flat = [p for g in groups for p in g]
@@ -630,13 +635,33 @@ def typed_out(sr: int, raw):
     return raw.view(dt)
 
 
+def panel_cuts(rp, nrows: int, cap_entries: int):
+    """Row cuts [0, ..., nrows] of panels of at most cap_entries output
+    entries each (a single row may exceed it)."""
+    cuts, r0 = [0], 0
+    while r0 < nrows:
+        r1 = int(np.searchsorted(rp, rp[r0] + cap_entries, side="right")) - 1
+        r1 = max(r1, r0 + 1)
+        r1 = min(r1, nrows)
+        cuts.append(r1)
+        r0 = r1
+    return cuts
+
+
 def panel_product(sr: int, A: DeviceCSR, B: DeviceCSR, budget_bytes: int, on_panel,
-                  handle: Optional[Handle] = None):
+                  handle: Optional[Handle] = None, learned: Optional[dict] = None,
+                  stats: Optional[dict] = None):
     """C = A (x).(+) B in row panels whose output fits in budget_bytes of device
     memory (for products larger than HBM).  One symbolic call on all of A gives
     the row counts; each panel (a row view of A) then runs symbolic + numeric
-    into a reused buffer and on_panel(r0, r1, C_panel) is called.  Returns
-    (nnz(C), number of panels)."""
+    into a reused buffer and on_panel(r0, r1, C_panel) is called.
+
+    learned: None for the plain form, else the options of the learned-sizing
+    path ({} for ub-sized capacities, or model / margin / exact_max_ub /
+    learned_max): each panel then runs learned plan, symbolic and numeric.
+    stats: if given, filled with the device milliseconds of each panel's
+    compute ("panel_ms", CUDA events around the library calls only) and the
+    cuts.  Returns (nnz(C), number of panels)."""
     import torch
     h = handle or Handle()
     dev = A.rp.device
@@ -647,25 +672,43 @@ def panel_product(sr: int, A: DeviceCSR, B: DeviceCSR, budget_bytes: int, on_pan
     per = 4 + OUT_BYTES[sr]
     cap = max(1, budget_bytes // per)
     rp = c_rp.cpu().numpy()
-    cuts, r0 = [0], 0
-    while r0 < A.nrows:
-        r1 = int(np.searchsorted(rp, rp[r0] + cap, side="right")) - 1
-        r1 = max(r1, r0 + 1)
-        r1 = min(r1, A.nrows)
-        cuts.append(r1)
-        r0 = r1
+    cuts = panel_cuts(rp, A.nrows, cap)
     biggest = max(int(rp[b] - rp[a]) for a, b in zip(cuts[:-1], cuts[1:]))
     col = torch.empty(max(biggest, 1), dtype=torch.int32, device=dev)
     val = out_tensor(sr, max(biggest, 1), dev)
+    times = []
     for a, b in zip(cuts[:-1], cuts[1:]):
         Av = A.rows(a, b) if (a, b) != (0, A.nrows) else A
-        wsp = torch.empty(h.workspace_size(sr, Av, B), dtype=torch.uint8, device=dev)
         prp = torch.empty(b - a + 1, dtype=torch.int64, device=dev)
-        n = h.symbolic(sr, Av, B, prp, wsp)
-        h.numeric(sr, Av, B, prp, col, val, wsp)
+        if learned is None:
+            wsp = torch.empty(h.workspace_size(sr, Av, B), dtype=torch.uint8, device=dev)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            n = h.symbolic(sr, Av, B, prp, wsp)
+            h.numeric(sr, Av, B, prp, col, val, wsp)
+            e1.record()
+        else:
+            wsp = torch.empty(h.learned_workspace_size(sr, Av, B), dtype=torch.uint8, device=dev)
+            sb = h.learned_plan(sr, Av, B, wsp, **learned)
+            staging = torch.empty(max(sb, 1), dtype=torch.uint8, device=dev)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            h.learned_plan(sr, Av, B, wsp, **learned)
+            n = h.learned_symbolic(sr, Av, B, prp, wsp, staging)
+            h.learned_numeric(sr, Av, B, prp, col, val, wsp, staging)
+            e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
         h.check(wsp)
         on_panel(a, b, DeviceCSR(b - a, B.ncols, prp, col[:n], None if val is None else val[:n]))
         del wsp
+        if learned is not None:
+            del staging
+    if stats is not None:
+        stats["panel_ms"] = times
+        stats["cuts"] = cuts
     return total, len(cuts) - 1
 
 

@@ -179,21 +179,35 @@ class Summa:
             self.numeric()
             self.merge_write()
 
-    def capture(self):
-        """Capture numeric + merge write into one CUDA graph."""
+    def capture(self, full: bool = False):
+        """Capture numeric + merge write into one CUDA graph; with full=True
+        (batched form) the whole product: row analysis, symbolic phase and
+        scan of every block product, numeric phase, merge count and merge
+        write, with no host synchronisation inside (every buffer was sized
+        by plan())."""
         torch = self._torch
+        if full and not self.batched:
+            raise ValueError("the full graph needs the batched form")
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.stream(s):
-            self.numeric()        # warm-up outside the graph
+
+        def body():
+            if full:
+                self.h.symbolic_batched(self.sr, self.As, self.Bs, self.p_rp, self.ws, sync=False)
+            self.numeric()
+            if full:
+                self.h.merge_count(self.sr, self.groups, self.c_rp, self.mws, sync=False)
             self.merge_write()
+
+        with torch.cuda.stream(s):
+            body()                # warm-up outside the graph
         torch.cuda.current_stream().wait_stream(s)
         torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
-            self.numeric()
-            self.merge_write()
+            body()
         self.graph = g
+        self.graph_full = full
         return g
 
     def check(self):
@@ -216,3 +230,46 @@ class Summa:
         return api.DeviceCSR(self.row_cuts[I + 1] - self.row_cuts[I],
                              self.col_cuts[J + 1] - self.col_cuts[J], self.c_rp[k],
                              self.c_col[k][:self.c_nnz[k]], val)
+
+
+def summa_panels(handle: api.Handle, sr: int, A: api.DeviceCSR, B: api.DeviceCSR,
+                 budget_bytes: int, on_panel, q: int = 4, batched: bool = True,
+                 stats: Optional[dict] = None):
+    """The q x q Sparse-SUMMA emulation of C = A (x).(+) B in row panels whose
+    output fits in budget_bytes (for products larger than HBM): every panel (a
+    row view of A) is a full q x q grid of its own (block products of all
+    stages and the merge of their partials); on_panel(r0, r1, summa) is called
+    with the panel's finished Summa (blocks via summa.block(I, J)).
+    stats: if given, filled with each panel's device milliseconds ("panel_ms",
+    CUDA events around the phases; the host synchronisations of the symbolic
+    and merge-count calls included) and the cuts.  Returns the panel count."""
+    import torch
+    h = handle
+    c_rp = torch.empty(A.nrows + 1, dtype=torch.int64, device=A.rp.device)
+    ws = torch.empty(h.workspace_size(sr, A, B), dtype=torch.uint8, device=A.rp.device)
+    h.symbolic(sr, A, B, c_rp, ws)
+    del ws
+    per = 4 + api.OUT_BYTES[sr]
+    cuts = api.panel_cuts(c_rp.cpu().numpy(), A.nrows, max(1, budget_bytes // per))
+    times = []
+    for r0, r1 in zip(cuts[:-1], cuts[1:]):
+        Av = A.rows(r0, r1) if (r0, r1) != (0, A.nrows) else A
+        sm = Summa(h, sr, Av, B, q=q, batched=batched)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sm.symbolic()
+        sm.numeric()
+        sm.merge_count()
+        sm.merge_write()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        sm.check()
+        on_panel(r0, r1, sm)
+        del sm
+        torch.cuda.empty_cache()
+    if stats is not None:
+        stats["panel_ms"] = times
+        stats["cuts"] = cuts
+    return len(cuts) - 1

@@ -70,7 +70,10 @@ def compare_all_rows_streamed(sr, A, B, C, ub, panel_products=6e8):
         assert_pattern_equal(rp[r0:r1 + 1] - a, C.col[a:b].cpu().numpy(), exp.rp, exp.col,
                              f"rows [{r0}, {r1})")
         if sr != api.BOOL_OR_AND:
-            assert_values(sr, C.val[a:b].cpu().numpy(), exp.val, what=f"rows [{r0}, {r1})")
+            got = C.val[a:b].cpu().numpy()
+            if sr == api.OVERLAP_I32:
+                got = np.ascontiguousarray(got).view(api.OVERLAP_NP).reshape(-1)
+            assert_values(sr, got, exp.val, what=f"rows [{r0}, {r1})")
         del exp
         r0 = r1
         npanels += 1
@@ -141,3 +144,93 @@ def test_laplacian2048_closed_form():
           np.where((np.abs(dx) == 1) & (np.abs(dy) == 1), 2.0,
           np.where(((np.abs(dx) == 2) & (dy == 0)) | ((dx == 0) & (np.abs(dy) == 2)), 1.0, np.nan))))
     assert np.array_equal(C.val, exp)   # small integers: exact in FP64
+
+
+def _sample_by_panel(ub, cuts, k_heavy, k_rand, seed):
+    """The heaviest rows and random non-empty rows, grouped by panel."""
+    rows = sample_rows(ub, k_heavy=k_heavy, k_rand=k_rand, seed=seed, max_products=4e8)
+    return {(a, b): rows[(rows >= a) & (rows < b)] for a, b in zip(cuts[:-1], cuts[1:])}
+
+
+def _check_fp64_rows(A, rows, got_rp, got_col, got_val):
+    exp = oracle.spgemm(api.PLUS_TIMES_F64, A, A, rows=rows)
+    assert_pattern_equal(got_rp, got_col, exp.rp, exp.col, f"{len(rows)} rows")
+    # inputs are non-negative: sum_k |a b| is the value itself
+    assert_values(api.PLUS_TIMES_F64, got_val, exp.val, bound=exp.val)
+
+
+def test_rmat20_summa_panels_sampled_rows():
+    """R-MAT 20 A^2 over plus-times FP64 as the 4 x 4 Sparse-SUMMA emulation in
+    row panels (C is about 294 GB): sampled rows of every panel, assembled from
+    the panel's C blocks, against the oracle."""
+    from paper_2504_06408_gb300.summa import summa_panels
+    A = I.rmat(20, dtype=np.float64, seed=1, lo=0.0, hi=1.0)
+    dA = api.DeviceCSR.from_host(A, val_dtype=np.float64)
+    ub = oracle.row_upper_bounds(A, A)
+    h = api.Handle()
+    checked = []
+
+    def on_panel(r0, r1, sm):
+        rows = sample[(r0, r1)]
+        if rows.size == 0:
+            return
+        parts_rp, parts_col, parts_val = [0], [], []
+        for r in rows:
+            Ib = int(np.searchsorted(sm.row_cuts, r - r0, side="right")) - 1
+            i = r - r0 - sm.row_cuts[Ib]
+            for Jb in range(sm.q):
+                blk = sm.block(Ib, Jb)
+                a, b = int(blk.rp[i].item()), int(blk.rp[i + 1].item())
+                parts_col.append(blk.col[a:b].cpu().numpy() + sm.col_cuts[Jb])
+                parts_val.append(blk.val[a:b].cpu().numpy())
+            parts_rp.append(sum(x.size for x in parts_col))
+        _check_fp64_rows(A, rows, np.array(parts_rp), np.concatenate(parts_col),
+                         np.concatenate(parts_val))
+        checked.append(rows.size)
+
+    budget = 24 << 30
+    # the panel cuts of summa_panels, known in advance from the row counts
+    c_rp = torch.empty(A.nrows + 1, dtype=torch.int64, device="cuda")
+    ws = torch.empty(h.workspace_size(api.PLUS_TIMES_F64, dA, dA), dtype=torch.uint8, device="cuda")
+    h.symbolic(api.PLUS_TIMES_F64, dA, dA, c_rp, ws)
+    del ws
+    cuts = api.panel_cuts(c_rp.cpu().numpy(), A.nrows, budget // 12)
+    sample = _sample_by_panel(ub, cuts, 12, 200, 21)
+    npanels = summa_panels(h, api.PLUS_TIMES_F64, dA, dA, budget, on_panel, q=4)
+    assert npanels == len(cuts) - 1 >= 8
+    assert sum(checked) >= 200
+
+
+def test_rmat21_learned_panels_sampled_rows():
+    """R-MAT 21 A^2 over plus-times FP64 through the learned-sizing path with
+    the trained network, in row panels (C is about 757 GB): sampled rows of
+    every panel against the oracle."""
+    from paper_2504_06408_gb300 import learned as L
+    A = I.rmat(21, dtype=np.float64, seed=1, lo=0.0, hi=1.0)
+    dA = api.DeviceCSR.from_host(A, val_dtype=np.float64)
+    ub = oracle.row_upper_bounds(A, A)
+    params, meta = L.load()
+    h = api.Handle()
+    budget = 24 << 30
+    c_rp = torch.empty(A.nrows + 1, dtype=torch.int64, device="cuda")
+    ws = torch.empty(h.workspace_size(api.PLUS_TIMES_F64, dA, dA), dtype=torch.uint8, device="cuda")
+    h.symbolic(api.PLUS_TIMES_F64, dA, dA, c_rp, ws)
+    del ws
+    cuts = api.panel_cuts(c_rp.cpu().numpy(), A.nrows, budget // 12)
+    sample = _sample_by_panel(ub, cuts, 12, 200, 22)
+    checked = []
+
+    def on_panel(r0, r1, C):
+        rows = sample[(r0, r1)]
+        if rows.size == 0:
+            return
+        got = api.to_host_rows(C, api.PLUS_TIMES_F64, rows - r0)
+        _check_fp64_rows(A, rows, got.rp, got.col, got.val)
+        checked.append(rows.size)
+
+    total, npanels = api.panel_product(
+        api.PLUS_TIMES_F64, dA, dA, budget, on_panel, handle=h,
+        learned={"model": params, "margin": meta["margin"], "exact_max_ub": meta["exact_max_ub"]})
+    assert npanels == len(cuts) - 1 >= 20
+    assert total == int(c_rp[-1].item())
+    assert sum(checked) >= 200

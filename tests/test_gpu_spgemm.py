@@ -43,6 +43,9 @@ TIERS = {
     # rebuilds every row's bitmap from its products
     "dense_rebuild": dict(sym_warp_max_ub=1, sym_block_max_ub=1, num_warp_max_nnz=1,
                           num_block_max_nnz=1, bitmap_cache_bytes=1),
+    # the rank kernel with 1024-column slabs: many value passes per row
+    "dense_small_slabs_rank": dict(sym_warp_max_ub=1, sym_block_max_ub=1, num_warp_max_nnz=1,
+                                   num_block_max_nnz=1, dense_slab_cols=1024),
 }
 
 
@@ -233,7 +236,8 @@ def entry_mode_rows(seed):
     return A, B
 
 
-@pytest.mark.parametrize("tier", ["default", "all_dense", "dense_rebuild"])
+@pytest.mark.parametrize("tier", ["default", "all_dense", "dense_rebuild",
+                                  "dense_small_slabs_rank"])
 @pytest.mark.parametrize("sr", [api.MIN_PLUS_F32, api.PLUS_TIMES_F64, api.BOOL_OR_AND,
                                 api.OVERLAP_I32])
 def test_dense_row_entry_modes_and_value_passes(sr, tier):
@@ -244,3 +248,24 @@ def test_dense_row_entry_modes_and_value_passes(sr, tier):
     # the 3000-entry row has more outputs than one value pass of the rank
     # kernel holds (about 18K at 8 bytes per output)
     assert got.rp[5] - got.rp[4] > 40_000
+
+
+@pytest.mark.parametrize("top", [65535, 65536, 2**31 - 1])
+def test_overlap_compact_and_wide_positions(top):
+    """The overlap semiring's CTA hash tier packs pairs in 32 bits when every
+    position of A and B is below 2^16 and keeps 64-bit pairs otherwise: rows
+    of a few thousand outputs, positions drawn up to `top` (one entry of B set
+    to `top` exactly), against the oracle."""
+    rng = np.random.default_rng(top % 1000)
+    # 12,000 reads: every row has 2,000-7,400 outputs (the compact tier below
+    # 6,144, the rank tier above)
+    A = I.kmer(12000, 1 << 17, len_lo=100, len_hi=300, col_cap=64, seed=4)
+    At = oracle.transpose(A, np.int32)
+    a_val = rng.integers(0, min(top, 65535) + 1, A.nnz).astype(np.int32)
+    b_val = rng.integers(0, top, At.nnz, dtype=np.int64).astype(np.int32)
+    b_val[At.nnz // 2] = top
+    A = A.with_values(a_val)
+    B = I.CSR(At.nrows, At.ncols, At.rp, At.col, b_val)
+    got, h = check(api.OVERLAP_I32, A, B, None, f"positions up to {top}")
+    n = np.diff(got.rp)
+    assert n.max() > 2048   # rows beyond the 24-byte hash tier's limit

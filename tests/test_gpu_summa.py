@@ -43,22 +43,37 @@ def test_split_columns_matches_oracle_blocks():
         assert np.array_equal(got.val, r.val)
 
 
-def _partials(sr, S, seed):
+def _partials(sr, S, seed, shape=(60, 40, 70), density=(0.1, 0.1)):
     """S partials of one shape with output-type values (products of random
     factors, so the overlap records are genuine)."""
     out = []
+    m, k, n = shape
     for s in range(S):
-        pa = I.random_csr(60, 40, 0.1, seed + 10 * s, dtype=None, empty_row_frac=0.2)
-        pb = I.random_csr(40, 70, 0.1, seed + 10 * s + 1, dtype=None)
+        pa = I.random_csr(m, k, density[0], seed + 10 * s, dtype=None, empty_row_frac=0.2)
+        pb = I.random_csr(k, n, density[1], seed + 10 * s + 1, dtype=None)
         a, b = values_for(sr, pa, seed + s), values_for(sr, pb, seed + s + 5)
         out.append(oracle.spgemm(sr, a, b))
     return out
 
 
+# (number of partials per merge, shape of the factors, densities): light rows
+# (at most 32 entries over all stages), heavy rows (hundreds of entries, the
+# bitmap kernel) and a merge wider than 2^18 columns (the sequence-sort path)
+MERGE_CASES = {
+    "light": [((1, (60, 40, 70), (0.1, 0.1))), ((3, (60, 40, 70), (0.1, 0.1))),
+              ((5, (60, 40, 70), (0.1, 0.1)))],
+    "heavy": [((4, (50, 30, 3000), (0.3, 0.05))), ((16, (20, 30, 500), (0.2, 0.1))),
+              ((2, (40, 60, 5000), (0.2, 0.02)))],
+    "wide": [((3, (30, 20, 300_000), (0.3, 0.0004))), ((2, (30, 20, 300_000), (0.3, 0.0004)))],
+}
+
+
+@pytest.mark.parametrize("case", list(MERGE_CASES))
 @pytest.mark.parametrize("sr", SR)
-def test_merge_stages_matches_oracle(sr):
+def test_merge_stages_matches_oracle(sr, case):
     h = api.Handle()
-    groups_host = [_partials(sr, S, 10 * S) for S in (1, 3, 5)]
+    groups_host = [_partials(sr, S, 10 * S + k, shape, dens)
+                   for k, (S, shape, dens) in enumerate(MERGE_CASES[case])]
     dt = oracle.OUT_DTYPE[sr]
     dev_groups = []
     for g in groups_host:
@@ -220,3 +235,30 @@ def test_summa_graph_replay_matches():
         sm.run()
         torch.cuda.synchronize()
         _check_blocks(sm, sr, A, A)
+
+
+@pytest.mark.parametrize("sr", [api.MIN_PLUS_F32, api.PLUS_TIMES_F64, api.OVERLAP_I32])
+def test_summa_full_graph_replay_matches(sr):
+    """One CUDA graph over the whole batched product (row analysis, symbolic
+    phase, scan, numeric phase, merge count and merge write; no host
+    synchronisation inside): every replay recomputes the row pointers, the
+    partials and C from scratch and matches the oracle."""
+    pat = I.rmat(12, seed=13, dtype=None)
+    A = values_for(sr, pat, 5)
+    B = values_for(sr, pat, 6) if sr != api.OVERLAP_I32 else I.positions_csr(pat, 6)
+    h = api.Handle()
+    dA = api.DeviceCSR.from_host(A, val_dtype=api.IN_NP[sr])
+    dB = api.DeviceCSR.from_host(B, val_dtype=api.IN_NP[sr])
+    sm = Summa(h, sr, dA, dB, q=4)
+    sm.plan()
+    sm.capture(full=True)
+    for _ in range(2):
+        for rp in sm.p_rp + sm.c_rp:
+            rp.fill_(-1)
+        for k in range(len(sm.c_col)):
+            sm.c_col[k].fill_(-1)
+        sm._pcol.fill_(-1)
+        sm.run()
+        sm.check()
+        torch.cuda.synchronize()
+        _check_blocks(sm, sr, A, B)
