@@ -118,6 +118,63 @@ def host_placement():
     return info
 
 
+def _cpulist(text):
+    out = set()
+    for part in text.strip().split(","):
+        if not part:
+            continue
+        if "-" in part:
+            a, b = part.split("-")
+            out.update(range(int(a), int(b) + 1))
+        else:
+            out.add(int(part))
+    return out
+
+
+def bind_host_to_gpu_node():
+    """Keep this process's CPUs and new host pages on the current GPU's NUMA
+    node (best effort, this process only): the e2e leg's pinned buffers are
+    placed where they are first allocated, and device-host copies to a
+    remote node cross the CPU-CPU link.  Returns what was applied."""
+    info = host_placement()
+    node = info.get("gpu_numa_node")
+    bus = info.get("gpu_pci")
+    if node is None or node < 0 or not bus:
+        return info
+    try:
+        local = _cpulist(open(f"/sys/bus/pci/devices/{bus}/local_cpulist").read())
+        allowed = os.sched_getaffinity(0)
+        both = allowed & local
+        info["cpus_local_to_gpu"] = len(both)
+        if both and both != allowed:
+            os.sched_setaffinity(0, both)
+            info["affinity_set"] = True
+    except (OSError, ValueError):
+        pass
+    try:   # set_mempolicy(MPOL_PREFERRED, {node}): new pages from the GPU's node
+        import ctypes
+        import platform
+        nr = {"aarch64": 237, "x86_64": 238}.get(platform.machine())
+        if nr is not None and node < 64:
+            mask = ctypes.c_ulong(1 << node)
+            rc = ctypes.CDLL(None, use_errno=True).syscall(nr, 1, ctypes.byref(mask), 65)
+            info["mempolicy_preferred_node"] = node if rc == 0 else None
+    except OSError:
+        pass
+    return info
+
+
+def reset_mempolicy():
+    try:
+        import ctypes
+        import platform
+        nr = {"aarch64": 237, "x86_64": 238}.get(platform.machine())
+        if nr is not None:
+            ctypes.CDLL(None, use_errno=True).syscall(nr, 0, None, 0)
+    except OSError:
+        pass
+
+
 def dist_info():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -442,21 +499,14 @@ def summa_forms(api, Summa, h, sr, dA, flush, reps, ref=None, tuning=None):
 
 
 def summa_tuning(api, scale):
-    """Tier limits of the batched SUMMA form, tuned by coordinate descent on a
-    calibration product two R-MAT scales smaller (same generator, other seed),
-    cached per GPU in the autotuner's JSON file."""
-    import torch
+    """Tier limits of the batched SUMMA form on this workload: the autotuner's
+    result shipped with the package for this GPU, else the per-user cache,
+    else None (the library defaults)."""
     from paper_2504_06408_gb300 import autotune
-    from paper_2504_06408_gb300 import inputs as I
-    tag = f"summa4x4_rmat{scale - 2}_seed2"
-    t = autotune.load(api.PLUS_TIMES_F64, tag)
+    tag = f"summa4x4_rmat{scale}"
+    t = autotune.load(api.PLUS_TIMES_F64, tag, autotune.SHIPPED)
     if t is None:
-        Ac = I.rmat(max(scale - 2, 10), dtype=np.float64, seed=2, lo=0.0, hi=1.0)
-        dAc = api.DeviceCSR.from_host(Ac, val_dtype=np.float64)
-        t = autotune.tune_summa(api.PLUS_TIMES_F64, dAc, dAc, reps=3, sweeps=1)
-        autotune.save(api.PLUS_TIMES_F64, tag, t)
-        del dAc
-        torch.cuda.empty_cache()
+        t = autotune.load(api.PLUS_TIMES_F64, tag)
     return t
 
 
@@ -496,12 +546,13 @@ def er_forms(api, h, flush, reps=21):
     return out
 
 
-def kmer_form(api, h, flush, reps, peak):
+def kmer_form(api, h, flush, reps, peak, reads=200_000):
     """k-mer overlap product C = A A^T (200,000 reads x 2^24 k-mers, overlap
-    semiring, int32 positions); A^T by the library's transpose (untimed)."""
+    semiring, int32 positions; fewer reads for profiling captures); A^T by the
+    library's transpose (untimed)."""
     import torch
     from paper_2504_06408_gb300 import inputs as I
-    A = I.kmer(seed=1)
+    A = I.kmer(nrows=reads, seed=1)
     dA = api.DeviceCSR.from_host(A, val_dtype=np.int32)
     dAt = h.transpose(dA, 4)
     ms, nnz = plain_ms_of(api, h, api.OVERLAP_I32, dA, dAt, flush, reps)
@@ -748,6 +799,14 @@ def main():
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the learned / batched vs plain comparisons")
     ap.add_argument("--form-reps", type=int, default=3)
+    ap.add_argument("--forms", default="",
+                    help="comma-separated subset of the comparison forms to run (names as in "
+                         "the output, without the scale prefix: min_plus, bool, er4096, "
+                         "kmer_overlap, laplacian, summa, float_cold_warm, rmat20, rmat21); "
+                         "default all")
+    ap.add_argument("--kmer-reads", type=int, default=200_000,
+                    help="reads of the k-mer overlap form (200,000 = the workload; fewer for "
+                         "profiling captures)")
     ap.add_argument("--no-big-forms", action="store_true",
                     help="skip the R-MAT 20 / 21 forms whose C exceeds device memory")
     ap.add_argument("--scale", type=int, default=SCALE,
@@ -779,7 +838,11 @@ def main():
 
     sr = api.MIN_PLUS_F32
     A = I.rmat(args.scale, dtype=np.float32, seed=1)
-    h = api.Handle()
+    # the kernel tier limits the autotuner found for this workload on this GPU
+    # (shipped with the package), else the library defaults
+    from paper_2504_06408_gb300 import autotune
+    tuning = autotune.load(sr, f"rmat{args.scale}", autotune.SHIPPED)
+    h = api.Handle(tuning=tuning or None)
     dA = api.DeviceCSR.from_host(A, val_dtype=np.float32)
     ws = torch.empty(h.workspace_size(sr, dA, dA), dtype=torch.uint8, device="cuda")
     c_rp = torch.empty(A.nrows + 1, dtype=torch.int64, device="cuda")
@@ -864,6 +927,8 @@ def main():
             print(f"e2e left out: {world} ranks need {need / 1e9:.0f} GB of pinned host memory, "
                   f"{(avail or 0) / 1e9:.0f} GB available", file=sys.stderr, flush=True)
     if run_e2e:
+        saved_affinity = os.sched_getaffinity(0)
+        placement = bind_host_to_gpu_node()
         pinned = []
 
         def pin(n, dt):
@@ -906,8 +971,10 @@ def main():
                "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e_s, "steps": len(et),
                "step_ms": [1e3 * x for x in et],
                "d2h_gbs_same_run": d2h_gbs, "d2h_floor_ms": 1e3 * d2h / (d2h_gbs * 1e9),
-               "host": host_placement()}
+               "host": placement}
         del h2, pinned, hA, out
+        os.sched_setaffinity(0, saved_affinity)   # the CPU baseline uses every core
+        reset_mempolicy()
 
     forms = None
     if not args.no_forms:
@@ -921,40 +988,57 @@ def main():
                          % reps}
         del c_col, c_val, step
         torch.cuda.empty_cache()
-        forms[f"rmat{args.scale}_min_plus"] = learned_forms(api, h, sr, dA, dA, flush, reps,
-                                                            ms_per_step, params, meta)
-        torch.cuda.empty_cache()
-        forms[f"rmat{args.scale}_bool"] = bool_form(api, h, A, flush, reps, peak)
+
+        wanted = [w for w in args.forms.split(",") if w]
+
+        def form(name, fn):
+            """one comparison form; a failure is recorded, not fatal to the bench line"""
+            if wanted and not any(w in name for w in wanted):
+                return
+            try:
+                forms[name] = fn()
+            except Exception as ex:   # noqa: BLE001
+                forms[name] = {"error": f"{type(ex).__name__}: {str(ex)[:300]}"}
+            torch.cuda.empty_cache()
+
+        form(f"rmat{args.scale}_min_plus",
+             lambda: learned_forms(api, h, sr, dA, dA, flush, reps, ms_per_step, params, meta))
+        form(f"rmat{args.scale}_bool", lambda: bool_form(api, h, A, flush, reps, peak))
         del dA
         torch.cuda.empty_cache()
-        forms["er4096"] = er_forms(api, h, flush)
-        forms["kmer_overlap"] = kmer_form(api, h, flush, reps, peak)
-        torch.cuda.empty_cache()
-        lap = I.laplacian(2048)
-        dL = api.DeviceCSR.from_host(lap, val_dtype=np.float64)
-        pms, _ = plain_ms_of(api, h, api.PLUS_TIMES_F64, dL, dL, flush, reps)
-        forms["laplacian2048_plus_times_f64"] = learned_forms(
-            api, h, api.PLUS_TIMES_F64, dL, dL, flush, reps, pms, params, meta)
-        del dL
-        torch.cuda.empty_cache()
-        A64 = I.rmat(args.scale, dtype=np.float64, seed=1, lo=0.0, hi=1.0)
-        dA64 = api.DeviceCSR.from_host(A64, val_dtype=np.float64)
-        pms, _, ref = plain_ms_of(api, h, api.PLUS_TIMES_F64, dA64, dA64, flush, reps, keep=True)
-        torch.cuda.empty_cache()
-        tuning = summa_tuning(api, args.scale)
-        sf = summa_forms(api, Summa, h, api.PLUS_TIMES_F64, dA64, flush, reps, ref=ref,
-                         tuning=tuning)
-        sf["plain_unblocked_ms"] = pms
-        best = min(sf.get("batched_tuned_graph_full_ms", float("inf")),
-                   sf["batched_graph_full_ms"])
-        sf["batched_graph_full_vs_unblocked"] = best / pms
-        forms[f"rmat{args.scale}_plus_times_f64_summa4x4"] = sf
-        del dA64, ref
-        torch.cuda.empty_cache()
-        forms["float_cold_warm"] = cold_warm_forms()
+        form("er4096", lambda: er_forms(api, h, flush))
+        form("kmer_overlap", lambda: kmer_form(api, h, flush, reps, peak, args.kmer_reads))
+
+        def laplacian_form():
+            lap = I.laplacian(2048)
+            dL = api.DeviceCSR.from_host(lap, val_dtype=np.float64)
+            pms, _ = plain_ms_of(api, h, api.PLUS_TIMES_F64, dL, dL, flush, reps)
+            return learned_forms(api, h, api.PLUS_TIMES_F64, dL, dL, flush, reps, pms, params,
+                                 meta)
+
+        form("laplacian2048_plus_times_f64", laplacian_form)
+
+        def summa_form():
+            A64 = I.rmat(args.scale, dtype=np.float64, seed=1, lo=0.0, hi=1.0)
+            dA64 = api.DeviceCSR.from_host(A64, val_dtype=np.float64)
+            pms, _, ref = plain_ms_of(api, h, api.PLUS_TIMES_F64, dA64, dA64, flush, reps,
+                                      keep=True)
+            torch.cuda.empty_cache()
+            tuning = summa_tuning(api, args.scale)
+            sf = summa_forms(api, Summa, h, api.PLUS_TIMES_F64, dA64, flush, reps, ref=ref,
+                             tuning=tuning)
+            sf["plain_unblocked_ms"] = pms
+            best = min(sf.get("batched_tuned_graph_full_ms", float("inf")),
+                       sf["batched_graph_full_ms"])
+            sf["batched_graph_full_vs_unblocked"] = best / pms
+            return sf
+
+        form(f"rmat{args.scale}_plus_times_f64_summa4x4", summa_form)
+        form("float_cold_warm", cold_warm_forms)
         if not args.no_big_forms:
-            forms["rmat20_plus_times_f64_summa4x4_panels"] = config4_form(api, peak)
-            forms["rmat21_plus_times_f64_learned_panels"] = config5_form(api, params, meta, peak)
+            form("rmat20_plus_times_f64_summa4x4_panels", lambda: config4_form(api, peak))
+            form("rmat21_plus_times_f64_learned_panels",
+                 lambda: config5_form(api, params, meta, peak))
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -967,7 +1051,7 @@ def main():
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                "data": "synthetic",
                "config": dict(workload_config(P=P, nnz_c=nnz, nnz_a=A.nnz, scale=args.scale),
-                              parallelism=f"replicas x{world}"),
+                              parallelism=f"replicas x{world}", tuning=tuning or "defaults"),
                "hbm_roofline_frac_step": (t_alg_all / (ms_per_step * 1e-3) / 1e9) / peak,
                "hbm_compulsory_frac_step": (t_min / (ms_per_step * 1e-3) / 1e9) / peak,
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,

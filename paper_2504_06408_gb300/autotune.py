@@ -29,6 +29,9 @@ SPACE = {
 }
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "spgemm_gb300_tuning.json")
+# tunings measured on this project's target GPU, shipped with the package
+# (written by `python -m paper_2504_06408_gb300.autotune --out <this file> ...`)
+SHIPPED = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_gb300.json")
 
 
 def _time_call(h: api.Handle, sr, dA, dB, ws, c_rp, c_col, c_val, reps: int) -> float:
@@ -173,3 +176,39 @@ def tuned_handle(sr: int, dA, dB, tag: str, path: str = DEFAULT_CACHE, **kw) -> 
         t = tune(sr, dA, dB, **kw)
         save(sr, tag, t, path)
     return api.Handle(tuning=t or None)
+
+
+def main(argv=None):
+    """Tune a workload on the current GPU and store the result in a JSON file."""
+    import argparse
+
+    import numpy as np
+    import torch
+
+    from . import inputs as I
+    ap = argparse.ArgumentParser(description="tune the kernel tier limits on this GPU")
+    ap.add_argument("form", choices=["plain", "summa"])
+    ap.add_argument("--scale", type=int, default=18, help="R-MAT scale of A (A^2 is tuned)")
+    ap.add_argument("--semiring", default="plus_times_f64", choices=sorted(
+        api.SEMIRING_NAMES.values()))
+    ap.add_argument("--sweeps", type=int, default=1)
+    ap.add_argument("--out", default=DEFAULT_CACHE)
+    args = ap.parse_args(argv)
+    sr = {v: k for k, v in api.SEMIRING_NAMES.items()}[args.semiring]
+    dt = api.IN_NP[sr]
+    kw = {"lo": 0.0, "hi": 1.0} if dt == np.float64 else {}
+    A = I.rmat(args.scale, dtype=dt, seed=1, **kw)
+    dA = api.DeviceCSR.from_host(A, val_dtype=dt)
+    if args.form == "plain":
+        t = tune(sr, dA, dA, reps=3, sweeps=args.sweeps, log=print)
+        tag = f"rmat{args.scale}"
+    else:
+        t = tune_summa(sr, dA, dA, reps=3, sweeps=args.sweeps, log=print)
+        tag = f"summa4x4_rmat{args.scale}"
+    save(sr, tag, t, args.out)
+    torch.cuda.synchronize()
+    print(json.dumps({"tag": tag, "tuning": t}))
+
+
+if __name__ == "__main__":
+    main()

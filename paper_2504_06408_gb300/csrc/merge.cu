@@ -426,22 +426,30 @@ struct MergeLaunch {
         if (blocks > (int64_t)dev->sms * 16) blocks = (int64_t)dev->sms * 16;
         if (blocks < 1) blocks = 1;
         const size_t smem = merge_heavy_smem(max_ncols);
+        // as many CTAs as fit the SMs (one heavy row each at a time)
+        auto grid_of = [&](const void* fn) {
+            int per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kMergeThreads, smem);
+            return (per_sm < 1 ? 1 : per_sm) * dev->sms;
+        };
         if (count_only) {
             k_merge_light<S, false><<<(unsigned)blocks, 256, 0, st>>>(w->probs, nprob, R, w->cnt,
                                                                        w->heavy, w->ctr, w->status);
             err = cudaFuncSetAttribute(k_merge_heavy<S, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (err != cudaSuccess) return;
-            k_merge_heavy<S, false><<<dev->sms * 4, kMergeThreads, smem, st>>>(
-                w->probs, nprob, w->heavy, w->ctr, w->cnt, w->status);
+            k_merge_heavy<S, false><<<grid_of((const void*)k_merge_heavy<S, false>), kMergeThreads,
+                                      smem, st>>>(w->probs, nprob, w->heavy, w->ctr, w->cnt,
+                                                  w->status);
         } else {
             k_merge_light<S, true><<<(unsigned)blocks, 256, 0, st>>>(w->probs, nprob, R, w->cnt,
                                                                       w->heavy, w->ctr, w->status);
             err = cudaFuncSetAttribute(k_merge_heavy<S, true>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (err != cudaSuccess) return;
-            k_merge_heavy<S, true><<<dev->sms * 4, kMergeThreads, smem, st>>>(
-                w->probs, nprob, w->heavy, w->ctr, w->cnt, w->status);
+            k_merge_heavy<S, true><<<grid_of((const void*)k_merge_heavy<S, true>), kMergeThreads,
+                                     smem, st>>>(w->probs, nprob, w->heavy, w->ctr, w->cnt,
+                                                 w->status);
         }
         count_launch(*dev, 2);
         err = cudaGetLastError();

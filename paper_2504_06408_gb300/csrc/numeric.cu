@@ -1276,7 +1276,7 @@ cudaError_t launch_numeric(int sr, const WsPtrs& w, const DCsr& B0, int nprob, i
     cudaMemsetAsync(&w.ctr->claim[2], 0, 2 * sizeof(int32_t), st);
     cudaMemsetAsync(&w.ctr->ovl_wide, 0, sizeof(int32_t), st);
     cudaMemsetAsync(&w.ctr->num_block_max, 0, sizeof(int64_t), st);
-    if (sr == SR_OVERLAP && t.num_block_max_nnz < kOvlCompactMax) {
+    if (sr == SR_OVERLAP && t.num_block_max_nnz <= kOvlCompactMax) {
         // the compact overlap block tier, when every position of every A and
         // B fits 16 bits
         for (int p = 0; p < nprob && probs_host; ++p) {

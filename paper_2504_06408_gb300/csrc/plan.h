@@ -183,7 +183,7 @@ cudaError_t launch_numeric(int sr, const WsPtrs& w, const DCsr& B0, int nprob, i
                            const ProbTable* probs_host = nullptr);
 // overlap semiring: rows of up to this many outputs take the CTA hash tier
 // with 12-byte slots when every position of A and B is below 2^16
-constexpr int64_t kOvlCompactMax = 6144;
+constexpr int64_t kOvlCompactMax = 2048;
 cudaError_t launch_validate(const DCsr& M, int64_t nnz, DevStatus* status, cudaStream_t st);
 // C's row pointers of every product against the nnz its symbolic call counted
 // (status->invalid on a mismatch); used by the checked build
