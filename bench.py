@@ -275,12 +275,15 @@ def traffic_from_profiles(kernel_src_hash):
     return None
 
 
+# the sources the dominant kernel (k_num_rank, numeric.cu) is compiled from
+RANK_KERNEL_SOURCES = ("common.cuh", "numeric.cu", "plan.h", "rowwork.cuh", "semiring.cuh")
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2504_06408_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, name), "rb").read())
+    for name in RANK_KERNEL_SOURCES:
+        h.update(open(os.path.join(csrc, name), "rb").read())
     return h.hexdigest()
 
 
@@ -858,14 +861,16 @@ def main():
         h.symbolic(sr, dA, dA, c_rp, ws)
         h.numeric(sr, dA, dA, c_rp, c_col, c_val, ws)
 
-    for _ in range(args.warmup):
-        step()
-    h.check(ws)
-    torch.cuda.synchronize()
-    h.set_timing(True)
-    times, dense_ms, launches, stages = [], [], 0, []
+    # the clock sampler (an nvidia-smi process) starts before the warm-up steps,
+    # so that its start-up does not fall inside the timed region
     sampler = ClockSampler(torch.cuda.current_device())
+    times, dense_ms, launches, stages = [], [], 0, []
     with sampler:
+        for _ in range(args.warmup):
+            step()
+        h.check(ws)
+        torch.cuda.synchronize()
+        h.set_timing(True)
         barrier()
         torch.cuda.synchronize()
         for _ in range(args.steps):
@@ -991,9 +996,10 @@ def main():
 
         wanted = [w for w in args.forms.split(",") if w]
 
-        def form(name, fn):
-            """one comparison form; a failure is recorded, not fatal to the bench line"""
-            if wanted and not any(w in name for w in wanted):
+        def form(name, fn, key):
+            """one comparison form (selected by `key` with --forms); a failure is
+            recorded, not fatal to the bench line"""
+            if wanted and key not in wanted:
                 return
             try:
                 forms[name] = fn()
@@ -1002,12 +1008,14 @@ def main():
             torch.cuda.empty_cache()
 
         form(f"rmat{args.scale}_min_plus",
-             lambda: learned_forms(api, h, sr, dA, dA, flush, reps, ms_per_step, params, meta))
-        form(f"rmat{args.scale}_bool", lambda: bool_form(api, h, A, flush, reps, peak))
+             lambda: learned_forms(api, h, sr, dA, dA, flush, reps, ms_per_step, params, meta),
+             "min_plus")
+        form(f"rmat{args.scale}_bool", lambda: bool_form(api, h, A, flush, reps, peak), "bool")
         del dA
         torch.cuda.empty_cache()
-        form("er4096", lambda: er_forms(api, h, flush))
-        form("kmer_overlap", lambda: kmer_form(api, h, flush, reps, peak, args.kmer_reads))
+        form("er4096", lambda: er_forms(api, h, flush), "er4096")
+        form("kmer_overlap", lambda: kmer_form(api, h, flush, reps, peak, args.kmer_reads),
+             "kmer_overlap")
 
         def laplacian_form():
             lap = I.laplacian(2048)
@@ -1016,7 +1024,7 @@ def main():
             return learned_forms(api, h, api.PLUS_TIMES_F64, dL, dL, flush, reps, pms, params,
                                  meta)
 
-        form("laplacian2048_plus_times_f64", laplacian_form)
+        form("laplacian2048_plus_times_f64", laplacian_form, "laplacian")
 
         def summa_form():
             A64 = I.rmat(args.scale, dtype=np.float64, seed=1, lo=0.0, hi=1.0)
@@ -1033,12 +1041,13 @@ def main():
             sf["batched_graph_full_vs_unblocked"] = best / pms
             return sf
 
-        form(f"rmat{args.scale}_plus_times_f64_summa4x4", summa_form)
-        form("float_cold_warm", cold_warm_forms)
+        form(f"rmat{args.scale}_plus_times_f64_summa4x4", summa_form, "summa")
+        form("float_cold_warm", cold_warm_forms, "float_cold_warm")
         if not args.no_big_forms:
-            form("rmat20_plus_times_f64_summa4x4_panels", lambda: config4_form(api, peak))
+            form("rmat20_plus_times_f64_summa4x4_panels", lambda: config4_form(api, peak),
+                 "rmat20")
             form("rmat21_plus_times_f64_learned_panels",
-                 lambda: config5_form(api, params, meta, peak))
+                 lambda: config5_form(api, params, meta, peak), "rmat21")
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
