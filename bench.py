@@ -989,7 +989,8 @@ def main():
         reps = args.form_reps
         forms = {"note": "median of %d CUDA-event timings per form, L2 flushed before each; "
                          "each form's C is compared with the plain C on the device "
-                         "(same_* keys); plain_ms of the headline workload = ms_per_step"
+                         "(same_* keys); plain_ms of the headline workload = the median of "
+                         "its timed steps"
                          % reps}
         del c_col, c_val, step
         torch.cuda.empty_cache()
@@ -1008,7 +1009,8 @@ def main():
             torch.cuda.empty_cache()
 
         form(f"rmat{args.scale}_min_plus",
-             lambda: learned_forms(api, h, sr, dA, dA, flush, reps, ms_per_step, params, meta),
+             lambda: learned_forms(api, h, sr, dA, dA, flush, reps, statistics.median(times),
+                                  params, meta),
              "min_plus")
         form(f"rmat{args.scale}_bool", lambda: bool_form(api, h, A, flush, reps, peak), "bool")
         del dA
