@@ -765,7 +765,7 @@ __global__ void __launch_bounds__(kRankThreads, 1)
                Counters* ctr, DevStatus* st, int sp_stride,
                int slab_cols, int bm_words, int cap, const uint32_t* __restrict__ bm_cache,
                const int32_t* __restrict__ row_slot, int cache_words, int64_t cache_slots,
-               int stage_words) {
+               int stage_words, int ovl_mode) {
     using Slot = typename S::Slot;
     using In = typename S::In;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -782,6 +782,9 @@ __global__ void __launch_bounds__(kRankThreads, 1)
     const int tend = ctr->num_bin_off[(kTierDense + 1) * kSubBins];
     // the value array holds `empty` between passes: filled once here, and each
     // pass's write-out empties the slots it reads
+    // overlap: the compact-slot kernel (ovl_mode 1) takes the rows when every
+    // position fits 16 bits, the 24-byte one (ovl_mode 2) when one does not
+    if ((ovl_mode == 1 && ctr->ovl_wide) || (ovl_mode == 2 && !ctr->ovl_wide)) return;
     if constexpr (S::kVal) fill_slots<S>(vals, cap);
     // Rows are claimed one ahead: thread 0 claims the next row while this one
     // starts, and loads its id, then its cache slot, each a phase later, and
@@ -1143,6 +1146,38 @@ static int occupancy_grid(const void* fn, int threads, size_t smem, const DevInf
     return per_sm * dev.sms;
 }
 
+// Launch parameters of the rank-indexed kernel for semiring S: the row bitmap
+// ((word, prefix) pairs) and the value array of `cap` outputs share the
+// CTA's dynamic shared memory; ok = false when they do not fit with at least
+// one slab's outputs.
+struct RankCfg {
+    bool ok;
+    int64_t bm_words, cap;
+    size_t smem;
+    int stage_words;
+};
+template <class S>
+RankCfg rank_cfg(int64_t max_ncols, int64_t slab, const DevInfo& dev) {
+    RankCfg c{};
+    c.bm_words = (max_ncols + 1023) / 1024 * 32;
+    const size_t fixed = (size_t)c.bm_words * 8 + 16;
+    // dynamic shared memory: the device's per-block limit less the kernel's
+    // static variables (the batch arrays and a little more)
+    const size_t optin = dev.max_smem_optin > 0 ? (size_t)dev.max_smem_optin : 212 * 1024;
+    const size_t budget = optin - sizeof(BatchSmem<typename S::In, kRankThreads>) - 1024;
+    int64_t cap = 0;
+    if (fixed + 16 < budget)
+        cap = S::kVal ? (int64_t)((budget - fixed - 32) / rank_entry_bytes<S>()) : 0;
+    if (cap > (int64_t)1 << 30) cap = (int64_t)1 << 30;
+    c.cap = cap;
+    c.ok = fixed < budget && (!S::kVal || cap >= slab) &&
+           rank_region_bytes<S>(cap) + fixed <= budget && max_ncols < INT32_MAX;
+    const size_t region = rank_region_bytes<S>(cap);
+    c.smem = region + fixed;
+    c.stage_words = (int)(region / (kRankThreads / 32) / 4);
+    return c;
+}
+
 struct NumericLaunch {
     const WsPtrs* w;
     DCsr B0;              // B of the first product (slab pointers: single product only)
@@ -1153,6 +1188,21 @@ struct NumericLaunch {
     cudaStream_t st;
     const SlabTables* tables;
     cudaError_t err = cudaSuccess;
+    template <class S>
+    cudaError_t launch_rank(const RankCfg& c, int64_t slab, int nslabs, int ovl_mode) {
+        cudaError_t e = cudaFuncSetAttribute(
+            k_num_rank<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
+        if (e != cudaSuccess) return e;
+        const int grid = occupancy_grid((const void*)k_num_rank<S>, kRankThreads, c.smem, *dev);
+        const bool cached = w->bm_cache && w->bm_cache_words >= c.bm_words;
+        k_num_rank<S><<<grid, kRankThreads, c.smem, st>>>(
+            w->probs, nprob, w->rows_num, w->ctr, w->status, nslabs + 1, (int)slab,
+            (int)c.bm_words, (int)c.cap, cached ? w->bm_cache : nullptr,
+            cached ? w->row_slot : nullptr, (int)w->bm_cache_words, w->bm_cache_slots,
+            c.stage_words, ovl_mode);
+        count_launch(*dev);
+        return cudaGetLastError();
+    }
     template <class S> void operator()() {
         cudaError_t e;
         {   // dense tier
@@ -1174,34 +1224,18 @@ struct NumericLaunch {
             mark_stage(*dev, kStSlabPtr, st);
             // rank-indexed kernel when the row bitmap, its prefix and a value
             // array of at least one slab fit in shared memory
-            const int64_t bm_words = (max_ncols + 1023) / 1024 * 32;
-            const size_t fixed = (size_t)bm_words * 8 + 16;
-            // dynamic shared memory: the device's per-block limit less the
-            // kernel's static variables (the batch arrays and a little more)
-            const size_t optin = dev->max_smem_optin > 0 ? (size_t)dev->max_smem_optin : 212 * 1024;
-            const size_t budget = optin - sizeof(BatchSmem<typename S::In, kRankThreads>) - 1024;
-            int64_t cap = 0;
-            if (fixed + 16 < budget)
-                cap = S::kVal ? (int64_t)((budget - fixed - 32) / rank_entry_bytes<S>()) : 0;
-            if (cap > (int64_t)1 << 30) cap = (int64_t)1 << 30;
-            const bool rank_ok = fixed < budget && (!S::kVal || cap >= slab) &&
-                                 rank_region_bytes<S>(cap) + fixed <= budget &&
-                                 max_ncols < INT32_MAX;
-            if (rank_ok) {
-                const size_t region = rank_region_bytes<S>(cap);
-                const size_t rsmem = region + fixed;
-                const int stage_words = (int)(region / (kRankThreads / 32) / 4);
-                e = cudaFuncSetAttribute(k_num_rank<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)rsmem);
+            const RankCfg rc = rank_cfg<S>(max_ncols, slab, *dev);
+            if (rc.ok) {
+                if constexpr (std::is_same<S, SrOverlap>::value) {
+                    // compact 12-byte slots when every position fits 16 bits
+                    // (twice the outputs per value pass, 32-bit atomics)
+                    const RankCfg cc = rank_cfg<SrOverlapC>(max_ncols, slab, *dev);
+                    e = launch_rank<SrOverlapC>(cc, slab, nslabs, 1);
+                    if (e == cudaSuccess) e = launch_rank<S>(rc, slab, nslabs, 2);
+                } else {
+                    e = launch_rank<S>(rc, slab, nslabs, 0);
+                }
                 if (e != cudaSuccess) { err = e; return; }
-                const int grid = occupancy_grid((const void*)k_num_rank<S>, kRankThreads, rsmem, *dev);
-                const bool cached = w->bm_cache && w->bm_cache_words >= bm_words;
-                k_num_rank<S><<<grid, kRankThreads, rsmem, st>>>(
-                    w->probs, nprob, w->rows_num, w->ctr, w->status, nslabs + 1, (int)slab,
-                    (int)bm_words, (int)cap, cached ? w->bm_cache : nullptr,
-                    cached ? w->row_slot : nullptr, (int)w->bm_cache_words, w->bm_cache_slots,
-                    stage_words);
-                count_launch(*dev);
             } else {
                 const int grid = occupancy_grid((const void*)k_num_dense<S>, kBlockThreads, smem, *dev);
                 k_num_dense<S><<<grid, kBlockThreads, smem, st>>>(w->probs, nprob, w->rows_num, w->ctr,
@@ -1276,10 +1310,13 @@ cudaError_t launch_numeric(int sr, const WsPtrs& w, const DCsr& B0, int nprob, i
     cudaMemsetAsync(&w.ctr->claim[2], 0, 2 * sizeof(int32_t), st);
     cudaMemsetAsync(&w.ctr->ovl_wide, 0, sizeof(int32_t), st);
     cudaMemsetAsync(&w.ctr->num_block_max, 0, sizeof(int64_t), st);
-    if (sr == SR_OVERLAP && t.num_block_max_nnz <= kOvlCompactMax) {
-        // the compact overlap block tier, when every position of every A and
-        // B fits 16 bits
-        for (int p = 0; p < nprob && probs_host; ++p) {
+    if (sr == SR_OVERLAP && !probs_host) {
+        // positions unchecked: no compact overlap slots
+        cudaMemsetAsync(&w.ctr->ovl_wide, 1, 1, st);
+    } else if (sr == SR_OVERLAP) {
+        // compact overlap slots (block and rank tiers) when every position of
+        // every A and B fits 16 bits
+        for (int p = 0; p < nprob; ++p) {
             const DCsr* mats[2] = {&probs_host->p[p].A, &probs_host->p[p].B};
             for (const DCsr* M : mats) {
                 int64_t blocks = (M->nrows + 255) / 256;
@@ -1288,7 +1325,8 @@ cudaError_t launch_numeric(int sr, const WsPtrs& w, const DCsr& B0, int nprob, i
                 if (M->val) k_ovl_check<<<(unsigned)blocks, 256, 0, st>>>(*M, w.ctr);
             }
         }
-        k_ovl_limit<<<1, 32, 0, st>>>(w.ctr, probs_host ? kOvlCompactMax : 0);
+        k_ovl_limit<<<1, 32, 0, st>>>(
+            w.ctr, t.num_block_max_nnz <= kOvlCompactMax ? kOvlCompactMax : 0);
         count_launch(dev, 2 * nprob + 1);
     }
     int64_t blocks = (R + 255) / 256;

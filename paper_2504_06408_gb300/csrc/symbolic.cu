@@ -239,22 +239,29 @@ __global__ void __launch_bounds__(kWarpTierWarps * 32)
     }
 }
 
-__global__ void __launch_bounds__(kBlockThreads)
+constexpr int kSymBlockSmallThreads = 256;   // CTA size for rows with ub < 4096
+
+// One launch per class of rows (sub-bins [sub_lo, sub_hi) of the tier, by
+// floor(log2 ub_i)), each with the shared memory its largest table needs, so
+// that classes of small rows keep many CTAs per SM.
+template <int NT>
+__global__ void __launch_bounds__(NT)
     k_sym_block(const Prob* __restrict__ probs, int nprob, const int32_t* __restrict__ rows,
                 Counters* ctr, const int64_t* __restrict__ ub, int64_t* __restrict__ cnt,
                 DevStatus* st, int table_slots, int64_t dense_min, uint32_t* bm_cache,
-                int32_t* row_slot, int64_t cache_words, int64_t cache_slots) {
+                int32_t* row_slot, int64_t cache_words, int64_t cache_slots, int sub_lo,
+                int sub_hi, int claim) {
     extern __shared__ int32_t smem_i32[];
     int32_t* tab = smem_i32;
-    __shared__ BatchSmem<char> bs;
+    __shared__ BatchSmem<char, NT> bs;
     __shared__ int s_row, s_cnt, s_slot;
     const int lane = lane_id();
-    const int beg = ctr->sym_bin_off[kTierBlock * kSubBins];
-    const int end = ctr->sym_bin_off[(kTierBlock + 1) * kSubBins];
+    const int beg = ctr->sym_bin_off[kTierBlock * kSubBins + sub_lo];
+    const int end = ctr->sym_bin_off[kTierBlock * kSubBins + sub_hi];
     const Slab single{0, 0, true, true, true, nullptr, nullptr, 0, 0};
     for (;;) {
         if (threadIdx.x == 0) {
-            s_row = beg + atomicAdd(&ctr->claim[0], 1);
+            s_row = beg + atomicAdd(&ctr->claim[claim], 1);
             s_cnt = 0;
         }
         __syncthreads();
@@ -771,18 +778,42 @@ cudaError_t launch_symbolic(const WsPtrs& w, int nprob, int64_t R, const Tuning&
         mark_stage(dev, kStSymDense, st);
     }
     {
-        int64_t T = next_pow2(2 * t.sym_block_max_ub);
-        if (T < 32) T = 32;
-        const size_t smem = (size_t)T * sizeof(int32_t);
-        e = cudaFuncSetAttribute(k_sym_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
+        // classes by floor(log2 ub_i), heaviest first: sub-bins [0, 28) ub >= 4096
+        // (tables up to the tier's limit, 512 threads), 28: ub in [2048, 4096)
+        // (8192 slots), [29, 40): ub < 2048 (4096 slots); 256 threads for both
+        int64_t Tmax = next_pow2(2 * t.sym_block_max_ub);
+        if (Tmax < 32) Tmax = 32;
+        struct Class { int64_t min_ub, T; int lo, hi, claim; bool wide; };
+        const Class classes[3] = {{4096, Tmax, 0, kSubBins - 12, 0, true},
+                                  {2048, 8192, kSubBins - 12, kSubBins - 11, 7, false},
+                                  {0, 4096, kSubBins - 11, kSubBins, 15, false}};
+        e = cudaFuncSetAttribute(k_sym_block<kBlockThreads>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(Tmax * 4));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_sym_block<kSymBlockSmallThreads>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 8192 * 4);
         if (e != cudaSuccess) return e;
-        const int grid = occupancy((const void*)k_sym_block, kBlockThreads, smem, dev);
-        k_sym_block<<<grid, kBlockThreads, smem, st>>>(w.probs, nprob, w.rows_sym, w.ctr, w.ub,
-                                                       w.cnt, w.status, (int)T, t.num_block_max_nnz,
-                                                       w.bm_cache, w.row_slot, w.bm_cache_words,
-                                                       w.bm_cache_slots);
-        count_launch(dev);
+        for (const Class& c : classes) {
+            if (t.sym_block_max_ub < c.min_ub) continue;   // no row of this class
+            const int64_t T = c.T < Tmax ? c.T : Tmax;
+            const size_t smem = (size_t)T * sizeof(int32_t);
+            if (c.wide) {
+                const int grid = occupancy((const void*)k_sym_block<kBlockThreads>, kBlockThreads,
+                                           smem, dev);
+                k_sym_block<kBlockThreads><<<grid, kBlockThreads, smem, st>>>(
+                    w.probs, nprob, w.rows_sym, w.ctr, w.ub, w.cnt, w.status, (int)T,
+                    t.num_block_max_nnz, w.bm_cache, w.row_slot, w.bm_cache_words,
+                    w.bm_cache_slots, c.lo, c.hi, c.claim);
+            } else {
+                const int grid = occupancy((const void*)k_sym_block<kSymBlockSmallThreads>,
+                                           kSymBlockSmallThreads, smem, dev);
+                k_sym_block<kSymBlockSmallThreads><<<grid, kSymBlockSmallThreads, smem, st>>>(
+                    w.probs, nprob, w.rows_sym, w.ctr, w.ub, w.cnt, w.status, (int)T,
+                    t.num_block_max_nnz, w.bm_cache, w.row_slot, w.bm_cache_words,
+                    w.bm_cache_slots, c.lo, c.hi, c.claim);
+            }
+            count_launch(dev);
+        }
         mark_stage(dev, kStSymBlock, st);
     }
     {
