@@ -309,6 +309,10 @@ SPG_DEV void cta_walk_segments(const DCsr& B, int64_t beg, int64_t len, In a,
                                 if (bv <= lane) k += step;
                             }
                             me = e + k;
+                            // the next window starts in lane 31's segment or
+                            // later: no walk over this window's segments again
+                            const int e31 = __shfl_sync(kFull, me, 31);
+                            e = e31 < nseg - 1 ? e31 : nseg - 1;
                         }
                     }
                     qv[u] = bs.base[me] + t;
