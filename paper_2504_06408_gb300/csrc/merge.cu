@@ -261,8 +261,12 @@ __global__ void __launch_bounds__(kMergeThreads)
     using Out = typename S::Out;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_wsum[kMergeThreads / 32];
+    // the row's entries in every stage: start in the stage's partial, and
+    // offset in the stages' concatenation (s_off[nparts] = all entries)
+    __shared__ int64_t s_a[kMaxStages], s_off[kMaxStages + 1];
     const int tid = threadIdx.x, lane = lane_id(), wid = warp_id();
     constexpr int nwarps = kMergeThreads / 32;
+    constexpr int kU = 4;   // entry loads in flight per thread
     const int nheavy = ctr->claim[kClMergeHeavy];
     for (int r = blockIdx.x; r < nheavy; r += gridDim.x) {
         const int64_t g = heavy[r];
@@ -272,18 +276,41 @@ __global__ void __launch_bounds__(kMergeThreads)
         // (word, prefix) pairs of the row's bitmap, then the written bits
         uint2* pw = reinterpret_cast<uint2*>(smem_raw);
         uint32_t* done = reinterpret_cast<uint32_t*>(smem_raw + ((size_t)words + 1) * 8);
+        const int np = M.nparts;
+        if (wid == 0) {   // every stage's row bounds at once (np <= 32)
+            int64_t a = 0, len = 0;
+            if (lane < np) {
+                a = ld_i64(M.rp[lane] + i);
+                len = ld_i64(M.rp[lane] + i + 1) - a;
+                s_a[lane] = a;
+            }
+            const int64_t incl = warp_incl_scan(len);
+            if (lane < np) s_off[lane + 1] = incl;
+            if (lane == 0) s_off[0] = 0;
+        }
         for (int w = tid; w < words; w += kMergeThreads) {
             pw[w] = make_uint2(0u, 0u);
             if (kWrite) done[w] = 0u;
         }
         __syncthreads();
-        for (int s = 0; s < M.nparts; ++s) {
-            const int64_t a = ld_i64(M.rp[s] + i), b = ld_i64(M.rp[s] + i + 1);
-            for (int64_t q = a + tid; q < b; q += kMergeThreads) {
-                const int32_t c = ld_i32(M.col[s] + q);
-                const uint32_t bit = 1u << (c & 31);
-                uint32_t* wp = &pw[c >> 5].x;
-                if (!(*wp & bit)) atomicOr(wp, bit);
+        // bitmap of the row's columns (no barrier between stages: the OR does
+        // not depend on their order), kU loads in flight per thread
+        for (int s = 0; s < np; ++s) {
+            const int64_t a = s_a[s], len = s_off[s + 1] - s_off[s];
+            for (int64_t j0 = tid; j0 < len; j0 += kU * kMergeThreads) {
+                int32_t c[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int64_t j = j0 + (int64_t)u * kMergeThreads;
+                    c[u] = j < len ? ld_i32(M.col[s] + a + j) : -1;
+                }
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    if (c[u] < 0) continue;
+                    const uint32_t bit = 1u << (c[u] & 31);
+                    uint32_t* wp = &pw[c[u] >> 5].x;
+                    if (!(*wp & bit)) atomicOr(wp, bit);
+                }
             }
         }
         __syncthreads();
@@ -313,24 +340,38 @@ __global__ void __launch_bounds__(kMergeThreads)
             __syncthreads();
             const int64_t off = M.c_rp[i], n = M.c_rp[i + 1] - off;
             Out* cv = reinterpret_cast<Out*>(M.c_val);
-            for (int s = 0; s < M.nparts; ++s) {   // stage order: (+) folds left to right
-                const int64_t a = ld_i64(M.rp[s] + i), b = ld_i64(M.rp[s] + i + 1);
-                for (int64_t q = a + tid; q < b; q += kMergeThreads) {
-                    const int32_t c = ld_i32(M.col[s] + q);
-                    const uint2 e = pw[c >> 5];
-                    const uint32_t bit = 1u << (c & 31);
-                    const int64_t rk = (int64_t)e.y + __popc(e.x & (bit - 1u));
-                    if (rk >= n) {
-                        flag_overflow(st, g);
-                        continue;
+            for (int s = 0; s < np; ++s) {   // stage order: (+) folds left to right
+                const int64_t a = s_a[s], len = s_off[s + 1] - s_off[s];
+                const Out* sv = reinterpret_cast<const Out*>(M.val[s]);
+                for (int64_t j0 = tid; j0 < len; j0 += kU * kMergeThreads) {
+                    int32_t c[kU];
+                    Out x[kU];
+#pragma unroll
+                    for (int u = 0; u < kU; ++u) {   // the loads first, kU in flight
+                        const int64_t j = j0 + (int64_t)u * kMergeThreads;
+                        c[u] = -1;
+                        if (j < len) {
+                            c[u] = ld_i32(M.col[s] + a + j);
+                            if constexpr (S::kVal) x[u] = sv[a + j];
+                        }
                     }
-                    if (!(done[c >> 5] & bit)) {   // the first stage that holds this column
-                        M.c_col[off + rk] = c;
-                        if constexpr (S::kVal) cv[off + rk] = reinterpret_cast<const Out*>(M.val[s])[q];
-                        atomicOr(done + (c >> 5), bit);
-                    } else {
-                        if constexpr (S::kVal)
-                            cv[off + rk] = S::add(cv[off + rk], reinterpret_cast<const Out*>(M.val[s])[q]);
+#pragma unroll
+                    for (int u = 0; u < kU; ++u) {
+                        if (c[u] < 0) continue;
+                        const uint2 e = pw[c[u] >> 5];
+                        const uint32_t bit = 1u << (c[u] & 31);
+                        const int64_t rk = (int64_t)e.y + __popc(e.x & (bit - 1u));
+                        if (rk >= n) {
+                            flag_overflow(st, g);
+                            continue;
+                        }
+                        if (!(done[c[u] >> 5] & bit)) {   // the first stage that holds this column
+                            M.c_col[off + rk] = c[u];
+                            if constexpr (S::kVal) cv[off + rk] = x[u];
+                            atomicOr(done + (c[u] >> 5), bit);
+                        } else {
+                            if constexpr (S::kVal) cv[off + rk] = S::add(cv[off + rk], x[u]);
+                        }
                     }
                 }
                 __syncthreads();   // this stage's values land before the next stage folds into them
