@@ -108,6 +108,10 @@ typedef struct {
                                    that would cross it is not allocated and the call
                                    returns SPG_ERR_OOM (buffers already held stay with
                                    the handle).  0: no limit beyond the device's        */
+    int64_t rank_light_ub;      /* numeric dense tier: rows with fewer products than
+                                   this (rounded up to a power of two) whose outputs
+                                   fit one pass of a half-SM CTA run two per SM
+                                   (0: 8192; < 0: never)                                */
 } spg_tuning;
 
 /* Counters of the last analysis on a handle (host copy, filled by spgemm_symbolic). */

@@ -26,6 +26,7 @@ SPACE = {
     "num_warp_max_nnz": [32, 64, 128, 256, 512],
     "num_block_max_nnz": [512, 1024, 2048, 4096],
     "dense_slab_cols": [8192, 16384, 32768],
+    "rank_light_ub": [-1, 4096, 8192, 16384, 65536],
 }
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "spgemm_gb300_tuning.json")

@@ -122,6 +122,7 @@ Tuning default_tuning(int sr) {
     t.num_warp_max_nnz = 128;
     t.num_block_max_nnz = 2048;
     t.bitmap_cache_bytes = (int64_t)4 << 30;
+    t.rank_light_ub = 8192;
     switch (sr) {
         case SR_BOOL: t.dense_slab_cols = 1 << 18; break;
         case SR_MP_F32: case SR_PT_F32: t.dense_slab_cols = 16384; break;
@@ -160,6 +161,9 @@ Tuning clamp_tuning(Tuning t, int sr) {
     if (t.dense_slab_cols > 65536 * 16) t.dense_slab_cols = 65536 * 16;
     while (num_dense_smem(sr, t.dense_slab_cols) > kSmemBudget && t.dense_slab_cols > 1024)
         t.dense_slab_cols -= 1024;
+    if (t.rank_light_ub < 0) t.rank_light_ub = 0;
+    if (t.rank_light_ub > ((int64_t)1 << 30)) t.rank_light_ub = (int64_t)1 << 30;
+    if (t.rank_light_ub > 0) t.rank_light_ub = next_pow2(t.rank_light_ub);
     return t;
 }
 
@@ -195,6 +199,7 @@ static Tuning effective_tuning(const spg_handle* h, int sr) {
     if (u.dense_slab_cols > 0) t.dense_slab_cols = u.dense_slab_cols;
     if (u.sym_slab_cols > 0) t.sym_slab_cols = u.sym_slab_cols;
     if (u.bitmap_cache_bytes != 0) t.bitmap_cache_bytes = u.bitmap_cache_bytes;
+    if (u.rank_light_ub != 0) t.rank_light_ub = u.rank_light_ub;
     return clamp_tuning(t, sr);
 }
 
@@ -351,6 +356,9 @@ spg_status spgemm_create(spg_handle** handle) {
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&h->dev.max_smem_optin,
                                    cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&h->dev.max_smem_sm,
+                                   cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device);
     if (e == cudaSuccess) e = cudaMallocHost(&h->pinned, kPinnedBytes);
     if (e != cudaSuccess) {
         delete h;

@@ -24,7 +24,7 @@ namespace spg {
 
 constexpr uint8_t kRouteLearned = 0, kRouteExact = 1;
 
-// claim[] slots used here (the plain kernels use 0..3, 7 and 15)
+// claim[] slots used here (the plain kernels use 0..4, 7 and 15)
 constexpr int kClWarpRows = 8, kClBlockRows = 9, kClBlockNext = 10, kClOverflow = 11,
               kClTinyRows = 12;
 constexpr int kTinyRows = 1;   // tiny rows per warp at a time (more costs registers)

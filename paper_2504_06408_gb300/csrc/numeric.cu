@@ -751,34 +751,45 @@ constexpr size_t rank_entry_bytes() {
     return S::kVal ? sizeof(typename S::Slot) + 4 : 0;
 }
 // the value array's region, which first serves as the warps' C.col staging:
-// at least 3 KB per warp
-constexpr size_t kRankStageMin = (size_t)(kRankThreads / 32) * 3072;
-template <class S>
+// at least 3 KB per warp of an NT-thread CTA
+template <class S, int NT>
 __host__ __device__ inline size_t rank_region_bytes(int64_t cap) {
     const size_t v = rank_val_bytes<S>(cap);
-    return v > kRankStageMin ? v : kRankStageMin;
+    constexpr size_t kStageMin = (size_t)(NT / 32) * 3072;
+    return v > kStageMin ? v : kStageMin;
 }
 
-template <class S>
-__global__ void __launch_bounds__(kRankThreads, 1)
+// NT = 1024: one CTA per SM, the whole shared memory for the bitmap and the
+// value array (value passes over slab groups).  NT = 512: two CTAs per SM,
+// each with half of it, for rows whose outputs fit one pass: two rows in
+// flight per SM hide the per-row phases' latency.  Rows are light when they
+// lie in the dense tier's sub-bins from light_sub on (ub_i below the tuning's
+// rank_light_ub: a few thousand products, whose time is per-row latency, not
+// product work) and nnz(C_i) <= n_split.  The 512-thread kernel (small = 1)
+// walks only those sub-bins and takes the light rows; the 1024-thread one
+// (small = 0) takes every other row, each with its own claim counter.
+template <class S, int NT>
+__global__ void __launch_bounds__(NT, kRankThreads / NT)
     k_num_rank(const Prob* __restrict__ probs, int nprob, const int32_t* __restrict__ rows,
                Counters* ctr, DevStatus* st, int sp_stride,
                int slab_cols, int bm_words, int cap, const uint32_t* __restrict__ bm_cache,
                const int32_t* __restrict__ row_slot, int cache_words, int64_t cache_slots,
-               int stage_words, int ovl_mode) {
+               int stage_words, int ovl_mode, int light_sub, int64_t n_split, int small,
+               int claim) {
     using Slot = typename S::Slot;
     using In = typename S::In;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Slot* vals = reinterpret_cast<Slot*>(smem_raw);                          // [cap]
     int32_t* cols = reinterpret_cast<int32_t*>(smem_raw + rank_slot_bytes<S>(cap));   // [cap]
     // filled with 16-byte stores: its offset must be 16-aligned
-    uint2* bw = reinterpret_cast<uint2*>(smem_raw + rank_region_bytes<S>(cap));   // [words + 1]
-    __shared__ BatchSmem<In, kRankThreads> bs;
+    uint2* bw = reinterpret_cast<uint2*>(smem_raw + rank_region_bytes<S, NT>(cap));   // [words + 1]
+    __shared__ BatchSmem<In, NT> bs;
     __shared__ int s_row;
-    __shared__ int s_wsum[kRankThreads / 32];
+    __shared__ int s_wsum[NT / 32];
     const int lane = lane_id(), wid = warp_id(), nwarps = blockDim.x >> 5;
     const int tid = threadIdx.x;
-    const int tbeg = ctr->num_bin_off[kTierDense * kSubBins];
+    const int tmid = ctr->num_bin_off[kTierDense * kSubBins + light_sub];
+    const int tbeg = small ? tmid : ctr->num_bin_off[kTierDense * kSubBins];
     const int tend = ctr->num_bin_off[(kTierDense + 1) * kSubBins];
     // the value array holds `empty` between passes: filled once here, and each
     // pass's write-out empties the slots it reads
@@ -791,7 +802,7 @@ __global__ void __launch_bounds__(kRankThreads, 1)
     // prefetches its cached bitmap into L2 before the value passes, so the
     // next row's bitmap copy does not wait on DRAM (nothing waits on these
     // loads until a phase boundary has passed).
-    if (tid == 0) s_row = tbeg + atomicAdd(&ctr->claim[3], 1);
+    if (tid == 0) s_row = tbeg + atomicAdd(&ctr->claim[claim], 1);
     __syncthreads();
     for (;;) {
         const int r = s_row;   // written one row ahead, read after a barrier
@@ -799,19 +810,25 @@ __global__ void __launch_bounds__(kRankThreads, 1)
         int nr = tend;
         int64_t g2 = -1;
         int slot2 = -1;
-        if (tid == 0) nr = tbeg + atomicAdd(&ctr->claim[3], 1);
+        if (tid == 0) nr = tbeg + atomicAdd(&ctr->claim[claim], 1);
         const int64_t g = rows[r];
         const Prob& P = probs[nprob == 1 ? 0 : find_prob(probs, nprob, g)];
         const int64_t i = g - P.row_base;
         const int64_t off = P.c_rp[i];
         const int64_t n = P.c_rp[i + 1] - off;
+        if (r >= tmid && (n <= n_split) != (small != 0)) {   // the other kernel's row
+            __syncthreads();           // every thread has read r
+            if (tid == 0) s_row = nr;
+            __syncthreads();
+            continue;
+        }
         const int64_t a0 = ld_i64(P.A.rp + i), a1 = ld_i64(P.A.rp + i + 1);
         const int ncols = (int)P.B.ncols;
         const int words = (ncols + 31) >> 5;
         const int nslabs = (ncols + slab_cols - 1) / slab_cols;
         const int32_t* __restrict__ sp = P.sp;   // this product's slab-start table, or null
         const RowEntries mode = a1 - a0 <= 32 ? kEntriesPerLane
-                                : a1 - a0 <= kRankThreads ? kEntriesPerThread : kEntriesBatched;
+                                : a1 - a0 <= NT ? kEntriesPerThread : kEntriesBatched;
         // (a slot outside the cache means the workspace did not come from this
         // product's symbolic call: the row is rebuilt and checked against c_rp)
         const int slot = row_slot ? row_slot[g] : -1;
@@ -1146,35 +1163,43 @@ static int occupancy_grid(const void* fn, int threads, size_t smem, const DevInf
     return per_sm * dev.sms;
 }
 
-// Launch parameters of the rank-indexed kernel for semiring S: the row bitmap
-// ((word, prefix) pairs) and the value array of `cap` outputs share the
-// CTA's dynamic shared memory; ok = false when they do not fit with at least
-// one slab's outputs.
+// Launch parameters of the rank-indexed kernel for semiring S on NT-thread
+// CTAs: the row bitmap ((word, prefix) pairs) and the value array of `cap`
+// outputs share the CTA's dynamic shared memory.  NT = 1024 takes the whole
+// per-block limit and needs room for at least one slab's outputs (rows of any
+// size, in value passes); NT = 512 takes half an SM (two CTAs per SM) and is
+// given only rows whose outputs all fit one pass.  ok = false when it does
+// not fit.
 struct RankCfg {
     bool ok;
     int64_t bm_words, cap;
     size_t smem;
     int stage_words;
 };
-template <class S>
+template <class S, int NT>
 RankCfg rank_cfg(int64_t max_ncols, int64_t slab, const DevInfo& dev) {
     RankCfg c{};
     c.bm_words = (max_ncols + 1023) / 1024 * 32;
     const size_t fixed = (size_t)c.bm_words * 8 + 16;
-    // dynamic shared memory: the device's per-block limit less the kernel's
-    // static variables (the batch arrays and a little more)
-    const size_t optin = dev.max_smem_optin > 0 ? (size_t)dev.max_smem_optin : 212 * 1024;
-    const size_t budget = optin - sizeof(BatchSmem<typename S::In, kRankThreads>) - 1024;
-    int64_t cap = 0;
-    if (fixed + 16 < budget)
-        cap = S::kVal ? (int64_t)((budget - fixed - 32) / rank_entry_bytes<S>()) : 0;
+    // dynamic shared memory: the per-block limit (half an SM's for NT = 512)
+    // less the kernel's static variables (the batch arrays and a little more)
+    size_t lim = dev.max_smem_optin > 0 ? (size_t)dev.max_smem_optin : 212 * 1024;
+    if (NT < kRankThreads) {
+        const size_t per_sm = dev.max_smem_sm > 0 ? (size_t)dev.max_smem_sm : 228 * 1024;
+        const size_t half = per_sm / (kRankThreads / NT) - 1024;   // 1 KB reserved per CTA
+        if (half < lim) lim = half;
+    }
+    const size_t stat = sizeof(BatchSmem<typename S::In, NT>) + 1024;
+    if (lim <= stat + fixed + 32) return c;
+    const size_t budget = lim - stat;
+    int64_t cap = S::kVal ? (int64_t)((budget - fixed - 32) / rank_entry_bytes<S>()) : 0;
     if (cap > (int64_t)1 << 30) cap = (int64_t)1 << 30;
     c.cap = cap;
-    c.ok = fixed < budget && (!S::kVal || cap >= slab) &&
-           rank_region_bytes<S>(cap) + fixed <= budget && max_ncols < INT32_MAX;
-    const size_t region = rank_region_bytes<S>(cap);
+    const bool room = NT == kRankThreads ? (!S::kVal || cap >= slab) : (!S::kVal || cap >= 1);
+    c.ok = room && rank_region_bytes<S, NT>(cap) + fixed <= budget && max_ncols < INT32_MAX;
+    const size_t region = rank_region_bytes<S, NT>(cap);
     c.smem = region + fixed;
-    c.stage_words = (int)(region / (kRankThreads / 32) / 4);
+    c.stage_words = (int)(region / (NT / 32) / 4);
     return c;
 }
 
@@ -1188,20 +1213,52 @@ struct NumericLaunch {
     cudaStream_t st;
     const SlabTables* tables;
     cudaError_t err = cudaSuccess;
-    template <class S>
-    cudaError_t launch_rank(const RankCfg& c, int64_t slab, int nslabs, int ovl_mode) {
+    template <class S, int NT>
+    cudaError_t launch_rank(const RankCfg& c, int64_t slab, int nslabs, int ovl_mode,
+                            int light_sub, int64_t n_split, int small, int claim) {
         cudaError_t e = cudaFuncSetAttribute(
-            k_num_rank<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
+            k_num_rank<S, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
         if (e != cudaSuccess) return e;
-        const int grid = occupancy_grid((const void*)k_num_rank<S>, kRankThreads, c.smem, *dev);
+        const int grid = occupancy_grid((const void*)k_num_rank<S, NT>, NT, c.smem, *dev);
         const bool cached = w->bm_cache && w->bm_cache_words >= c.bm_words;
-        k_num_rank<S><<<grid, kRankThreads, c.smem, st>>>(
+        k_num_rank<S, NT><<<grid, NT, c.smem, st>>>(
             w->probs, nprob, w->rows_num, w->ctr, w->status, nslabs + 1, (int)slab,
             (int)c.bm_words, (int)c.cap, cached ? w->bm_cache : nullptr,
             cached ? w->row_slot : nullptr, (int)w->bm_cache_words, w->bm_cache_slots,
-            c.stage_words, ovl_mode);
+            c.stage_words, ovl_mode, light_sub, n_split, small, claim);
         count_launch(*dev);
         return cudaGetLastError();
+    }
+    // the dense tier's rows split: light rows (fewer than rank_light_ub products)
+    // whose outputs fit one pass of the 512-thread kernel take it (claim slot
+    // 4), the rest the 1024-thread kernel (claim slot 3)
+    template <class S>
+    cudaError_t launch_rank_pair(int64_t slab, int nslabs, int ovl_mode) {
+        const RankCfg big = rank_cfg<S, kRankThreads>(max_ncols, slab, *dev);
+        const RankCfg small = rank_cfg<S, kRankThreads / 2>(max_ncols, slab, *dev);
+        int64_t split = 0;
+        if (small.ok && t->rank_light_ub > 0) {   // only where two CTAs really fit an SM
+            cudaError_t ea = cudaFuncSetAttribute(k_num_rank<S, kRankThreads / 2>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)small.smem);
+            if (ea != cudaSuccess) return ea;
+            int per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, (const void*)k_num_rank<S, kRankThreads / 2>, kRankThreads / 2, small.smem);
+            if (per_sm >= 2) split = S::kVal ? small.cap : INT64_MAX;
+        }
+        cudaError_t e = cudaSuccess;
+        // sub-bins by floor(log2 ub_i), heaviest first: ub_i < rank_light_ub (a
+        // power of two) from kSubBins - log2(rank_light_ub) on (kSubBins: none)
+        int lg = 0;
+        while (lg < kSubBins && ((int64_t)1 << lg) < t->rank_light_ub) ++lg;
+        const int light_sub = split > 0 ? kSubBins - lg : kSubBins;
+        if (split > 0)
+            e = launch_rank<S, kRankThreads / 2>(small, slab, nslabs, ovl_mode, light_sub, split,
+                                                 1, 4);
+        if (e == cudaSuccess)
+            e = launch_rank<S, kRankThreads>(big, slab, nslabs, ovl_mode, light_sub, split, 0, 3);
+        return e;
     }
     template <class S> void operator()() {
         cudaError_t e;
@@ -1224,16 +1281,15 @@ struct NumericLaunch {
             mark_stage(*dev, kStSlabPtr, st);
             // rank-indexed kernel when the row bitmap, its prefix and a value
             // array of at least one slab fit in shared memory
-            const RankCfg rc = rank_cfg<S>(max_ncols, slab, *dev);
+            const RankCfg rc = rank_cfg<S, kRankThreads>(max_ncols, slab, *dev);
             if (rc.ok) {
                 if constexpr (std::is_same<S, SrOverlap>::value) {
                     // compact 12-byte slots when every position fits 16 bits
                     // (twice the outputs per value pass, 32-bit atomics)
-                    const RankCfg cc = rank_cfg<SrOverlapC>(max_ncols, slab, *dev);
-                    e = launch_rank<SrOverlapC>(cc, slab, nslabs, 1);
-                    if (e == cudaSuccess) e = launch_rank<S>(rc, slab, nslabs, 2);
+                    e = launch_rank_pair<SrOverlapC>(slab, nslabs, 1);
+                    if (e == cudaSuccess) e = launch_rank_pair<S>(slab, nslabs, 2);
                 } else {
-                    e = launch_rank<S>(rc, slab, nslabs, 0);
+                    e = launch_rank_pair<S>(slab, nslabs, 0);
                 }
                 if (e != cudaSuccess) { err = e; return; }
             } else {
@@ -1307,7 +1363,7 @@ cudaError_t launch_numeric(int sr, const WsPtrs& w, const DCsr& B0, int nprob, i
     if (R == 0) return cudaSuccess;
     // reset numeric bins and claims
     cudaMemsetAsync(w.ctr->num_bin_count, 0, sizeof(w.ctr->num_bin_count), st);
-    cudaMemsetAsync(&w.ctr->claim[2], 0, 2 * sizeof(int32_t), st);
+    cudaMemsetAsync(&w.ctr->claim[2], 0, 3 * sizeof(int32_t), st);   // slots 2..4
     cudaMemsetAsync(&w.ctr->ovl_wide, 0, sizeof(int32_t), st);
     cudaMemsetAsync(&w.ctr->num_block_max, 0, sizeof(int64_t), st);
     if (sr == SR_OVERLAP && !probs_host) {

@@ -24,6 +24,7 @@ struct Tuning {
     int64_t dense_slab_cols;
     int64_t sym_slab_cols;
     int64_t bitmap_cache_bytes;   // < 0: no bitmap cache
+    int64_t rank_light_ub;        // light rows of the rank kernel: ub_i below this (<= 0: none)
 };
 
 // Per-semiring defaults chosen so that every tier's shared memory fits.
@@ -106,6 +107,7 @@ struct StageTimer {
 struct DevInfo {
     int sms;
     int max_smem_optin;
+    int max_smem_sm = 0;           // shared memory per SM (0: unknown)
     int64_t* launches = nullptr;   // kernels launched (incremented by the launchers)
     StageTimer* timer = nullptr;
 };

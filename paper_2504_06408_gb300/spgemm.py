@@ -53,7 +53,8 @@ class spg_tuning(ctypes.Structure):
                 ("num_warp_max_nnz", ctypes.c_int64), ("num_block_max_nnz", ctypes.c_int64),
                 ("dense_slab_cols", ctypes.c_int64), ("sym_slab_cols", ctypes.c_int64),
                 ("bitmap_cache_bytes", ctypes.c_int64), ("host_panel_bytes", ctypes.c_int64),
-                ("deterministic", ctypes.c_int64), ("host_alloc_limit", ctypes.c_int64)]
+                ("deterministic", ctypes.c_int64), ("host_alloc_limit", ctypes.c_int64),
+                ("rank_light_ub", ctypes.c_int64)]
 
 
 class spg_stats(ctypes.Structure):

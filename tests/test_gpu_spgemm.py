@@ -43,9 +43,10 @@ TIERS = {
     # rebuilds every row's bitmap from its products
     "dense_rebuild": dict(sym_warp_max_ub=1, sym_block_max_ub=1, num_warp_max_nnz=1,
                           num_block_max_nnz=1, bitmap_cache_bytes=1),
-    # the rank kernel with 1024-column slabs: many value passes per row
+    # the rank kernel with 1024-column slabs: many value passes per row, every
+    # row on the 1024-thread kernel (no light rows on half-SM CTAs)
     "dense_small_slabs_rank": dict(sym_warp_max_ub=1, sym_block_max_ub=1, num_warp_max_nnz=1,
-                                   num_block_max_nnz=1, dense_slab_cols=1024),
+                                   num_block_max_nnz=1, dense_slab_cols=1024, rank_light_ub=-1),
 }
 
 
@@ -248,6 +249,35 @@ def test_dense_row_entry_modes_and_value_passes(sr, tier):
     # the 3000-entry row has more outputs than one value pass of the rank
     # kernel holds (about 18K at 8 bytes per output)
     assert got.rp[5] - got.rp[4] > 40_000
+
+
+def light_dense_rows(seed):
+    """Rows of 40, 300, 520 and 600 entries over B rows of 8 random columns out
+    of 120,000: a few thousand products and outputs each (ub <= 4,800), i.e.
+    dense-tier rows light enough for the 512-thread rank kernel, with one
+    entry per lane, per thread, and in two batches of entries."""
+    rng = np.random.default_rng(seed)
+    degs = [40, 300, 520, 600, 0]
+    K, N, per_b = 3000, 120_000, 8
+    a_rows = np.repeat(np.arange(len(degs)), degs)
+    a_cols = np.concatenate([np.sort(rng.choice(K, d, replace=False)) for d in degs if d])
+    A = I._from_sorted_coo(len(degs), K, a_rows, a_cols, None)
+    b_rows = np.repeat(np.arange(K), per_b)
+    b_cols = np.concatenate([np.sort(rng.choice(N, per_b, replace=False)) for _ in range(K)])
+    B = I._from_sorted_coo(K, N, b_rows, b_cols, None)
+    return A, B
+
+
+@pytest.mark.parametrize("tier", ["default", "all_dense", "dense_rebuild"])
+@pytest.mark.parametrize("sr", [api.MIN_PLUS_F32, api.PLUS_TIMES_F64, api.BOOL_OR_AND,
+                                api.OVERLAP_I32])
+def test_light_dense_rows(sr, tier):
+    A, B = light_dense_rows(17)
+    A = values_for(sr, A, 18)
+    B = values_for(sr, B, 19)
+    got, h = check(sr, A, B, TIERS[tier], tier)
+    n = np.diff(got.rp)
+    assert n[3] > 4000 and n[2] > 2048   # above the block tier: dense rows
 
 
 @pytest.mark.parametrize("top", [65535, 65536, 2**31 - 1])
