@@ -618,7 +618,7 @@ static spg_status symbolic_impl(spg_handle* h, int sr, int nprob, const spg_csr*
     }
     h->stats.products = (int64_t)hc->products;
     h->stats.nnz_c = tot;
-    for (int tier = 0; tier < kTiers; ++tier) {
+    for (int tier = 0; tier < kSymTiers; ++tier) {
         int64_t n = 0;
         for (int b = 0; b < kSubBins; ++b) n += hc->sym_bin_count[tier * kSubBins + b];
         h->stats.rows_per_tier[tier] = n;
@@ -1347,7 +1347,7 @@ spg_status spgemm_learned_symbolic(spg_handle* h, spg_semiring sr, const spg_csr
     *c_nnz = hc->nnz[0];
     h->stats.products = (int64_t)hc->products;
     h->stats.nnz_c = hc->nnz[0];
-    for (int tier = 0; tier < kTiers; ++tier) {
+    for (int tier = 0; tier < kSymTiers; ++tier) {
         int64_t n = 0;
         for (int b = 0; b < kSubBins; ++b) n += hc->sym_bin_count[tier * kSubBins + b];
         h->stats.rows_per_tier[tier] = n;

@@ -24,10 +24,15 @@ SPG_DEV int64_t dev_next_pow2_n(int64_t x) {
 
 // block_max: the block tier's limit in effect (the tuning's, or the compact
 // overlap tier's when the positions allow it, set on the device)
-SPG_DEV int num_tier(int64_t nnz, const Tuning& t, int64_t block_max) {
+// Dense rows with fewer than t.rank_light_ub products whose outputs fit one
+// value pass of a half-SM CTA (nnz <= light_n, set on the device) are light:
+// their own tier, taken by the 512-thread rank kernel.
+SPG_DEV int num_tier(int64_t nnz, int64_t ub, const Tuning& t, int64_t block_max,
+                     int64_t light_n) {
     if (nnz == 0) return kTierEmpty;
     if (nnz <= t.num_warp_max_nnz) return kTierWarp;
     if (nnz <= block_max) return kTierBlock;
+    if (nnz <= light_n && ub < t.rank_light_ub) return kTierDenseLight;
     return kTierDense;
 }
 
@@ -78,8 +83,10 @@ __global__ void __launch_bounds__(256) k_num_hist(const Prob* __restrict__ probs
          g += (int64_t)gridDim.x * blockDim.x) {
         const Prob* P;
         const int64_t n = row_nnz(probs, nprob, g, &P);
-        const int tier = (skip && skip[g]) ? kTierEmpty : num_tier(n, t, block_limit(t, ctr));
-        atomicAdd(&s_hist[num_bin_key(tier, ub[g])], 1);
+        const int64_t u = ub[g];
+        const int tier = (skip && skip[g]) ? kTierEmpty
+                                           : num_tier(n, u, t, block_limit(t, ctr), ctr->light_n);
+        atomicAdd(&s_hist[num_bin_key(tier, u)], 1);
     }
     __syncthreads();
     for (int b = threadIdx.x; b < kNumBins; b += blockDim.x)
@@ -112,8 +119,10 @@ __global__ void __launch_bounds__(1024) k_num_scatter(const Prob* __restrict__ p
     if (g < R) {
         const Prob* P;
         const int64_t n = row_nnz(probs, nprob, g, &P);
-        key = num_bin_key((skip && skip[g]) ? kTierEmpty : num_tier(n, t, block_limit(t, ctr)),
-                          ub[g]);
+        const int64_t u = ub[g];
+        key = num_bin_key((skip && skip[g]) ? kTierEmpty
+                                            : num_tier(n, u, t, block_limit(t, ctr), ctr->light_n),
+                          u);
         rank = atomicAdd(&s_cnt[key], 1);
     }
     __syncthreads();
@@ -762,20 +771,18 @@ __host__ __device__ inline size_t rank_region_bytes(int64_t cap) {
 // NT = 1024: one CTA per SM, the whole shared memory for the bitmap and the
 // value array (value passes over slab groups).  NT = 512: two CTAs per SM,
 // each with half of it, for rows whose outputs fit one pass: two rows in
-// flight per SM hide the per-row phases' latency.  Rows are light when they
-// lie in the dense tier's sub-bins from light_sub on (ub_i below the tuning's
-// rank_light_ub: a few thousand products, whose time is per-row latency, not
-// product work) and nnz(C_i) <= n_split.  The 512-thread kernel (small = 1)
-// walks only those sub-bins and takes the light rows; the 1024-thread one
-// (small = 0) takes every other row, each with its own claim counter.
+// flight per SM hide the per-row phases' latency.  The 512-thread kernel
+// takes the light dense rows (their own tier: ub_i below the tuning's
+// rank_light_ub, a few thousand products whose time is per-row latency, not
+// product work, and outputs within one pass), the 1024-thread one the dense
+// tier's; each kernel has its own claim counter.
 template <class S, int NT>
 __global__ void __launch_bounds__(NT, kRankThreads / NT)
     k_num_rank(const Prob* __restrict__ probs, int nprob, const int32_t* __restrict__ rows,
                Counters* ctr, DevStatus* st, int sp_stride,
                int slab_cols, int bm_words, int cap, const uint32_t* __restrict__ bm_cache,
                const int32_t* __restrict__ row_slot, int cache_words, int64_t cache_slots,
-               int stage_words, int ovl_mode, int light_sub, int64_t n_split, int small,
-               int claim) {
+               int stage_words, int ovl_mode, int tier, int claim) {
     using Slot = typename S::Slot;
     using In = typename S::In;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -788,9 +795,8 @@ __global__ void __launch_bounds__(NT, kRankThreads / NT)
     __shared__ int s_wsum[NT / 32];
     const int lane = lane_id(), wid = warp_id(), nwarps = blockDim.x >> 5;
     const int tid = threadIdx.x;
-    const int tmid = ctr->num_bin_off[kTierDense * kSubBins + light_sub];
-    const int tbeg = small ? tmid : ctr->num_bin_off[kTierDense * kSubBins];
-    const int tend = ctr->num_bin_off[(kTierDense + 1) * kSubBins];
+    const int tbeg = ctr->num_bin_off[tier * kSubBins];
+    const int tend = ctr->num_bin_off[(tier + 1) * kSubBins];
     // the value array holds `empty` between passes: filled once here, and each
     // pass's write-out empties the slots it reads
     // overlap: the compact-slot kernel (ovl_mode 1) takes the rows when every
@@ -816,12 +822,6 @@ __global__ void __launch_bounds__(NT, kRankThreads / NT)
         const int64_t i = g - P.row_base;
         const int64_t off = P.c_rp[i];
         const int64_t n = P.c_rp[i + 1] - off;
-        if (r >= tmid && (n <= n_split) != (small != 0)) {   // the other kernel's row
-            __syncthreads();           // every thread has read r
-            if (tid == 0) s_row = nr;
-            __syncthreads();
-            continue;
-        }
         const int64_t a0 = ld_i64(P.A.rp + i), a1 = ld_i64(P.A.rp + i + 1);
         const int ncols = (int)P.B.ncols;
         const int words = (ncols + 31) >> 5;
@@ -1203,6 +1203,56 @@ RankCfg rank_cfg(int64_t max_ncols, int64_t slab, const DevInfo& dev) {
     return c;
 }
 
+// The largest nnz(C_i) of a light dense row for semiring S (0: none): the
+// 1024-thread rank kernel must serve the dense tier, the 512-thread one must
+// fit two CTAs per SM; a light row's outputs fit one pass of the latter.
+template <class S>
+int64_t light_limit(const Tuning& t, int64_t max_ncols, const DevInfo& dev) {
+    if (t.rank_light_ub <= 0) return 0;
+    int64_t slab;
+    int nslabs;
+    dense_slabs(t, max_ncols, &slab, &nslabs);
+    if (!rank_cfg<S, kRankThreads>(max_ncols, slab, dev).ok) return 0;
+    const RankCfg small = rank_cfg<S, kRankThreads / 2>(max_ncols, slab, dev);
+    if (!small.ok) return 0;
+    if (cudaFuncSetAttribute(k_num_rank<S, kRankThreads / 2>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)small.smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, (const void*)k_num_rank<S, kRankThreads / 2>, kRankThreads / 2,
+            small.smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (per_sm < 2) return 0;
+    return S::kVal ? small.cap : INT64_MAX;
+}
+
+// light limits of the semiring: with compact overlap slots (narrow) and
+// without (wide); the same for the other semirings
+struct LightFn {
+    const Tuning* t;
+    int64_t max_ncols;
+    const DevInfo* dev;
+    int64_t narrow = 0, wide = 0;
+    template <class S> void operator()() {
+        if constexpr (std::is_same<S, SrOverlap>::value) {
+            narrow = light_limit<SrOverlapC>(*t, max_ncols, *dev);
+            wide = light_limit<S>(*t, max_ncols, *dev);
+        } else {
+            narrow = wide = light_limit<S>(*t, max_ncols, *dev);
+        }
+    }
+};
+
+__global__ void k_set_light(Counters* ctr, int64_t narrow, int64_t wide) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) ctr->light_n = ctr->ovl_wide ? wide : narrow;
+}
+
 struct NumericLaunch {
     const WsPtrs* w;
     DCsr B0;              // B of the first product (slab pointers: single product only)
@@ -1212,10 +1262,11 @@ struct NumericLaunch {
     const DevInfo* dev;
     cudaStream_t st;
     const SlabTables* tables;
+    int64_t light_narrow, light_wide;   // light-row limits (LightFn)
     cudaError_t err = cudaSuccess;
     template <class S, int NT>
     cudaError_t launch_rank(const RankCfg& c, int64_t slab, int nslabs, int ovl_mode,
-                            int light_sub, int64_t n_split, int small, int claim) {
+                            int tier, int claim) {
         cudaError_t e = cudaFuncSetAttribute(
             k_num_rank<S, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
         if (e != cudaSuccess) return e;
@@ -1225,39 +1276,20 @@ struct NumericLaunch {
             w->probs, nprob, w->rows_num, w->ctr, w->status, nslabs + 1, (int)slab,
             (int)c.bm_words, (int)c.cap, cached ? w->bm_cache : nullptr,
             cached ? w->row_slot : nullptr, (int)w->bm_cache_words, w->bm_cache_slots,
-            c.stage_words, ovl_mode, light_sub, n_split, small, claim);
+            c.stage_words, ovl_mode, tier, claim);
         count_launch(*dev);
         return cudaGetLastError();
     }
-    // the dense tier's rows split: light rows (fewer than rank_light_ub products)
-    // whose outputs fit one pass of the 512-thread kernel take it (claim slot
-    // 4), the rest the 1024-thread kernel (claim slot 3)
+    // the dense tier on the 1024-thread kernel (claim slot 3) and, when light
+    // rows can exist, the light tier on the 512-thread one (claim slot 4)
     template <class S>
-    cudaError_t launch_rank_pair(int64_t slab, int nslabs, int ovl_mode) {
+    cudaError_t launch_rank_pair(int64_t slab, int nslabs, int ovl_mode, int64_t light_n) {
         const RankCfg big = rank_cfg<S, kRankThreads>(max_ncols, slab, *dev);
-        const RankCfg small = rank_cfg<S, kRankThreads / 2>(max_ncols, slab, *dev);
-        int64_t split = 0;
-        if (small.ok && t->rank_light_ub > 0) {   // only where two CTAs really fit an SM
-            cudaError_t ea = cudaFuncSetAttribute(k_num_rank<S, kRankThreads / 2>,
-                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)small.smem);
-            if (ea != cudaSuccess) return ea;
-            int per_sm = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &per_sm, (const void*)k_num_rank<S, kRankThreads / 2>, kRankThreads / 2, small.smem);
-            if (per_sm >= 2) split = S::kVal ? small.cap : INT64_MAX;
+        cudaError_t e = launch_rank<S, kRankThreads>(big, slab, nslabs, ovl_mode, kTierDense, 3);
+        if (e == cudaSuccess && light_n > 0) {
+            const RankCfg small = rank_cfg<S, kRankThreads / 2>(max_ncols, slab, *dev);
+            e = launch_rank<S, kRankThreads / 2>(small, slab, nslabs, ovl_mode, kTierDenseLight, 4);
         }
-        cudaError_t e = cudaSuccess;
-        // sub-bins by floor(log2 ub_i), heaviest first: ub_i < rank_light_ub (a
-        // power of two) from kSubBins - log2(rank_light_ub) on (kSubBins: none)
-        int lg = 0;
-        while (lg < kSubBins && ((int64_t)1 << lg) < t->rank_light_ub) ++lg;
-        const int light_sub = split > 0 ? kSubBins - lg : kSubBins;
-        if (split > 0)
-            e = launch_rank<S, kRankThreads / 2>(small, slab, nslabs, ovl_mode, light_sub, split,
-                                                 1, 4);
-        if (e == cudaSuccess)
-            e = launch_rank<S, kRankThreads>(big, slab, nslabs, ovl_mode, light_sub, split, 0, 3);
         return e;
     }
     template <class S> void operator()() {
@@ -1286,10 +1318,10 @@ struct NumericLaunch {
                 if constexpr (std::is_same<S, SrOverlap>::value) {
                     // compact 12-byte slots when every position fits 16 bits
                     // (twice the outputs per value pass, 32-bit atomics)
-                    e = launch_rank_pair<SrOverlapC>(slab, nslabs, 1);
-                    if (e == cudaSuccess) e = launch_rank_pair<S>(slab, nslabs, 2);
+                    e = launch_rank_pair<SrOverlapC>(slab, nslabs, 1, light_narrow);
+                    if (e == cudaSuccess) e = launch_rank_pair<S>(slab, nslabs, 2, light_wide);
                 } else {
-                    e = launch_rank_pair<S>(slab, nslabs, 0);
+                    e = launch_rank_pair<S>(slab, nslabs, 0, light_narrow);
                 }
                 if (e != cudaSuccess) { err = e; return; }
             } else {
@@ -1385,6 +1417,10 @@ cudaError_t launch_numeric(int sr, const WsPtrs& w, const DCsr& B0, int nprob, i
             w.ctr, t.num_block_max_nnz <= kOvlCompactMax ? kOvlCompactMax : 0);
         count_launch(dev, 2 * nprob + 1);
     }
+    LightFn lf{&t, max_ncols, &dev};
+    if (!dispatch_semiring(sr, lf)) return cudaErrorInvalidValue;
+    k_set_light<<<1, 32, 0, st>>>(w.ctr, lf.narrow, lf.wide);
+    count_launch(dev);
     int64_t blocks = (R + 255) / 256;
     if (blocks > (int64_t)dev.sms * 8) blocks = (int64_t)dev.sms * 8;
     k_num_hist<<<(unsigned)blocks, 256, 0, st>>>(w.probs, nprob, R, t, w.ub, w.ctr, w.skip);
@@ -1395,7 +1431,7 @@ cudaError_t launch_numeric(int sr, const WsPtrs& w, const DCsr& B0, int nprob, i
     mark_stage(dev, kStNumBin, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    NumericLaunch f{&w, B0, nprob, &t, max_ncols, &dev, st, tables};
+    NumericLaunch f{&w, B0, nprob, &t, max_ncols, &dev, st, tables, lf.narrow, lf.wide};
     if (!dispatch_semiring(sr, f)) return cudaErrorInvalidValue;
     return f.err;
 }

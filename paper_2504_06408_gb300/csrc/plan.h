@@ -11,10 +11,11 @@
 namespace spg {
 
 constexpr int kMaxProb = 128;    // products in one batched call
-constexpr int kTiers = 4;        // 0 dense, 1 block, 2 warp, 3 empty
+constexpr int kTiers = 5;        // 0 dense, 1 block, 2 warp, 3 empty, 4 light dense (numeric)
+constexpr int kSymTiers = 4;     // the symbolic phase uses tiers 0..3
 constexpr int kSubBins = 40;     // per tier: by floor(log2(work)), heaviest first
 constexpr int kNumBins = kTiers * kSubBins;
-constexpr int kTierDense = 0, kTierBlock = 1, kTierWarp = 2, kTierEmpty = 3;
+constexpr int kTierDense = 0, kTierBlock = 1, kTierWarp = 2, kTierEmpty = 3, kTierDenseLight = 4;
 
 struct Tuning {
     int64_t sym_warp_max_ub;
@@ -51,6 +52,7 @@ struct Counters {
     int32_t words_ready;                // the word-packed copies of B were built
     int32_t ovl_wide;                   // overlap semiring: a position is outside [0, 2^16)
     int64_t num_block_max;              // numeric: block-tier limit in effect (0: the tuning's)
+    int64_t light_n;                    // numeric: largest nnz(C_i) of a light dense row (0: none)
     unsigned long long learned_nnz;     // learned path: entries of the rows it finished
     int64_t nnz[kMaxProb];              // per-product nnz(C)
 };

@@ -220,8 +220,8 @@ def _stream_ptr(stream=None):
 class Handle:
     """spg_handle wrapper; one per thread, reusable across calls."""
 
-    def __init__(self, tuning: Optional[dict] = None, lib_path: str = LIB_PATH):
-        self.lib = load_library(lib_path)
+    def __init__(self, tuning: Optional[dict] = None, lib_path: Optional[str] = None):
+        self.lib = load_library(lib_path or LIB_PATH)
         self._h = ctypes.c_void_p()
         self._ok(self.lib.spgemm_create(ctypes.byref(self._h)))
         if tuning:
