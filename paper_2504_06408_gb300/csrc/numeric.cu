@@ -709,6 +709,16 @@ struct BitSetOp {
     }
 };
 
+// (+) into a rank slot.  Min-plus folds with a plain atomicMin: reading the
+// slot first (to skip atomics that cannot lower it) puts a dependent
+// shared-memory round trip on every product, which costs more than the
+// atomics it saves (R-MAT 18 numeric dense tier 38.7 -> 36.3 ms).
+template <class S>
+SPG_DEV void rank_acc(typename S::Slot* s, typename S::In a, typename S::In b) {
+    if constexpr (std::is_same<S, SrMpF32>::value) atomicMin(s, f32_to_ordered(__fadd_rn(a, b)));
+    else S::acc(s, a, b);
+}
+
 // kFilter: the walk may reach products outside the pass's columns (no slab
 // table), which are skipped
 template <class S, bool kFilter>
@@ -737,12 +747,16 @@ struct RankAccOp {
             return;
         }
 #endif
-        S::acc(vals + r, a, b);
+        rank_acc<S>(vals + r, a, b);
         cols[r] = col;
     }
 };
 
 constexpr int kRankThreads = 1024;
+// rank scan: chunks of 32 words scanned together (one for the overlap slots,
+// whose walk needs the registers)
+template <class S>
+constexpr int rank_scan_chunks() { return sizeof(typename S::Slot) > 8 ? 1 : 4; }
 
 // bytes of the rank kernel's value array, rounded up to 16
 template <class S>
@@ -870,13 +884,25 @@ __global__ void __launch_bounds__(NT, kRankThreads / NT)
         const int per_warp = ((words + nwarps - 1) / nwarps + 31) & ~31;
         const int wb = wid * per_warp;
         {
+            constexpr int kSU = rank_scan_chunks<S>();
             int run = 0;
-            for (int j = 0; j < per_warp; j += 32) {
-                const int w = wb + j + lane;
-                const int c = w < words ? __popc(bw[w].x) : 0;
-                const int inc = warp_incl_scan(c);
-                if (w < words) bw[w].y = (uint32_t)(run + inc - c);
-                run += __shfl_sync(kFull, inc, 31);
+            // kSU chunks of 32 words at a time: their scans are independent
+            // (only the running total links them), so their shuffles overlap
+            for (int j0 = 0; j0 < per_warp; j0 += 32 * kSU) {
+                int c[kSU], inc[kSU];
+#pragma unroll
+                for (int u = 0; u < kSU; ++u) {
+                    const int w = wb + j0 + 32 * u + lane;
+                    c[u] = (j0 + 32 * u < per_warp && w < words) ? __popc(bw[w].x) : 0;
+                }
+#pragma unroll
+                for (int u = 0; u < kSU; ++u) inc[u] = warp_incl_scan(c[u]);
+#pragma unroll
+                for (int u = 0; u < kSU; ++u) {
+                    const int w = wb + j0 + 32 * u + lane;
+                    if (j0 + 32 * u < per_warp && w < words) bw[w].y = (uint32_t)(run + inc[u] - c[u]);
+                    run += __shfl_sync(kFull, inc[u], 31);
+                }
             }
             if (lane == 0) s_wsum[wid] = run;
             __syncthreads();
@@ -910,7 +936,12 @@ __global__ void __launch_bounds__(NT, kRankThreads / NT)
         //     instead.  Lane l takes outputs t = l, l + 32, ..., finds the
         //     word holding t by a binary search over the words' prefix
         //     counts, the bit by select_bit, and stores C.col[t] (coalesced).
-        {
+        if constexpr (S::kVal) {
+            const int add = s_wsum[wid];
+            const int wend = min(wb + per_warp, words);
+#pragma unroll 4
+            for (int w = wb + lane; w < wend; w += 32) bw[w].y += (uint32_t)add;
+        } else {
             int32_t* stage = reinterpret_cast<int32_t*>(smem_raw) + (size_t)wid * stage_words;
             const int add = s_wsum[wid];
             const int wtot = (wid + 1 < nwarps ? s_wsum[wid + 1] : T) - add;
@@ -922,7 +953,6 @@ __global__ void __launch_bounds__(NT, kRankThreads / NT)
                 const int lw = w < words ? (int)bw[w].y : 0;
                 __syncwarp();
                 if (w < words) bw[w].y = (uint32_t)(lw + add);
-                if constexpr (S::kVal) continue;
                 const int Tc = lnext - lbase;
                 if (Tc == 0) continue;
                 uint32_t bits = w < words ? bw[w].x : 0u;
@@ -961,7 +991,9 @@ __global__ void __launch_bounds__(NT, kRankThreads / NT)
             }
         }
         __syncthreads();
-        if (slot2 >= 0 && slot2 < cache_slots)
+        // (the next row's bitmap: with values, prefetched after the first
+        // pass's walk, by when thread 0's load of its cache slot has landed)
+        if (!S::kVal && slot2 >= 0 && slot2 < cache_slots)
             prefetch_l2(bm_cache + (int64_t)slot2 * cache_words, (uint32_t)cache_words * 4u);
         // (4) values, in passes over groups of column slabs that fit `cap` outputs;
         //     each pass writes its stretch of C.col and C.val
@@ -969,10 +1001,21 @@ __global__ void __launch_bounds__(NT, kRankThreads / NT)
             int s0 = 0;
             while (s0 < nslabs) {
                 const int r0 = (int)bw[(s0 * slab_cols) >> 5].y;
+                // s1 = s0 + 1, then every later slab while the group's outputs
+                // fit cap.  The output count before a slab end grows with the
+                // end, so the lanes test 32 ends at once and the ones that
+                // pass are a prefix of the lanes.
                 int s1 = s0 + 1;
-                while (s1 < nslabs && (int)bw[min((s1 + 1) * slab_cols, ncols + 31) >> 5].y - r0 <= cap)
-                    ++s1;
-                const int r1 = (int)bw[min(s1 * slab_cols, ncols + 31) >> 5].y;
+                for (;;) {
+                    const int t = s1 + 1 + lane;   // group [s0, t)
+                    const bool fits =
+                        t <= nslabs &&
+                        (int)bw[min((int64_t)t * slab_cols, (int64_t)ncols + 31) >> 5].y - r0 <= cap;
+                    const int k = __popc(__ballot_sync(kFull, fits));
+                    s1 += k;
+                    if (k < 32) break;
+                }
+                const int r1 = (int)bw[min((int64_t)s1 * slab_cols, (int64_t)ncols + 31) >> 5].y;
                 const int cnt = r1 - r0;
                 if (cnt > 0) {
                     const int clo = s0 * slab_cols;
@@ -990,6 +1033,9 @@ __global__ void __launch_bounds__(NT, kRankThreads / NT)
                         cta_range_products<In, S::kVal>(P.A, P.B, a0, a1, le, mode, sp, sp_stride,
                                                         nslabs, 0, nslabs, bs, op);
                     }
+                    if (slot2 >= 0 && slot2 < cache_slots)
+                        prefetch_l2(bm_cache + (int64_t)slot2 * cache_words, (uint32_t)cache_words * 4u);
+                    slot2 = -1;   // once per row
                     typename S::Out* cv = reinterpret_cast<typename S::Out*>(P.c_val) + off + r0;
                     int32_t* cc = P.c_col + off + r0;
                     for (int t = tid; t < cnt; t += blockDim.x) {
