@@ -307,9 +307,7 @@ __global__ void __launch_bounds__(kMergeThreads)
 #pragma unroll
                 for (int u = 0; u < kU; ++u) {
                     if (c[u] < 0) continue;
-                    const uint32_t bit = 1u << (c[u] & 31);
-                    uint32_t* wp = &pw[c[u] >> 5].x;
-                    if (!(*wp & bit)) atomicOr(wp, bit);
+                    atomicOr(&pw[c[u] >> 5].x, 1u << (c[u] & 31));   // no read of the word first
                 }
             }
         }

@@ -158,8 +158,8 @@ struct HashAccOp {
 
 // Dense slab accumulator.  The presence bitmap is kept for every semiring:
 // semirings whose Slot cannot mark presence set the bit on every product
-// (after a read, so repeated columns cost no atomic); the others set it only
-// on a column's first product, which their Slot reveals.
+// (a plain atomicOr: no read of the word first); the others set it only on a
+// column's first product, which their Slot reveals.
 template <class S>
 struct DenseAccOp {
     typename S::Slot* vals;
@@ -170,7 +170,7 @@ struct DenseAccOp {
         const int32_t c = col - lo;
         const uint32_t bit = 1u << (c & 31);
         if constexpr (S::kBitmap) {
-            if (!(bm[c >> 5] & bit)) atomicOr(bm + (c >> 5), bit);
+            atomicOr(bm + (c >> 5), bit);
             if constexpr (S::kVal) S::acc(vals + c, a, b);
         } else {
             if (S::acc_first(vals + c, a, b)) atomicOr(bm + (c >> 5), bit);
@@ -703,9 +703,7 @@ struct BitSetOp {
     uint2* bw;
     template <class In> SPG_DEV void any(int32_t col, In, In, bool valid) {
         if (!valid) return;
-        const uint32_t bit = 1u << (col & 31);
-        uint32_t* word = &bw[col >> 5].x;
-        if (!(*word & bit)) atomicOr(word, bit);
+        atomicOr(&bw[col >> 5].x, 1u << (col & 31));   // plain atomic: no read of the word first
     }
 };
 
