@@ -771,12 +771,12 @@ template <class S>
 constexpr size_t rank_entry_bytes() {
     return S::kVal ? sizeof(typename S::Slot) + 4 : 0;
 }
-// the value array's region, which first serves as the warps' C.col staging:
-// at least 3 KB per warp of an NT-thread CTA
+// the value array's region; without values it serves as the warps' C.col
+// staging instead: at least 3 KB per warp of an NT-thread CTA
 template <class S, int NT>
 __host__ __device__ inline size_t rank_region_bytes(int64_t cap) {
     const size_t v = rank_val_bytes<S>(cap);
-    constexpr size_t kStageMin = (size_t)(NT / 32) * 3072;
+    constexpr size_t kStageMin = S::kVal ? 0 : (size_t)(NT / 32) * 3072;
     return v > kStageMin ? v : kStageMin;
 }
 
