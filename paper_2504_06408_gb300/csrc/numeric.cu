@@ -707,16 +707,6 @@ struct BitSetOp {
     }
 };
 
-// (+) into a rank slot.  Min-plus folds with a plain atomicMin: reading the
-// slot first (to skip atomics that cannot lower it) puts a dependent
-// shared-memory round trip on every product, which costs more than the
-// atomics it saves (R-MAT 18 numeric dense tier 38.7 -> 36.3 ms).
-template <class S>
-SPG_DEV void rank_acc(typename S::Slot* s, typename S::In a, typename S::In b) {
-    if constexpr (std::is_same<S, SrMpF32>::value) atomicMin(s, f32_to_ordered(__fadd_rn(a, b)));
-    else S::acc(s, a, b);
-}
-
 // kFilter: the walk may reach products outside the pass's columns (no slab
 // table), which are skipped
 template <class S, bool kFilter>
@@ -745,7 +735,7 @@ struct RankAccOp {
             return;
         }
 #endif
-        rank_acc<S>(vals + r, a, b);
+        S::acc(vals + r, a, b);
         cols[r] = col;
     }
 };

@@ -92,10 +92,10 @@ struct SrMpF32 {
     using Out = float;
     static constexpr bool kVal = true, kBitmap = false;
     static SPG_DEV Slot empty() { return 0xffffffffu; }
-    // read first: once a slot is small, most products cannot lower it
+    // a plain atomicMin: reading the slot first to skip products that cannot
+    // lower it puts a dependent shared-memory round trip on every product
     static SPG_DEV void acc(Slot* s, In a, In b) {
-        const uint32_t m = f32_to_ordered(__fadd_rn(a, b));
-        if (m < *(volatile Slot*)s) atomicMin(s, m);
+        atomicMin(s, f32_to_ordered(__fadd_rn(a, b)));
     }
     // as acc(); returns true if the slot was untouched before (first product)
     static SPG_DEV bool acc_first(Slot* s, In a, In b) {

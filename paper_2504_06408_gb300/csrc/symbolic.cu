@@ -543,8 +543,12 @@ __global__ void __launch_bounds__(kBlockThreads, 3)
                 cta_row_products<In, kWords, Op, kBatch, kSymDenseWin>(
                     Ax, Bx, a0, a1, P.nnz_base + (a0 - ld_i64(P.A.rp)), slab, bs, op);
             }
+            int mine = 0;
+            bool counted = false;   // (CTA-uniform)
             if (nslabs == 1 && cache_slots > 0 && words <= cache_words) {
-                // keep the row's bitmap for the numeric phase while cache slots last
+                // keep the row's bitmap for the numeric phase while cache slots
+                // last; the copy counts the row's columns on the way (words past
+                // `words` in the last group of four are not the row's)
                 if (threadIdx.x == 0) {
                     const int sl = atomicAdd(&ctr->bm_next, 1);
                     s_slot = sl < cache_slots ? sl : -1;
@@ -554,11 +558,18 @@ __global__ void __launch_bounds__(kBlockThreads, 3)
                 if (s_slot >= 0) {
                     uint4* dst = reinterpret_cast<uint4*>(bm_cache + (int64_t)s_slot * cache_words);
                     const uint4* src = reinterpret_cast<const uint4*>(bm);
-                    for (int w = threadIdx.x; w < (words + 3) / 4; w += blockDim.x) __stcs(dst + w, src[w]);
+                    for (int w = threadIdx.x; w < (words + 3) / 4; w += blockDim.x) {
+                        const uint4 v = src[w];
+                        __stcs(dst + w, v);
+                        const int rest = words - 4 * w;   // >= 1
+                        mine += __popc(v.x) + (rest > 1 ? __popc(v.y) : 0) +
+                                (rest > 2 ? __popc(v.z) : 0) + (rest > 3 ? __popc(v.w) : 0);
+                    }
+                    counted = true;
                 }
             }
-            int mine = 0;
-            for (int w = threadIdx.x; w < words; w += blockDim.x) mine += __popc(bm[w]);
+            if (!counted)
+                for (int w = threadIdx.x; w < words; w += blockDim.x) mine += __popc(bm[w]);
             mine = warp_sum(mine);
             if (lane == 0 && mine) atomicAdd(&s_tot, (unsigned long long)mine);
             __syncthreads();
