@@ -907,7 +907,9 @@ def main():
     achieved = t_alg / (d_ms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
     traffic = traffic_from_profiles(kernel_source_hash()) if args.scale == SCALE else None
-    roofline = {"bound": "hbm", "kernel": "k_num_rank<SrMpF32> (numeric dense tier)",
+    roofline = {"bound": "hbm",
+                "kernel": "k_num_rank<SrMpF32> (numeric dense tier: the 1024-thread launch for "
+                          "dense rows and the 512-thread one for light rows)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_kind": peak_kind, "traffic": traffic, "kernel_ms": d_ms,
                 "algorithmic_bytes": t_alg}
