@@ -899,7 +899,9 @@ def main():
     # traffic model restricted to the rows it processes
     hc_rp = c_rp.cpu().numpy()
     ub, deg, cnt = row_stats(A, hc_rp)
-    dense = cnt > 2048      # numeric dense tier: nnz(C_i) above the block-tier limit
+    # numeric dense tier: nnz(C_i) above the block-tier limit in effect (the
+    # library's default 2048 unless the tuning sets it)
+    dense = cnt > int((tuning or {}).get("num_block_max_nnz") or 2048)
     s_in, s_out = 4, 4
     t_alg = (16 * int(dense.sum()) + int(deg[dense].sum()) * (4 + s_in) + 8 * int(deg[dense].sum())
              + int(ub[dense].sum()) * (4 + s_in) + int(cnt[dense].sum()) * (4 + s_out))
