@@ -807,9 +807,9 @@ __global__ void __launch_bounds__(NT, kRankThreads / NT)
     if constexpr (S::kVal) fill_slots<S>(vals, cap);
     // Rows are claimed one ahead: thread 0 claims the next row while this one
     // starts, and loads its id, then its cache slot, each a phase later, and
-    // prefetches its cached bitmap into L2 before the value passes, so the
-    // next row's bitmap copy does not wait on DRAM (nothing waits on these
-    // loads until a phase boundary has passed).
+    // prefetches its cached bitmap into L2 after the first value pass's walk,
+    // so the next row's bitmap copy does not wait on DRAM (nothing waits on
+    // these loads until a phase boundary has passed).
     if (tid == 0) s_row = tbeg + atomicAdd(&ctr->claim[claim], 1);
     __syncthreads();
     for (;;) {
