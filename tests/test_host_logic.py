@@ -179,3 +179,19 @@ def test_set_tuning_rejects_unknown_fields():
         h.set_tuning(num_block_max=4096)      # a misspelt field is not ignored
     with pytest.raises(ValueError):
         h.set_tuning(reserved=1)
+
+
+def test_shipped_tuning_names_only_known_fields():
+    """Every entry of the shipped GB300 tuning loads by its key and names only
+    spg_tuning fields with positive values (Handle.set_tuning raises on an
+    unknown name, which would stop the benchmark on the GPU)."""
+    known = {name for name, _ in api.spg_tuning._fields_} - {"reserved"}
+    with open(autotune.SHIPPED) as f:
+        data = json.load(f)
+    assert data
+    for key, tuning in data.items():
+        device, sr_name, tag = key.split("|")
+        sr = next(k for k, v in api.SEMIRING_NAMES.items() if v == sr_name)
+        assert autotune.load(sr, tag, autotune.SHIPPED, device=device) == tuning
+        assert set(tuning) <= known, key
+        assert all(isinstance(v, int) and v > 0 for v in tuning.values()), key
